@@ -1,0 +1,155 @@
+"""CPU oracle for the fork-join workloads -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg
+(and its ``--impl reference`` arm) may import this package.  The library's
+compute path never does: it shares no code with the oracle.
+
+The routines live in ``oracle.cpp`` (plain sequential C++, serial elision of
+each task program) and ``fmm_oracle.cpp`` (the FP64 Laplace FMM, stepwise);
+this module builds them with g++ into ``liboracle.so`` and exposes thin ctypes
+wrappers taking numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["oracle.cpp", "fmm_oracle.cpp"]
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no fused multiply-add, so every FP op rounds)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+           "-o", tmp] + srcs
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            u64, i64, i32, f64 = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            P = ctypes.c_void_p
+            sigs = {
+                "orc_splitmix64_next": (u64, [u64]),
+                "orc_fib": (i64, [i32, P]),
+                "orc_nqueens_bitmask": (u64, [i32, P]),
+                "orc_nqueens_array": (u64, [i32, P]),
+                "orc_nqueens_permutations": (u64, [i32]),
+                "orc_uts_recursive": (None, [u64, ctypes.c_uint32, ctypes.c_uint32, u64, P, P, P]),
+                "orc_uts_bfs": (None, [u64, ctypes.c_uint32, ctypes.c_uint32, u64, P, P]),
+                "orc_sort_u32": (None, [P, P, u64]),
+                "orc_integrate_thread": (f64, [f64, f64, f64, P]),
+                "orc_integrate_block": (f64, [f64, f64, f64, i32, P]),
+                "orc_kclique": (u64, [i64, P, i64, i32, i32, P]),
+                "orc_orient": (None, [i64, P, i64, i32, P, P]),
+                "orc_kclique_brute": (u64, [i32, P, i64, i32]),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def splitmix64(state: int) -> int:
+    return int(_load().orc_splitmix64_next(state))
+
+
+def fib(n: int):
+    """(fib(n), task count)."""
+    t = ctypes.c_uint64(0)
+    v = _load().orc_fib(n, ctypes.byref(t))
+    return int(v), int(t.value)
+
+
+def nqueens(n: int, algorithm: str = "bitmask"):
+    """(solutions, tasks) for the one-task-per-placed-row N-Queens tree."""
+    t = ctypes.c_uint64(0)
+    fn = {"bitmask": _load().orc_nqueens_bitmask, "array": _load().orc_nqueens_array}[algorithm]
+    s = fn(n, ctypes.byref(t))
+    return int(s), int(t.value)
+
+
+def nqueens_permutations(n: int) -> int:
+    return int(_load().orc_nqueens_permutations(n))
+
+
+UTS_THRESHOLD_Q0199 = 199 * 2 ** 64 // 1000  # floor(0.199 * 2^64), exact integer
+
+
+def uts(seed: int = 42, root_children: int = 2000, m: int = 5, threshold: int = UTS_THRESHOLD_Q0199,
+        algorithm: str = "recursive"):
+    """(nodes, leaves) of the hashed unbalanced tree."""
+    n, l, d = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    if algorithm == "recursive":
+        _load().orc_uts_recursive(seed, root_children, m, threshold, ctypes.byref(n), ctypes.byref(l),
+                                  ctypes.byref(d))
+    else:
+        _load().orc_uts_bfs(seed, root_children, m, threshold, ctypes.byref(n), ctypes.byref(l))
+    return int(n.value), int(l.value)
+
+
+def sort_u32(keys: np.ndarray) -> np.ndarray:
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    out = np.empty_like(keys)
+    _load().orc_sort_u32(_ptr(keys), _ptr(out), keys.size)
+    return out
+
+
+def integrate_thread(a: float, b: float, eps: float):
+    t = ctypes.c_uint64(0)
+    v = _load().orc_integrate_thread(a, b, eps, ctypes.byref(t))
+    return float(v), int(t.value)
+
+
+def integrate_block(a: float, b: float, eps: float, block_size: int):
+    t = ctypes.c_uint64(0)
+    v = _load().orc_integrate_block(a, b, eps, block_size, ctypes.byref(t))
+    return float(v), int(t.value)
+
+
+def kclique(n: int, edges: np.ndarray, k: int, order: str = "degree", per_edge: bool = False):
+    """Total k-clique count (and per-DAG-edge counts if asked)."""
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    m = edges.shape[0]
+    pe = np.zeros(max(m, 1), dtype=np.uint64) if per_edge else None
+    total = _load().orc_kclique(n, _ptr(edges), m, k, {"degree": 0, "id": 1}[order],
+                                _ptr(pe) if pe is not None else None)
+    return (int(total), pe[:m]) if per_edge else int(total)
+
+
+def orient(n: int, edges: np.ndarray, order: str = "degree"):
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    m = edges.shape[0]
+    off = np.zeros(n + 1, dtype=np.int64)
+    adj = np.zeros(max(m, 1), dtype=np.int32)
+    _load().orc_orient(n, _ptr(edges), m, {"degree": 0, "id": 1}[order], _ptr(off), _ptr(adj))
+    return off, adj[:m]
+
+
+def kclique_brute(n: int, edges: np.ndarray, k: int) -> int:
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    return int(_load().orc_kclique_brute(n, _ptr(edges), edges.shape[0], k))

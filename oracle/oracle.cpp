@@ -1,0 +1,361 @@
+// CPU oracle for the GTaP fork-join workloads.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, sequential
+// statement of what each task program computes.  It is used by the tests, by
+// the package's smoke check and by the bench's CPU-baseline leg, never by the
+// library's compute path, and it shares no code, header or constant table
+// with the CUDA sources.
+//
+// Every integer program is the *serial elision* of its task program: each
+// fork ("task") becomes an ordinary call and each join ("taskwait") a no-op.
+// The paper states that the queue clause does not change a program's meaning
+// (Sec. 4.2, DAQ) and fork-join over these programs is deterministic, so the
+// GPU runtime must reach exactly these results.  Each routine also counts the
+// task invocations the GPU program creates, so the task counts can be
+// compared too.
+//
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -shared -fPIC (no fused
+// multiply-add, so floating-point programs round at every operation).
+//
+// Parity status per routine (see tests/test_oracle_pins.py):
+//   fib, nqueens, uts, sort, integrate, kclique: pinned.
+//   fmm: pinned against the direct O(N^2) sum (exact regime and convergence).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the state advances by the
+// golden-ratio increment and the output is a 3-step xor-shift-multiply
+// finaliser.  splitmix64(x) below is "advance once from state x, then mix",
+// i.e. the first output of a stream seeded x.
+uint64_t sm64_finalize(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+uint64_t splitmix64(uint64_t x) { return sm64_finalize(x + 0x9E3779B97F4A7C15ULL); }
+
+}  // namespace
+
+extern "C" {
+
+// ---------------------------------------------------------------------------
+// SplitMix64 stream output k of seed s (for the golden-vector pin).
+uint64_t orc_splitmix64_next(uint64_t state_before) { return splitmix64(state_before); }
+
+// ---------------------------------------------------------------------------
+// Fibonacci, no cutoff (Sec. 6.3, "Fibonacci": a task at every recursive call).
+// fib(n) = n for n < 2, else fib(n-1) + fib(n-2), summed in int64.
+static int64_t fib_rec(int n, uint64_t* tasks) {
+    ++*tasks;
+    if (n < 2) return n;
+    int64_t l = fib_rec(n - 1, tasks);  // task
+    int64_t r = fib_rec(n - 2, tasks);  // task
+    return l + r;                        // after taskwait
+}
+int64_t orc_fib(int n, uint64_t* tasks) {
+    uint64_t t = 0;
+    int64_t v = fib_rec(n, &t);
+    if (tasks) *tasks = t;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// N-Queens by bitmask backtracking (Sec. 6.3, "N-Queens"), one task per
+// placed row: the root is the empty board at row 0, and a task at row r
+// spawns one child for every column where a queen in row r is not attacked.
+// A task at row n is a solution.  Nodes counts every task (root included).
+static void nq_bits(int n, int row, uint32_t cols, uint32_t diag_l, uint32_t diag_r,
+                    uint64_t* sols, uint64_t* nodes) {
+    ++*nodes;
+    if (row == n) { ++*sols; return; }
+    const uint32_t full = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    uint32_t avail = ~(cols | diag_l | diag_r) & full;
+    while (avail) {
+        uint32_t bit = avail & (0u - avail);
+        avail ^= bit;
+        nq_bits(n, row + 1, cols | bit, (diag_l | bit) << 1, (diag_r | bit) >> 1, sols, nodes);
+    }
+}
+uint64_t orc_nqueens_bitmask(int n, uint64_t* nodes) {
+    uint64_t s = 0, t = 0;
+    nq_bits(n, 0, 0, 0, 0, &s, &t);
+    if (nodes) *nodes = t;
+    return s;
+}
+
+// Independent second algorithm: queens stored as a column array, attacks
+// checked pairwise, no bit tricks.  Same tree, so the same node count.
+static void nq_array(int n, int row, int* q, uint64_t* sols, uint64_t* nodes) {
+    ++*nodes;
+    if (row == n) { ++*sols; return; }
+    for (int c = 0; c < n; ++c) {
+        bool ok = true;
+        for (int r = 0; r < row && ok; ++r) {
+            int dc = q[r] - c;
+            if (dc < 0) dc = -dc;
+            if (q[r] == c || dc == row - r) ok = false;
+        }
+        if (ok) { q[row] = c; nq_array(n, row + 1, q, sols, nodes); }
+    }
+}
+uint64_t orc_nqueens_array(int n, uint64_t* nodes) {
+    std::vector<int> q(n > 0 ? n : 1);
+    uint64_t s = 0, t = 0;
+    nq_array(n, 0, q.data(), &s, &t);
+    if (nodes) *nodes = t;
+    return s;
+}
+
+// Brute force: every permutation of columns (one queen per row and column),
+// keeping those with no two queens on a diagonal.
+uint64_t orc_nqueens_permutations(int n) {
+    std::vector<int> p(n);
+    for (int i = 0; i < n; ++i) p[i] = i;
+    uint64_t count = 0;
+    if (n == 0) return 1;
+    do {
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i)
+            for (int j = i + 1; j < n && ok; ++j)
+                if (std::abs(p[i] - p[j]) == j - i) ok = false;
+        if (ok) ++count;
+    } while (std::next_permutation(p.begin(), p.end()));
+    return count;
+}
+
+// ---------------------------------------------------------------------------
+// Unbalanced hashed tree (the UTS-like workload of the integer benchmark
+// set).  Node ids: root = splitmix64(seed); child i (0-based) of p =
+// splitmix64(p ^ (0x9E3779B97F4A7C15 * (i + 1))).  The root has
+// root_children children; any other node v has m children iff
+// splitmix64(v ^ 0xD1B54A32D192ED03) < threshold, else none.
+static uint64_t uts_child(uint64_t parent, uint32_t i) {
+    return splitmix64(parent ^ (0x9E3779B97F4A7C15ULL * (uint64_t)(i + 1)));
+}
+static uint32_t uts_arity(uint64_t v, uint32_t m, uint64_t threshold) {
+    return splitmix64(v ^ 0xD1B54A32D192ED03ULL) < threshold ? m : 0u;
+}
+struct UtsTotals { uint64_t nodes, leaves, max_depth; };
+static void uts_rec(uint64_t v, uint32_t arity, uint32_t m, uint64_t thr, uint64_t depth, UtsTotals* t) {
+    ++t->nodes;
+    if (depth > t->max_depth) t->max_depth = depth;
+    if (arity == 0) { ++t->leaves; return; }
+    for (uint32_t i = 0; i < arity; ++i) {
+        uint64_t c = uts_child(v, i);
+        uts_rec(c, uts_arity(c, m, thr), m, thr, depth + 1, t);
+    }
+}
+void orc_uts_recursive(uint64_t seed, uint32_t root_children, uint32_t m, uint64_t threshold,
+                       uint64_t* nodes, uint64_t* leaves, uint64_t* max_depth) {
+    UtsTotals t{0, 0, 0};
+    uts_rec(splitmix64(seed), root_children, m, threshold, 0, &t);
+    *nodes = t.nodes; *leaves = t.leaves;
+    if (max_depth) *max_depth = t.max_depth;
+}
+// Independent traversal: breadth-first with an explicit FIFO, no recursion.
+void orc_uts_bfs(uint64_t seed, uint32_t root_children, uint32_t m, uint64_t threshold,
+                 uint64_t* nodes, uint64_t* leaves) {
+    std::vector<uint64_t> frontier{splitmix64(seed)}, next;
+    uint64_t n = 0, l = 0;
+    bool root_level = true;
+    while (!frontier.empty()) {
+        next.clear();
+        for (uint64_t v : frontier) {
+            ++n;
+            uint32_t a = root_level ? root_children : uts_arity(v, m, threshold);
+            if (a == 0) ++l;
+            for (uint32_t i = 0; i < a; ++i) next.push_back(uts_child(v, i));
+        }
+        root_level = false;
+        frontier.swap(next);
+    }
+    *nodes = n; *leaves = l;
+}
+
+// ---------------------------------------------------------------------------
+// Mergesort (Cilksort, Sec. 6.3): the result of any correct sort is the
+// ascending order of the keys; the library sort is the oracle.
+void orc_sort_u32(const uint32_t* in, uint32_t* out, uint64_t n) {
+    std::memcpy(out, in, n * sizeof(uint32_t));
+    std::sort(out, out + n);
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive trapezoid integration with Richardson extrapolation (Program 1).
+// The integrand is fixed to the Runge function 1/(1 + 25 x^2), written with
+// + - * / only so that every step is correctly rounded on any IEEE machine.
+static double runge(double x) { return 1.0 / (1.0 + (25.0 * x) * x); }
+static double trap(double a, double b) { return ((b - a) * (runge(a) + runge(b))) * 0.5; }
+
+// Thread mode, Program 1(a): one trapezoid for the coarse estimate, two for
+// the fine one; accept when they agree within eps, else fork on the halves.
+static double integ_thread(double a, double b, double eps, uint64_t* tasks) {
+    ++*tasks;
+    double m = 0.5 * (a + b);
+    double coarse = trap(a, b);
+    double fine = trap(a, m) + trap(m, b);
+    if (std::fabs(fine - coarse) < eps) return (4.0 * fine - coarse) / 3.0;
+    double l = integ_thread(a, m, eps, tasks);
+    double r = integ_thread(m, b, eps, tasks);
+    return l + r;
+}
+double orc_integrate_thread(double a, double b, double eps, uint64_t* tasks) {
+    uint64_t t = 0;
+    double v = integ_thread(a, b, eps, &t);
+    if (tasks) *tasks = t;
+    return v;
+}
+
+// Block mode, Program 1(b): block_trap(a, b, n) splits [a, b] into n equal
+// trapezoids evaluated by the block's threads.  The paper does not fix the
+// summation order; the one used here (and by the GPU program) is: node
+// x_i = a + h*i (x_n = b), thread t sums trapezoids t, t+B, t+2B, ... in
+// order, then the B partial sums are combined by the halving tree
+// s[t] += s[t + s] for s = B/2, B/4, ..., 1.
+static double block_trap(double a, double b, int n, int B) {
+    double h = (b - a) / (double)n;
+    std::vector<double> part(B, 0.0);
+    for (int t = 0; t < B; ++t) {
+        double s = 0.0;
+        for (int i = t; i < n; i += B) {
+            double x0 = a + h * (double)i;
+            double x1 = (i + 1 == n) ? b : a + h * (double)(i + 1);
+            s += ((x1 - x0) * (runge(x0) + runge(x1))) * 0.5;
+        }
+        part[t] = s;
+    }
+    for (int stride = B / 2; stride >= 1; stride /= 2)
+        for (int t = 0; t < stride; ++t) part[t] += part[t + stride];
+    return part[0];
+}
+static double integ_block(double a, double b, double eps, int B, uint64_t* tasks) {
+    ++*tasks;
+    const int NTRAP = 256;
+    double coarse = block_trap(a, b, NTRAP, B);
+    double fine = block_trap(a, b, 2 * NTRAP, B);
+    if (std::fabs(fine - coarse) < eps) return (4.0 * fine - coarse) / 3.0;
+    double m = 0.5 * (a + b);
+    double l = integ_block(a, m, eps, B, tasks);
+    double r = integ_block(m, b, eps, B, tasks);
+    return l + r;
+}
+double orc_integrate_block(double a, double b, double eps, int block_size, uint64_t* tasks) {
+    uint64_t t = 0;
+    double v = integ_block(a, b, eps, block_size, &t);
+    if (tasks) *tasks = t;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// k-clique counting by graph orientation (Sec. 6.4.2).  Orient every
+// undirected edge from the lower to the higher vertex of a total order
+// (order_mode 0: (degree, id) lexicographic; 1: id), giving a DAG in which
+// every k-clique appears exactly once as a chain.  For each directed edge
+// (u, v) take C = N+(u) intersect N+(v) and count the (k-2)-cliques inside
+// C: count(S, 1) = |S|, count(S, j) = sum over w in S of count(S n N+(w), j-1).
+struct Dag { std::vector<int64_t> off; std::vector<int32_t> adj; };
+
+static Dag orient(int64_t n, const int32_t* edges, int64_t m, int order_mode) {
+    std::vector<int64_t> deg(n, 0);
+    for (int64_t e = 0; e < m; ++e) { ++deg[edges[2 * e]]; ++deg[edges[2 * e + 1]]; }
+    auto before = [&](int32_t a, int32_t b) {
+        if (order_mode == 0 && deg[a] != deg[b]) return deg[a] < deg[b];
+        return a < b;
+    };
+    Dag g;
+    g.off.assign(n + 1, 0);
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        ++g.off[(before(a, b) ? a : b) + 1];
+    }
+    for (int64_t v = 0; v < n; ++v) g.off[v + 1] += g.off[v];
+    g.adj.assign(m, 0);
+    std::vector<int64_t> fill(g.off.begin(), g.off.end() - 1);
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        if (before(a, b)) g.adj[fill[a]++] = b; else g.adj[fill[b]++] = a;
+    }
+    for (int64_t v = 0; v < n; ++v) std::sort(g.adj.begin() + g.off[v], g.adj.begin() + g.off[v + 1]);
+    return g;
+}
+
+static std::vector<int32_t> intersect(const int32_t* a, int64_t na, const int32_t* b, int64_t nb) {
+    std::vector<int32_t> out;
+    std::set_intersection(a, a + na, b, b + nb, std::back_inserter(out));
+    return out;
+}
+
+static uint64_t count_in(const Dag& g, const std::vector<int32_t>& S, int j) {
+    if (j == 1) return S.size();
+    uint64_t total = 0;
+    for (int32_t w : S) {
+        std::vector<int32_t> T = intersect(S.data(), (int64_t)S.size(), g.adj.data() + g.off[w],
+                                           g.off[w + 1] - g.off[w]);
+        if ((int)T.size() >= j - 1) total += count_in(g, T, j - 1);
+    }
+    return total;
+}
+
+// Total count; per_edge (optional, length m) receives the count of each
+// directed edge in DAG order (vertex u ascending, then its sorted out-list).
+uint64_t orc_kclique(int64_t n, const int32_t* edges, int64_t m, int k, int order_mode,
+                     uint64_t* per_edge) {
+    if (k == 1) return (uint64_t)n;
+    if (k == 2) { if (per_edge) for (int64_t e = 0; e < m; ++e) per_edge[e] = 1; return (uint64_t)m; }
+    Dag g = orient(n, edges, m, order_mode);
+    uint64_t total = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        for (int64_t p = g.off[u]; p < g.off[u + 1]; ++p) {
+            int32_t v = g.adj[p];
+            std::vector<int32_t> C = intersect(g.adj.data() + g.off[u], g.off[u + 1] - g.off[u],
+                                               g.adj.data() + g.off[v], g.off[v + 1] - g.off[v]);
+            uint64_t c = ((int)C.size() >= k - 2) ? count_in(g, C, k - 2) : 0;
+            if (per_edge) per_edge[p] = c;
+            total += c;
+        }
+    }
+    return total;
+}
+
+// The oriented DAG itself (CSR), for checking the GPU orientation step.
+// off has n+1 entries, adj has m entries.
+void orc_orient(int64_t n, const int32_t* edges, int64_t m, int order_mode, int64_t* off, int32_t* adj) {
+    Dag g = orient(n, edges, m, order_mode);
+    std::memcpy(off, g.off.data(), (n + 1) * sizeof(int64_t));
+    std::memcpy(adj, g.adj.data(), m * sizeof(int32_t));
+}
+
+// Brute force for tiny graphs (n <= 64): every k-subset of the vertices in
+// lexicographic order, kept if all of its pairs are edges.
+uint64_t orc_kclique_brute(int n, const int32_t* edges, int64_t m, int k) {
+    std::vector<std::vector<char>> a(n, std::vector<char>(n, 0));
+    for (int64_t e = 0; e < m; ++e) {
+        a[edges[2 * e]][edges[2 * e + 1]] = 1;
+        a[edges[2 * e + 1]][edges[2 * e]] = 1;
+    }
+    if (k <= 0 || k > n) return k == 0 ? 1 : 0;
+    std::vector<int> c(k);
+    for (int i = 0; i < k; ++i) c[i] = i;
+    uint64_t count = 0;
+    while (true) {
+        bool clique = true;
+        for (int i = 0; i < k && clique; ++i)
+            for (int j = i + 1; j < k && clique; ++j)
+                if (!a[c[i]][c[j]]) clique = false;
+        if (clique) ++count;
+        int i = k - 1;
+        while (i >= 0 && c[i] == n - k + i) --i;
+        if (i < 0) break;
+        ++c[i];
+        for (int j = i + 1; j < k; ++j) c[j] = c[j - 1] + 1;
+    }
+    return count;
+}
+
+}  // extern "C"

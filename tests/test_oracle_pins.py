@@ -1,0 +1,250 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong shift or index, a swapped operand) breaks at least one of them:
+closed forms, published values, brute force on tiny inputs, an independent
+second algorithm, and structural invariants.
+"""
+import math
+import os
+from itertools import combinations, permutations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_05982_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------------------- hashing
+def test_splitmix64_published_vector():
+    state = 0
+    for k, hexval in _read_golden("splitmix64_seed0.txt"):
+        assert oracle.splitmix64(state) == int(hexval, 16), k
+        state = (state + 0x9E3779B97F4A7C15) & (2 ** 64 - 1)
+
+
+def test_input_stream_matches_published_vector():
+    # the shared input generator follows the same published definition
+    vals = inputs.splitmix64_stream(0, 0, 3)
+    want = [int(h, 16) for _, h in _read_golden("splitmix64_seed0.txt")]
+    assert [int(v) for v in vals] == want
+
+
+# --------------------------------------------------------------------------- fib
+def _fib_fast_doubling(n):
+    # F(2k) = F(k) (2F(k+1) - F(k)), F(2k+1) = F(k)^2 + F(k+1)^2
+    def fd(k):
+        if k == 0:
+            return 0, 1
+        a, b = fd(k >> 1)
+        c = a * (2 * b - a)
+        d = a * a + b * b
+        return (d, c + d) if k & 1 else (c, d)
+    return fd(n)[0]
+
+
+def test_fib_closed_form_and_task_count():
+    for n in range(0, 27):
+        v, t = oracle.fib(n)
+        assert v == _fib_fast_doubling(n)
+        # every call is one task: T(n) = 1 + T(n-1) + T(n-2), T(0)=T(1)=1 -> 2F(n+1) - 1
+        assert t == 2 * _fib_fast_doubling(n + 1) - 1
+    assert oracle.fib(30) == (832040, 2692537)
+
+
+def test_fib_binet():
+    phi = (1 + 5 ** 0.5) / 2
+    for n in (10, 20, 30):
+        assert oracle.fib(n)[0] == round(phi ** n / 5 ** 0.5)
+
+
+# --------------------------------------------------------------------------- n-queens
+def test_nqueens_published_counts():
+    for n, sols in _read_golden("nqueens_solutions.txt"):
+        n, sols = int(n), int(sols)
+        assert oracle.nqueens(n)[0] == sols, n
+
+
+def test_nqueens_permutation_brute_force():
+    for n in range(1, 10):
+        assert oracle.nqueens(n)[0] == oracle.nqueens_permutations(n)
+
+
+def _partial_placements(n):
+    # brute force over column tuples: count valid placements of r queens in rows 0..r-1
+    total = 0
+    for r in range(n + 1):
+        for cols in permutations(range(n), r):
+            if all(abs(cols[i] - cols[j]) != j - i for i in range(r) for j in range(i + 1, r)):
+                total += 1
+    return total
+
+
+def test_nqueens_task_count_brute_force():
+    for n in range(1, 8):
+        assert oracle.nqueens(n)[1] == _partial_placements(n), n
+
+
+def test_nqueens_two_algorithms_agree():
+    for n in range(1, 12):
+        assert oracle.nqueens(n, "bitmask") == oracle.nqueens(n, "array"), n
+
+
+# --------------------------------------------------------------------------- hashed tree
+def test_uts_recursion_equals_bfs():
+    for seed, rc, m, thr in [(42, 2000, 5, oracle.UTS_THRESHOLD_Q0199), (1, 50, 3, 2 ** 62),
+                             (7, 10, 2, 2 ** 63 - 2 ** 60), (3, 100, 1, 2 ** 64 - 2 ** 58)]:
+        assert oracle.uts(seed, rc, m, thr) == oracle.uts(seed, rc, m, thr, algorithm="bfs")
+
+
+def test_uts_special_cases():
+    assert oracle.uts(42, 2000, 5, 0) == (2001, 2000)   # nobody below the root branches
+    assert oracle.uts(42, 0, 5, 2 ** 63) == (1, 1)       # a lone root is a leaf
+    assert oracle.uts(5, 1, 1, 0) == (2, 1)
+
+
+def test_uts_counting_identity():
+    # nodes = 1 + R + m * I and leaves = nodes - 1 - I, I = internal non-root nodes
+    # all subcritical (m * q < 1), so every tree is finite
+    for seed, rc, m, thr in [(42, 2000, 5, oracle.UTS_THRESHOLD_Q0199), (9, 300, 4, 2 ** 64 // 5),
+                             (11, 64, 3, 2 ** 62)]:
+        nodes, leaves = oracle.uts(seed, rc, m, thr)
+        assert (nodes - 1 - rc) % m == 0
+        internal = (nodes - 1 - rc) // m
+        assert leaves == nodes - 1 - internal
+
+
+def test_uts_branching_threshold_exact():
+    assert oracle.UTS_THRESHOLD_Q0199 == 3670902070668200771
+    assert oracle.UTS_THRESHOLD_Q0199 <= 0.199 * 2 ** 64 < oracle.UTS_THRESHOLD_Q0199 + 1 + 2 ** 12
+
+
+def test_uts_branching_frequency():
+    # a root with many children: the fraction of branching children estimates q
+    nodes, leaves = oracle.uts(123, 200000, 1, 2 ** 62)   # q = 1/4, m = 1 chains
+    # with m = 1, every non-root node except chain ends is internal: E[nodes-1] = R / (1 - q)
+    assert abs((nodes - 1) / 200000 - 4 / 3) < 0.02
+
+
+# --------------------------------------------------------------------------- sort
+def test_sort_is_sorted_permutation():
+    keys = inputs.keys_u32(1 << 16, seed=1)
+    out = oracle.sort_u32(keys)
+    assert np.all(out[1:] >= out[:-1])
+    ku, kc = np.unique(keys, return_counts=True)
+    ou, oc = np.unique(out, return_counts=True)
+    assert np.array_equal(ku, ou) and np.array_equal(kc, oc)
+    edge = np.array([5, 5, 0, 2 ** 32 - 1, 7, 0], dtype=np.uint32)
+    assert oracle.sort_u32(edge).tolist() == [0, 0, 5, 5, 7, 2 ** 32 - 1]
+
+
+# --------------------------------------------------------------------------- integrate
+def test_integrate_close_to_closed_form():
+    exact = 0.4 * math.atan(5.0)   # integral of 1/(1+25x^2) over [-1, 1]
+    v, t = oracle.integrate_thread(-1.0, 1.0, 1e-10)
+    assert abs(v - exact) < 1e-9 and t % 2 == 1
+    vb, tb = oracle.integrate_block(-1.0, 1.0, 1e-10, 256)
+    assert abs(vb - exact) < 1e-9 and tb % 2 == 1
+    # [0, 1] is half of the symmetric integral
+    v0, _ = oracle.integrate_thread(0.0, 1.0, 1e-10)
+    assert abs(v0 - exact / 2) < 1e-9
+
+
+def test_integrate_block_single_task_when_smooth():
+    # a tiny interval is accepted at once: one task, and the value is the Richardson step
+    vb, tb = oracle.integrate_block(0.0, 1e-3, 1e-6, 128)
+    assert tb == 1
+    assert abs(vb - math.atan(5e-3) / 5) < 1e-15
+
+
+# --------------------------------------------------------------------------- k-clique
+def _ek(sizes, k):
+    # elementary symmetric polynomial e_k
+    e = [1] + [0] * k
+    for s in sizes:
+        for j in range(k, 0, -1):
+            e[j] += e[j - 1] * s
+    return e[k]
+
+
+def test_kclique_brute_force_random():
+    for seed in range(4):
+        n, edges = inputs.random_graph(18, 0.55, seed)
+        for k in range(3, 7):
+            want = oracle.kclique_brute(n, edges, k)
+            assert oracle.kclique(n, edges, k, "degree") == want
+            assert oracle.kclique(n, edges, k, "id") == want
+
+
+def test_kclique_complete_graph():
+    n = 14
+    edges = np.array(list(combinations(range(n), 2)), dtype=np.int32)
+    for k in range(3, 9):
+        assert oracle.kclique(n, edges, k) == math.comb(n, k)
+
+
+def test_kclique_multipartite():
+    sizes = [3, 1, 4, 2, 5]
+    part = np.repeat(np.arange(len(sizes)), sizes)
+    n = len(part)
+    edges = np.array([(i, j) for i, j in combinations(range(n), 2) if part[i] != part[j]], dtype=np.int32)
+    for k in range(3, 6):
+        assert oracle.kclique(n, edges, k) == _ek(sizes, k)
+
+
+def test_kclique_triangles_trace():
+    n, edges = inputs.random_graph(120, 0.2, 11)
+    A = np.zeros((n, n), dtype=np.int64)
+    A[edges[:, 0], edges[:, 1]] = 1
+    A[edges[:, 1], edges[:, 0]] = 1
+    assert oracle.kclique(n, edges, 3) == int(np.trace(A @ A @ A)) // 6
+
+
+def test_kclique_per_edge_sums_and_small_rmat():
+    n, edges = inputs.rmat_graph(9, 16, seed=7)
+    for k in (3, 4, 5):
+        total, pe = oracle.kclique(n, edges, k, per_edge=True)
+        assert int(pe.sum()) == total
+        assert oracle.kclique(n, edges, k, "id") == total
+
+
+def test_orientation_is_a_dag_with_sorted_lists():
+    n, edges = inputs.rmat_graph(8, 8, seed=3)
+    off, adj = oracle.orient(n, edges)
+    deg = np.bincount(edges.ravel(), minlength=n)
+    assert off[-1] == len(edges)
+    for u in range(n):
+        out = adj[off[u]:off[u + 1]]
+        assert np.all(np.diff(out) > 0)
+        for v in out:
+            assert (deg[u], u) < (deg[v], v)
+
+
+# --------------------------------------------------------------------------- generators
+def test_rmat_generator_shape():
+    n, edges = inputs.rmat_graph(10, 16, seed=7)
+    assert n == 1024
+    assert np.all(edges[:, 0] < edges[:, 1])
+    key = edges[:, 0].astype(np.int64) * n + edges[:, 1]
+    assert np.all(np.diff(key) > 0)          # sorted, no duplicates
+    deg = np.bincount(edges.ravel(), minlength=n)
+    assert deg[0] == deg.max()               # a = 0.57 skews mass to vertex 0
+
+
+def test_keys_u32_low_bits():
+    k = inputs.keys_u32(4, seed=0)
+    want = [int(h, 16) & 0xFFFFFFFF for _, h in _read_golden("splitmix64_seed0.txt")]
+    assert k[:3].tolist() == want
