@@ -1,0 +1,211 @@
+/*
+ * gtap.h -- C ABI of a GPU-resident fork-join task runtime for GB300 (sm_103a).
+ *
+ * The runtime executes fine-grained fork-join task programs inside one
+ * persistent kernel: every warp (thread mode) or thread block (block mode)
+ * owns a deque of runnable task IDs, acquires work by batched pop and random
+ * work stealing, suspends a task at a join by storing its resume point in the
+ * task record, and re-enqueues it in place when its last child completes
+ * (paper Sec. 5.1; Algorithms 1 and 2).  Divergence-Aware Queueing (DAQ)
+ * gives each warp several queues and fills a warp batch from one queue
+ * (Sec. 4.2).  Task programs are built-in continuation state machines; they
+ * are selected by name with gtap_register_task.
+ *
+ * Conventions for every call:
+ *   - Every function returns a gtap_status; nothing throws or aborts the
+ *     process.  GTAP_OK is 0.
+ *   - Pointers documented as "device" must be device-accessible memory of
+ *     the current CUDA device (e.g. cudaMalloc or a torch CUDA tensor); all
+ *     others are host memory.  Device buffers passed in program arguments are
+ *     owned by the caller and must stay alive until gtap_wait returns.
+ *   - A context is used by one host thread at a time.
+ *
+ * Storage (Sec. 4: everything is preallocated before a run, no device-side
+ * allocation during it): gtap_init allocates the task-record pool, the
+ * deques and the control block with cudaMalloc (or carves them from a
+ * caller-provided device arena) and gtap_finalize releases them.
+ */
+#ifndef GTAP_H_
+#define GTAP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes.  Device-side failures (capacity exhaustion, Sec. 4: "aborts
+ * execution with a structured error report") are reported by gtap_wait and
+ * detailed by gtap_last_error. */
+typedef enum {
+    GTAP_OK = 0,
+    GTAP_ERR_INVALID_ARG = 1,     /* bad argument, unknown program name or handle */
+    GTAP_ERR_NO_MEMORY = 2,       /* host or device allocation failed at init */
+    GTAP_ERR_POOL_EXHAUSTED = 3,  /* task-record pool ran out during a run */
+    GTAP_ERR_DEQUE_OVERFLOW = 4,  /* a push found its deque full */
+    GTAP_ERR_LIST_OVERFLOW = 5,   /* a fixed-capacity output list (FMM interaction lists) overflowed */
+    GTAP_ERR_TIMEOUT = 6,         /* run deadline or gtap_wait timeout reached; the kernel was told to stop */
+    GTAP_ERR_CUDA = 7,            /* a CUDA runtime call failed */
+    GTAP_ERR_BUSY = 8,            /* a run is in flight (call gtap_wait first) */
+    GTAP_ERR_UNKNOWN_TASK = 9,    /* a task record carried an unregistered type */
+    GTAP_ERR_TASK_FAILED = 10,    /* a task program reported failure (e.g. scratch arena exhausted) */
+    GTAP_ERR_NOT_READY = 11       /* the requested result is not available yet */
+} gtap_status;
+
+typedef enum { GTAP_MODE_THREAD = 0, GTAP_MODE_BLOCK = 1 } gtap_mode;
+
+/* Steal policy bits (gtap_config.steal_policy). */
+#define GTAP_STEAL_FILL 0      /* steal whenever the warp batch is not full (Alg. 1) */
+#define GTAP_STEAL_EMPTY 1     /* steal only when the warp has no task at all */
+#define GTAP_STEAL_HALF 2      /* claim at most half of the victim's queue (else up to 32 - cnt) */
+
+/* Optional configuration; a zero field selects the default.  Pass NULL for
+ * all defaults. */
+typedef struct {
+    int blocks_per_sm;      /* persistent grid = blocks_per_sm x SM count (default: 4 thread mode, 2 block mode) */
+    int threads_per_block;  /* thread mode: 64..1024, multiple of 32 (default 256); block mode: 128 or 256 (default 256) */
+    int deque_capacity;     /* ring slots per queue, power of two (default 4096 thread mode, 1024 block mode) */
+    int steal_policy;       /* GTAP_STEAL_* bits (default GTAP_STEAL_FILL) */
+    int max_roots;          /* capacity of the root table (default 4096) */
+    int frame_bytes;        /* thread-mode task-record size, 64 or 128 (default 64) */
+    void* device_arena;     /* optional caller-owned device memory used for all runtime storage */
+    size_t arena_bytes;     /* its size; gtap_init fails with GTAP_ERR_NO_MEMORY if too small */
+    void* stream;           /* cudaStream_t for runs (default: the legacy default stream) */
+    uint64_t timeout_ns;    /* device-side run deadline (default 60 s); exceeded -> GTAP_ERR_TIMEOUT */
+    uint64_t seed;          /* victim-selection seed (default 0x5EED) */
+    size_t scratch_bytes;   /* device scratch arena for programs that need it (k-clique), default 0 */
+    int grid_blocks;        /* explicit persistent grid size (overrides blocks_per_sm x SM count), e.g. 1 */
+    int debug_checks;       /* 1: track every record's state (free / allocated / running) and report
+                               double allocation, double free or double execution as GTAP_ERR_TASK_FAILED */
+} gtap_config;
+
+/* Per-run statistics, summed over workers (gtap_get_stats). */
+typedef struct {
+    uint64_t tasks_executed;     /* task steps executed (a suspended task that resumes counts twice) */
+    uint64_t tasks_created;      /* tasks spawned in the run, roots included */
+    uint64_t steps;              /* scheduler iterations that executed at least one task */
+    uint64_t pops, popped;       /* successful pop claims and tasks they returned */
+    uint64_t steal_attempts, steals, stolen;
+    uint64_t idle_iterations;
+    uint64_t pushes, pushed;     /* push batches and tasks they published */
+    uint64_t frames_high_water;  /* fresh records ever taken from the pool (bump pointer) */
+    uint64_t scratch_used;       /* bytes taken from the scratch arena */
+    int n_workers;               /* warps (thread mode) or blocks (block mode) in the grid */
+    int grid_blocks, threads_per_block;
+    float kernel_ms;             /* duration of the last persistent launch (CUDA events) */
+} gtap_stats;
+
+/* Structured error report (Sec. 4: capacity exhaustion aborts with a report). */
+typedef struct {
+    int code;        /* gtap_status of the first device-side error, 0 if none */
+    int task_type;   /* type of the task that hit it, -1 if not task-specific */
+    int worker;      /* warp or block index */
+    int pad;
+    uint64_t detail; /* e.g. the capacity that was exceeded */
+} gtap_error_info;
+
+typedef struct gtap_ctx gtap_ctx;
+
+/* Create a context: mode, number of DAQ queues per warp (1..8; block mode
+ * requires 1, as the queue clause is not supported there, Sec. 4.3), and the
+ * size of the task-record pool in bytes.  All storage is allocated here.
+ * Errors: GTAP_ERR_INVALID_ARG, GTAP_ERR_NO_MEMORY, GTAP_ERR_CUDA. */
+gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, const gtap_config* cfg,
+                      gtap_ctx** out);
+
+/* Select a built-in task program by name and get its type ID for
+ * gtap_spawn_root.  Thread mode: "fib", "nqueens", "uts", "kclique",
+ * "integrate".  Block mode: "mergesort", "integrate_block", "fmm_dtt".
+ * Errors: GTAP_ERR_INVALID_ARG for an unknown name or the wrong mode. */
+gtap_status gtap_register_task(gtap_ctx* ctx, const char* program, int* out_type);
+
+/* Queue a root task for the next gtap_run: its arguments (the program's
+ * gtap_*_args struct) are copied now (firstprivate, Sec. 4.1).  queue
+ * selects the DAQ queue of the root.  Roots of one run are spread over the
+ * workers round-robin, so many instances of uneven size run in one launch.
+ * out_handle identifies the root for gtap_read_result.
+ * Errors: GTAP_ERR_INVALID_ARG (unregistered type, args too large, table full), GTAP_ERR_BUSY. */
+gtap_status gtap_spawn_root(gtap_ctx* ctx, int type, const void* args, size_t args_bytes, int queue,
+                            uint64_t* out_handle);
+
+/* Start one persistent-kernel run over the queued roots, asynchronously on
+ * the configured stream: a reset kernel re-zeroes deques, pool and control
+ * words and writes the root records, then the scheduler kernel runs until
+ * every root has completed (or an error/abort).  The queued roots stay
+ * queued, so calling gtap_run again re-runs the same roots.
+ * Errors: GTAP_ERR_INVALID_ARG (no roots), GTAP_ERR_BUSY, GTAP_ERR_CUDA. */
+gtap_status gtap_run(gtap_ctx* ctx);
+
+/* Wait for the run started by gtap_run, at most timeout_ms milliseconds
+ * (0 = the config's device deadline plus a margin).  Never hangs: on
+ * timeout it raises the device abort flag, waits for the kernel to drain and
+ * returns GTAP_ERR_TIMEOUT.  Returns the device-side error code if the run
+ * failed.  Results and statistics are read back here. */
+gtap_status gtap_wait(gtap_ctx* ctx, uint64_t timeout_ms);
+
+/* Copy the result of a completed root (bytes <= 16) into out (host).
+ * Errors: GTAP_ERR_INVALID_ARG (bad handle), GTAP_ERR_NOT_READY. */
+gtap_status gtap_read_result(gtap_ctx* ctx, uint64_t handle, void* out, size_t bytes);
+
+/* Statistics of the last completed run. */
+gtap_status gtap_get_stats(gtap_ctx* ctx, gtap_stats* out);
+
+/* Structured report of the last device-side error (code 0 if none). */
+gtap_status gtap_last_error(gtap_ctx* ctx, gtap_error_info* out);
+
+/* Forget the queued roots (the next gtap_spawn_root starts a new batch). */
+gtap_status gtap_clear_roots(gtap_ctx* ctx);
+
+/* Diagnostic snapshot of the device scheduler state after a run (for
+ * post-mortem of an error or timeout).  Fills up to n of: [0] roots
+ * remaining, [1] fresh-record bump pointer, [2] chunk-queue enqueue ticket,
+ * [3] chunk-queue dequeue ticket, [4] tasks left in all deques (sum of
+ * count), [5] queues with count > 0, [6] queue locks held, [7] largest count,
+ * [8] abort flag.  Returns GTAP_ERR_BUSY while a run is in flight. */
+gtap_status gtap_debug_snapshot(gtap_ctx* ctx, uint64_t* out, int n);
+
+/* Human-readable name of a status code (static storage). */
+const char* gtap_status_string(gtap_status s);
+
+/* Release every resource of the context (waits for an in-flight run first). */
+gtap_status gtap_finalize(gtap_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Built-in program arguments (passed to gtap_spawn_root).
+ * Routing ("route") selects the program's DAQ routing function; 0 sends
+ * every task to queue 0, which is the same as omitting the queue clause.
+ * Any routing gives the same result (the queue clause has no effect on
+ * program semantics, Sec. 4.2).
+ * ---------------------------------------------------------------------- */
+
+/* fib(n), no cutoff (Sec. 6.3).  Result: int64 fib(n).
+ * route 1: recursive calls -> q0, leaves (n < 2) -> q1, continuations -> q2 (mod n_queues). */
+typedef struct { int32_t n; int32_t route; } gtap_fib_args;
+
+/* N-Queens by bitmask backtracking, one task per placed row (Sec. 6.3).
+ * Result: uint64 solution count.  route 1: queue = depth mod n_queues. */
+typedef struct { int32_t n; int32_t route; } gtap_nqueens_args;
+
+/* Unbalanced hashed tree: root id splitmix64(seed), root_children children at
+ * the root, m children below iff splitmix64(v ^ 0xD1B54A32D192ED03) < threshold.
+ * Result: uint64 nodes in the high 32 bits, leaves in the low 32 bits.
+ * route 1: nodes with children -> q0, leaves -> q1, continuations -> q2. */
+typedef struct { uint64_t seed; uint64_t threshold; uint32_t root_children; uint32_t m; int32_t route; int32_t pad; } gtap_uts_args;
+
+/* Adaptive trapezoid integration of 1/(1+25x^2) over [a, b] (Program 1).
+ * Thread mode ("integrate") and block mode ("integrate_block").  Result: double. */
+typedef struct { double a; double b; double eps; } gtap_integrate_args;
+
+/* Block-mode mergesort (Cilksort with a forked parallel merge, Sec. 6.3) of
+ * n uint32 keys from src (device, read only) into dst (device); tmp (device,
+ * n keys) is scratch.  src may equal dst for an in-place sort.  Ranges of at
+ * most `leaf` keys (<= 4096) are sorted by one block; merges of at most
+ * `merge_cutoff` output keys are merged by one block, larger ones fork.
+ * Result: none (8 zero bytes). */
+typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; uint32_t leaf; uint32_t merge_cutoff; } gtap_mergesort_args;
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GTAP_H_ */

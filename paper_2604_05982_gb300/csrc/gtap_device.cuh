@@ -1,0 +1,999 @@
+// Device runtime: memory-ordering primitives, task-record pool, deques and the
+// persistent scheduler loops (thread mode and block mode).
+//
+// Sec. 5.1 of the paper describes the design this follows: one persistent
+// kernel, per-warp (thread mode) or per-block (block mode) ring-buffer deques
+// whose `head` and `count` live in global memory and are accessed through L2
+// while the owner's `tail` lives in shared memory; batched pop/steal claims by
+// CAS on `count` (Algorithm 2); one fence and one `count` increment per push
+// batch; suspension at a join with a waiting-child counter whose last
+// decrement re-enqueues the parent (Sec. 5.1.2).
+#pragma once
+#include <cstdint>
+#include "gtap_internal.h"
+#include "gtap.h"
+
+namespace gtap {
+
+// ---------------------------------------------------------------------------
+// Memory primitives.  Every cross-SM word is accessed through L2 (.cg loads,
+// atomics); publication uses release/acquire at GPU scope.
+__device__ __forceinline__ uint32_t ld_cg32(const void* p) { return __ldcg(reinterpret_cast<const unsigned int*>(p)); }
+__device__ __forceinline__ int ld_cg_i32(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ld_cg64(const void* p) {
+    return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+__device__ __forceinline__ void st_cg32(void* p, uint32_t v) { __stcg(reinterpret_cast<unsigned int*>(p), v); }
+__device__ __forceinline__ void st_cg64(void* p, unsigned long long v) {
+    __stcg(reinterpret_cast<unsigned long long*>(p), v);
+}
+
+__device__ __forceinline__ uint32_t atom_add_acqrel_u32(void* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int atom_cas_acq_i32(int* p, int cmp, int val) {
+    int old;
+    asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "l"(p), "r"(cmp), "r"(val) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long atom_cas_acq_u64(unsigned long long* p, unsigned long long cmp,
+                                                               unsigned long long val) {
+    unsigned long long old;
+    asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(val) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_release_i32(int* p, int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Copy a trivially copyable object through L2 in 16/8/4-byte pieces.
+template <class T>
+__device__ __forceinline__ T ld_obj(const void* src) {
+    static_assert(sizeof(T) % 4 == 0, "record fields must be 4-byte multiples");
+    T out;
+    if constexpr (sizeof(T) % 16 == 0) {
+        uint4 tmp[sizeof(T) / 16];
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 16); ++i) tmp[i] = __ldcg(reinterpret_cast<const uint4*>(src) + i);
+        memcpy(&out, tmp, sizeof(T));
+    } else if constexpr (sizeof(T) % 8 == 0) {
+        uint2 tmp[sizeof(T) / 8];
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 8); ++i) tmp[i] = __ldcg(reinterpret_cast<const uint2*>(src) + i);
+        memcpy(&out, tmp, sizeof(T));
+    } else {
+        unsigned int tmp[sizeof(T) / 4];
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 4); ++i) tmp[i] = __ldcg(reinterpret_cast<const unsigned int*>(src) + i);
+        memcpy(&out, tmp, sizeof(T));
+    }
+    return out;
+}
+template <class T>
+__device__ __forceinline__ void st_obj(void* dst, const T& v) {
+    static_assert(sizeof(T) % 4 == 0, "record fields must be 4-byte multiples");
+    if constexpr (sizeof(T) % 16 == 0) {
+        uint4 tmp[sizeof(T) / 16];
+        memcpy(tmp, &v, sizeof(T));
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 16); ++i) __stcg(reinterpret_cast<uint4*>(dst) + i, tmp[i]);
+    } else if constexpr (sizeof(T) % 8 == 0) {
+        uint2 tmp[sizeof(T) / 8];
+        memcpy(tmp, &v, sizeof(T));
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 8); ++i) __stcg(reinterpret_cast<uint2*>(dst) + i, tmp[i]);
+    } else {
+        unsigned int tmp[sizeof(T) / 4];
+        memcpy(tmp, &v, sizeof(T));
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 4); ++i) __stcg(reinterpret_cast<unsigned int*>(dst) + i, tmp[i]);
+    }
+}
+
+__device__ __forceinline__ char* frame_ptr(const KParams& P, uint32_t id) {
+    return P.frames + (uint64_t)id * P.frame_bytes;
+}
+
+// First error wins; every worker then drains (Sec. 4: structured error report).
+static __device__ __noinline__ void raise_error(const KParams& P, int code, int task_type, int worker, unsigned long long detail) {
+    if (atomicCAS(&P.ctl->err.code, 0, code) == 0) {
+        P.ctl->err.task_type = task_type;
+        P.ctl->err.worker = worker;
+        P.ctl->err.detail = detail;
+    }
+    __threadfence();
+    atomicExch(reinterpret_cast<unsigned long long*>(&P.ctl->abort_flag.v), 1ull);
+}
+
+// Debug event log: code:4 | lane:5 | worker:15 | iteration:24 | aux:16.
+__device__ __forceinline__ void dbg_log(const KParams& P, uint32_t id, unsigned code, int worker, uint32_t iter,
+                                        unsigned aux) {
+    if (P.flog == nullptr || id >= P.n_frames) return;
+    unsigned k = atomicAdd(&P.flogn[id], 1u);
+    unsigned long long ev = ((unsigned long long)code << 60) | ((unsigned long long)(threadIdx.x & 31) << 55) |
+                            ((unsigned long long)(worker & 0x7FFF) << 40) | ((unsigned long long)(iter & 0xFFFFFF) << 16) |
+                            (aux & 0xFFFF);
+    P.flog[(size_t)id * 8 + (k & 7)] = ev;
+}
+
+// Debug checks on record ownership (only when P.fstate is set).
+__device__ __forceinline__ void dbg_transition(const KParams& P, uint32_t id, unsigned from, unsigned to,
+                                               unsigned long long fault, int type, int worker) {
+    if (P.fstate == nullptr) return;
+    if (id >= P.n_frames) { raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, (DBG_BAD_ID << 32) | id); return; }
+    unsigned old = atomicCAS(&P.fstate[id], from, to);
+    if (old != from) raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, (fault << 32) | id);
+}
+
+__device__ __forceinline__ bool abort_requested(const KParams& P, bool check_host) {
+    if (ld_cg64(&P.ctl->abort_flag.v) != 0) return true;
+    // the host word lives in mapped host memory (a slow read): checked less often
+    if (check_host && P.host_abort != nullptr && *P.host_abort != 0) {
+        atomicExch(reinterpret_cast<unsigned long long*>(&P.ctl->abort_flag.v), 1ull);
+        return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Frame pool.  Free IDs are cached per worker in shared memory; surplus is
+// moved to / from a global bounded MPMC queue of 32-ID chunks (sequence-number
+// slots, after Vyukov's bounded queue); never-used IDs come from a bump
+// pointer.  All of it is warp-collective (called by one full warp).
+
+// Enqueue the 32 IDs my_id (one per lane) as one chunk.  The slot is claimed
+// with a fetch-and-add ticket, so contention never makes a push retry; the
+// queue has a slot for every chunk the pool can hold, so the ticket's slot is
+// free as soon as its previous occupant's dequeue has finished (a short,
+// bounded wait).  Returns false only if that wait gives up (an invariant
+// violation, reported as an error).
+__device__ __forceinline__ bool cq_push(const KParams& P, uint32_t my_id) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long slot = 0;
+    int ok = 0;
+    if (lane == 0) {
+        slot = atomicAdd(&P.ctl->cq_enq.v, 1ull);
+        for (int it = 0; it < (1 << 20); ++it) {
+            if (ld_acquire_u64(&P.cq_seq[slot & P.ncq_mask]) == slot) { ok = 1; break; }
+            __nanosleep(64);
+        }
+        if (!ok) raise_error(P, GTAP_ERR_TASK_FAILED, -1, -1, slot);
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    __stcg(&P.cq_ids[(slot & P.ncq_mask) * kChunk + lane], my_id);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release_u64(&P.cq_seq[slot & P.ncq_mask], slot + 1);
+    return true;
+}
+
+// Dequeue one chunk; lane i receives ID i.  Returns false if the queue is empty.
+__device__ __forceinline__ bool cq_pop(const KParams& P, uint32_t* my_id) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long slot = 0;
+    int ok = 0;
+    if (lane == 0) {
+        unsigned long long* deq = &P.ctl->cq_deq.v;
+        unsigned long long pos = ld_cg64(deq);
+        for (int it = 0; it < 1024; ++it) {
+            unsigned long long seq = ld_acquire_u64(&P.cq_seq[pos & P.ncq_mask]);
+            long long dif = (long long)(seq - (pos + 1));
+            if (dif == 0) {
+                unsigned long long got = atomicCAS(deq, pos, pos + 1);
+                if (got == pos) { ok = 1; slot = pos; break; }
+                pos = got;
+            } else if (dif < 0) {
+                break;  // empty
+            } else {
+                pos = ld_cg64(deq);
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    *my_id = __ldcg(&P.cq_ids[(slot & P.ncq_mask) * kChunk + lane]);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release_u64(&P.cq_seq[slot & P.ncq_mask], slot + P.ncq_mask + 1);
+    return true;
+}
+
+// Bring the local free stack up to `need` IDs (warp-collective).  Returns the
+// new top; less than `need` only when the pool is exhausted.
+__device__ __forceinline__ int pool_refill(const KParams& P, uint32_t* fstack, int ftop, int need) {
+    const int lane = threadIdx.x & 31;
+    while (ftop < need) {
+        uint32_t id;
+        if (cq_pop(P, &id)) {
+            fstack[ftop + lane] = id;
+            ftop += kChunk;
+            continue;
+        }
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(&P.ctl->bump.v, (unsigned long long)kChunk);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= P.n_frames) break;
+        unsigned long long avail = P.n_frames - b;
+        int got = avail < (unsigned long long)kChunk ? (int)avail : kChunk;
+        if (lane < got) fstack[ftop + lane] = (uint32_t)(b + lane);
+        ftop += got;
+        if (got < kChunk) break;
+    }
+    __syncwarp();
+    return ftop;
+}
+
+// Move chunks beyond `high` back to the global queue (warp-collective).
+__device__ __forceinline__ int pool_spill(const KParams& P, uint32_t* fstack, int ftop, int high) {
+    const int lane = threadIdx.x & 31;
+    while (ftop - kChunk >= high) {
+        __syncwarp();
+        uint32_t id = fstack[ftop - kChunk + lane];
+        __syncwarp();
+        if (!cq_push(P, id)) break;
+        ftop -= kChunk;
+    }
+    return ftop;
+}
+
+// ---------------------------------------------------------------------------
+// Per-warp shared-memory layout (thread mode).
+struct WarpSh {
+    int* ctrl;          // [0] ftop  [1] nfreed  [2] nstaged  [3] error
+    int* cls_count;     // [kMaxQueues]
+    uint32_t* tail;     // [kMaxQueues] owner tails (Sec. 5.1.3: tail kept in shared memory)
+    int* push_off;      // [kMaxQueues]
+    uint32_t* retained; // [32]
+    uint32_t* freed;    // [32]
+    uint32_t* fstack;   // [fcap]
+    uint32_t* staged_id;// [scap]
+    uint8_t* staged_q;  // [scap]
+    int fcap, scap;
+};
+
+__device__ __forceinline__ WarpSh carve_warp(char* base, int maxspawn) {
+    WarpSh w;
+    w.fcap = thread_fcap(maxspawn);
+    w.scap = thread_scap(maxspawn);
+    int* ints = reinterpret_cast<int*>(base);
+    w.ctrl = ints;
+    w.cls_count = ints + 8;
+    w.tail = reinterpret_cast<uint32_t*>(ints + 16);
+    w.push_off = ints + 24;
+    w.retained = reinterpret_cast<uint32_t*>(base + 128);
+    w.freed = reinterpret_cast<uint32_t*>(base + 256);
+    w.fstack = reinterpret_cast<uint32_t*>(base + 384);
+    w.staged_id = w.fstack + w.fcap;
+    w.staged_q = reinterpret_cast<uint8_t*>(w.staged_id + w.scap);
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// Thread-mode task context: what a task program sees while one lane runs one
+// step of one task (Sec. 4.2: one task per CUDA thread).
+struct TaskCtx {
+    const KParams& P;
+    const WarpSh& ws;
+    uint32_t self;
+    FrameHdr h;
+    char* frame;
+    int worker;
+    int nspawned;
+    bool freed_self;
+    bool staged_self = false;
+    uint32_t iter = 0;
+
+    __device__ TaskCtx(const KParams& p, const WarpSh& w, uint32_t id, int wk)
+        : P(p), ws(w), self(id), frame(frame_ptr(p, id)), worker(wk), nspawned(0), freed_self(false) {
+        h = ld_obj<FrameHdr>(frame);
+    }
+    __device__ int type() const { return (int)(h.w0 & 0xFF); }
+    __device__ int pc() const { return (int)((h.w0 >> 8) & 0xFF); }
+    template <class T> __device__ T* payload() const { return reinterpret_cast<T*>(frame + kHdrBytes); }
+    template <class T> __device__ T load() const { return ld_obj<T>(frame + kHdrBytes); }
+
+    __device__ void fail(int code, unsigned long long detail) { raise_error(P, code, type(), worker, detail); }
+
+    __device__ uint32_t alloc() {
+        int t = atomicSub(&ws.ctrl[0], 1) - 1;
+        if (t < 0) return kNoTask;
+        return ws.fstack[t];
+    }
+    __device__ void stage(uint32_t id, int q) {
+        if (P.fstate != nullptr) {
+            // debug: a record is queued only from "allocated" (1), or from "running" (2) by itself
+            unsigned old = atomicCAS(&P.fstate[id], 1u, 3u);
+            if (old != 1u) {
+                if (id == self && old == 2u && atomicCAS(&P.fstate[id], 2u, 3u) == 2u) staged_self = true;
+                else raise_error(P, GTAP_ERR_TASK_FAILED, (int)(200 + old * 16 + (id == self ? 1 : 0) + (id == h.parent ? 2 : 0)), worker, (5ull << 32) | id);
+            }
+        }
+        dbg_log(P, id, 2, worker, iter, id == self ? 1u : (id == h.parent ? 2u : 0u));
+        q = (P.n_queues > 1) ? (int)((unsigned)q % P.n_queues) : 0;
+        int p = atomicAdd(&ws.ctrl[2], 1);
+        if (p >= ws.scap) { fail(GTAP_ERR_DEQUE_OVERFLOW, (unsigned long long)ws.scap); return; }
+        ws.staged_id[p] = id;
+        ws.staged_q[p] = (uint8_t)q;
+        if (P.n_queues > 1) atomicAdd(&ws.cls_count[q], 1);
+    }
+
+    // Fork: create a child record (arguments copied now, Sec. 4.1) and stage it.
+    // slot8 = byte offset / 8 of the parent-record word that receives the result.
+    template <class A>
+    __device__ void spawn(int type, uint32_t slot8, int q, const A& a, uint32_t flags = 0, uint32_t aux = 0) {
+        static_assert(sizeof(A) % 4 == 0, "args must be 4-byte multiples");
+        uint32_t id = alloc();
+        if (id == kNoTask) { fail(GTAP_ERR_POOL_EXHAUSTED, P.n_frames); return; }
+        if (kHdrBytes + sizeof(A) > P.frame_bytes) { fail(GTAP_ERR_INVALID_ARG, sizeof(A)); return; }
+        dbg_transition(P, id, 0u, 1u, DBG_DOUBLE_ALLOC, type, worker);
+        dbg_log(P, id, 1, worker, iter, self & 0xFFFF);
+        char* f = frame_ptr(P, id);
+        FrameHdr ch;
+        ch.w0 = (uint32_t)type | (flags << 16);
+        ch.pending = 0;
+        ch.parent = self;
+        ch.w3 = (slot8 & 0xFFFFu) | (aux << 16);
+        st_obj(f, ch);
+        st_obj(f + kHdrBytes, a);
+        stage(id, q);
+        ++nspawned;
+    }
+
+    // Join (taskwait): wait for the children spawned in this step, then resume
+    // at pc_next on queue q_cont (the continuation is routed like a new task,
+    // Sec. 5.1.2).  The waiting-child count is stored before any child is
+    // published (children are published only after the step), so no
+    // child can decrement it early.
+    __device__ void join(int pc_next, int q_cont) {
+        uint32_t w0 = (h.w0 & ~0xFF00u) | ((uint32_t)pc_next << 8);
+        uint32_t pend = (uint32_t)nspawned | ((uint32_t)((P.n_queues > 1) ? ((unsigned)q_cont % P.n_queues) : 0) << 24);
+        uint2 v = make_uint2(w0, pend);
+        __stcg(reinterpret_cast<uint2*>(frame), v);
+        dbg_log(P, self, 11, worker, iter, (unsigned)nspawned | ((unsigned)pc_next << 8));
+        h.w0 = w0;
+        if (nspawned == 0) stage(self, q_cont);
+    }
+
+    // Complete: deliver the result to the parent's slot (store, or atomic add
+    // for accumulating programs), then decrement its waiting-child counter
+    // with acq_rel ordering; the child that brings it to zero re-enqueues the
+    // parent (Sec. 5.1.2).  The record is then freed.
+    __device__ void ret(unsigned long long v) {
+        const uint32_t parent = h.parent;
+        const uint32_t slot = h.w3 & 0xFFFFu;
+        const uint32_t flags = (h.w0 >> 16) & 0xFFu;
+        if (parent & kRootBit) {
+            RootEntry* r = &P.roots[parent & ~kRootBit];
+            if (flags & kFlagAccumulate) atomicAdd(&r->result[slot & 1], v);
+            else st_cg64(&r->result[slot & 1], v);
+            __threadfence();
+            atomicExch(&r->done, 1u);
+            atomicAdd(&P.ctl->roots_remaining.v, ~0ull);
+        } else {
+            char* pf = frame_ptr(P, parent);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(pf + slot * 8);
+            if (flags & kFlagAccumulate) { if (v) atomicAdd(dst, v); }
+            else st_cg64(dst, v);
+            uint32_t old = atom_add_acqrel_u32(pf + 4, 0xFFFFFFFFu);
+            dbg_log(P, parent, 10, worker, iter, (old & 0xFF) | ((self & 0xFF) << 8));
+            if ((old & 0xFFFFFFu) == 1u) stage(parent, (int)(old >> 24));
+        }
+        dbg_log(P, self, 5, worker, iter, 0);
+        dbg_transition(P, self, 2u, 0u, DBG_DOUBLE_FREE, type(), worker);
+        int p = atomicAdd(&ws.ctrl[1], 1);
+        ws.freed[p] = self;
+        freed_self = true;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Thread-mode scheduler loop (Algorithm 1), one instance per warp.
+// Dispatch is a functor: Dispatch::run(TaskCtx&) executes one step.
+template <class Dispatch>
+__device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
+    const int lane = threadIdx.x & 31;
+    const int wid = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    const int Q = (int)P.n_queues;
+    const uint32_t cap_mask = P.ring_mask;
+    WarpSh ws = carve_warp(smem_warp, (int)P.maxspawn);
+
+    QState* myq = P.qs + (size_t)wid * Q;
+    uint32_t* myring = P.rings + (size_t)wid * Q * (cap_mask + 1);
+    if (lane < 8) {
+        ws.cls_count[lane] = 0;
+        ws.push_off[lane] = 0;
+        ws.tail[lane] = (lane < Q) ? __ldcg(&myq[lane].tail0) : 0u;
+    }
+    if (lane == 0) { ws.ctrl[0] = 0; ws.ctrl[1] = 0; ws.ctrl[2] = 0; ws.ctrl[3] = 0; }
+    __syncwarp();
+
+    unsigned long long st_tasks = 0, st_steps = 0, st_pops = 0, st_popped = 0, st_sa = 0, st_steals = 0,
+                       st_stolen = 0, st_idle = 0, st_pushes = 0, st_pushed = 0, st_spawned = 0;
+    uint64_t rng = P.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(wid + 1));
+    const uint64_t t_start = global_ns();
+    const uint64_t deadline = t_start + P.timeout_ns;
+    uint32_t tid = kNoTask;  // this lane's task (valid for lane < cnt)
+    int src = 0;             // debug: where tid came from (0 retained, 1 popped, 2 stolen)
+    int cnt = 0;             // warp-uniform: lanes holding a task
+    int cls = 0;             // warp-uniform: DAQ queue of the current batch
+    int backoff = 32;
+    int ftop = 0;
+    const int fhigh = 32 * (int)P.maxspawn + 2 * kChunk;
+
+    for (uint32_t iter = 0;; ++iter) {
+        if ((iter & 15u) == 0u) {
+            int ab = 0;
+            if (lane == 0) ab = abort_requested(P, (iter & 255u) == 0u) ? 1 : 0;
+            if (__shfl_sync(0xffffffffu, ab, 0)) break;
+        }
+        // ---- PopBatch (Algorithm 2) from the own queue: the retained class, else the fullest (DAQ).
+        if (cnt < 32) {
+            int c = (lane < Q) ? ld_cg_i32(&myq[lane].count) : -1;
+            int q = cls;
+            if (cnt == 0) {
+                // fullest queue; ties -> lowest index
+                int best = c, bq = lane;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    int oc = __shfl_down_sync(0xffffffffu, best, o);
+                    int oq = __shfl_down_sync(0xffffffffu, bq, o);
+                    if (oc > best || (oc == best && oq < bq)) { best = oc; bq = oq; }
+                }
+                q = __shfl_sync(0xffffffffu, bq, 0);
+            }
+            int cq = __shfl_sync(0xffffffffu, c, q);
+            if (cq > 0) {
+                int claim = 0;
+                if (lane == 0) {
+                    int old = cq;
+                    for (int it = 0; it < 64 && old > 0; ++it) {
+                        int want = min(32 - cnt, old);
+                        int got = atom_cas_acq_i32(&myq[q].count, old, old - want);
+                        if (got == old) { claim = want; break; }
+                        old = got;
+                    }
+                }
+                claim = __shfl_sync(0xffffffffu, claim, 0);
+                if (claim > 0) {
+                    uint32_t t = ws.tail[q] - (uint32_t)claim;
+                    if (lane >= cnt && lane < cnt + claim) {
+                        uint32_t* slot = &myring[(size_t)q * (cap_mask + 1) + ((t + (uint32_t)(lane - cnt)) & cap_mask)];
+                        tid = __ldcg(slot);
+                        src = 1;
+                        dbg_log(P, tid, 7, wid, iter, (t + (uint32_t)(lane - cnt)) & 0xFFFF);
+                        if (P.fstate != nullptr) {
+                            uint32_t was = atomicExch(slot, kNoTask);
+                            if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 1, wid, (DBG_BAD_ID << 32) | was);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) ws.tail[q] = t;
+                    __syncwarp();
+                    cnt += claim;
+                    cls = q;
+                    ++st_pops;
+                    st_popped += claim;
+                }
+            }
+        }
+        // ---- StealBatch from a random victim.
+        const bool want_steal = (P.steal_policy & GTAP_STEAL_EMPTY) ? (cnt == 0) : (cnt < 32);
+        if (want_steal && P.n_workers > 1) {
+            ++st_sa;
+            rng ^= rng >> 12; rng ^= rng << 25; rng ^= rng >> 27;
+            uint32_t r = (uint32_t)((rng * 2685821657736338717ull) >> 32);
+            int victim = (int)(((unsigned long long)r * (P.n_workers - 1)) >> 32);
+            if (victim >= wid) ++victim;
+            QState* vq = P.qs + (size_t)victim * Q;
+            int c = (lane < Q) ? ld_cg_i32(&vq[lane].count) : -1;
+            int q = cls;
+            if (cnt == 0) {
+                int best = c, bq = lane;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    int oc = __shfl_down_sync(0xffffffffu, best, o);
+                    int oq = __shfl_down_sync(0xffffffffu, bq, o);
+                    if (oc > best || (oc == best && oq < bq)) { best = oc; bq = oq; }
+                }
+                q = __shfl_sync(0xffffffffu, bq, 0);
+            }
+            int cv = __shfl_sync(0xffffffffu, c, q);
+            if (cv > 0) {
+                int claim = 0;
+                uint32_t h = 0;
+                if (lane == 0) {
+                    if (atom_cas_acq_i32(&vq[q].lock, 0, 1) == 0) {  // try-lock: never wait on a thief
+                        int old = ld_cg_i32(&vq[q].count);
+                        for (int it = 0; it < 64 && old > 0; ++it) {
+                            int want = min(32 - cnt, old);
+                            if (P.steal_policy & GTAP_STEAL_HALF) want = min(want, (old + 1) >> 1);
+                            int got = atom_cas_acq_i32(&vq[q].count, old, old - want);
+                            if (got == old) { claim = want; break; }
+                            old = got;
+                        }
+                        h = __ldcg(&vq[q].head);
+                        if (claim == 0) st_release_i32(&vq[q].lock, 0);
+                    }
+                }
+                claim = __shfl_sync(0xffffffffu, claim, 0);
+                if (claim > 0) {
+                    h = __shfl_sync(0xffffffffu, h, 0);
+                    const uint32_t* vring = P.rings + ((size_t)victim * Q + q) * (cap_mask + 1);
+                    if (lane >= cnt && lane < cnt + claim) {
+                        uint32_t* slot = const_cast<uint32_t*>(&vring[(h + (uint32_t)(lane - cnt)) & cap_mask]);
+                        tid = __ldcg(slot);
+                        src = 2;
+                        dbg_log(P, tid, 8, wid, iter, (unsigned)victim & 0xFFFF);
+                        if (P.fstate != nullptr) {
+                            uint32_t was = atomicExch(slot, kNoTask);
+                            if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 2, wid, (DBG_BAD_ID << 32) | was);
+                        }
+                    }
+                    __threadfence();
+                    __syncwarp();
+                    // advance head only after the claimed IDs are read (wrap-around safety, Sec. 5.1.3)
+                    if (lane == 0) {
+                        __stcg(&vq[q].head, h + (uint32_t)claim);
+                        st_release_i32(&vq[q].lock, 0);
+                    }
+                    cnt += claim;
+                    cls = q;
+                    ++st_steals;
+                    st_stolen += claim;
+                }
+            }
+        }
+        // ---- Nothing to run: termination test (all roots complete), deadline, backoff.
+        if (cnt == 0) {
+            ++st_idle;
+            int stop = 0;
+            if (lane == 0) {
+                if (ld_cg64(&P.ctl->roots_remaining.v) == 0ull) stop = 1;
+                else if (abort_requested(P, (st_idle & 31ull) == 1ull)) stop = 1;
+                else if (global_ns() > deadline) { raise_error(P, GTAP_ERR_TIMEOUT, -1, wid, P.timeout_ns); stop = 1; }
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) break;
+            __nanosleep(backoff);
+            backoff = min(backoff * 2, 2048);
+            continue;
+        }
+        backoff = 32;
+
+        // ---- Ensure the free stack can serve every spawn of this step.
+        ftop = pool_refill(P, ws.fstack, ftop, cnt * (int)P.maxspawn);
+        if (lane == 0) { ws.ctrl[0] = ftop; ws.ctrl[1] = 0; ws.ctrl[2] = 0; }
+        if (lane < 8) ws.cls_count[lane] = 0;
+        __syncwarp();
+
+        // ---- Execute: lanes [0, cnt) run one step of their task.
+        int spawned = 0;
+        if (lane < cnt) {
+            if (P.fstate != nullptr) {
+                unsigned old = (tid < P.n_frames) ? atomicCAS(&P.fstate[tid], 3u, 2u) : 99u;
+                if (old != 3u) raise_error(P, GTAP_ERR_TASK_FAILED, (int)(old * 16 + src), wid, (DBG_EXEC_NOT_ALLOCATED << 32) | tid);
+            }
+            TaskCtx c(P, ws, tid, wid);
+            c.iter = iter;
+            dbg_log(P, tid, 3, wid, iter, (unsigned)c.pc() | ((unsigned)src << 8));
+            Dispatch::run(c);
+            spawned = c.nspawned;
+            if (!c.freed_self) dbg_log(P, tid, 4, wid, iter, 0);
+            if (!c.freed_self && !c.staged_self) dbg_transition(P, tid, 2u, 1u, DBG_EXEC_NOT_ALLOCATED, c.type(), wid);
+        }
+        __syncwarp();
+        st_spawned += (unsigned)__reduce_add_sync(0xffffffffu, (unsigned)spawned);
+        st_tasks += cnt;
+        ++st_steps;
+
+        // ---- Return freed records to the local stack; spill the surplus.
+        {
+            int top = max(ws.ctrl[0], 0);
+            int nf = ws.ctrl[1];
+            __syncwarp();
+            // the cache never exceeds its capacity (a spill that could not run leaves the surplus out)
+            nf = min(nf, ws.fcap - top);
+            if (lane < nf) ws.fstack[top + lane] = ws.freed[lane];
+            __syncwarp();
+            ftop = pool_spill(P, ws.fstack, top + nf, fhigh);
+        }
+
+        // ---- Retain up to 32 staged tasks of one queue class; push the rest (PushBatch).
+        const int nst = ws.ctrl[2];
+        cnt = 0;
+        if (nst > 0) {
+            int qstar = 0, nq_star = nst;
+            if (Q > 1) {
+                int c = (lane < Q) ? ws.cls_count[lane] : -1;
+                int best = c, bq = lane;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    int oc = __shfl_down_sync(0xffffffffu, best, o);
+                    int oq = __shfl_down_sync(0xffffffffu, bq, o);
+                    if (oc > best || (oc == best && oq < bq)) { best = oc; bq = oq; }
+                }
+                qstar = __shfl_sync(0xffffffffu, bq, 0);
+                nq_star = __shfl_sync(0xffffffffu, best, 0);
+            }
+            const int nkeep = min(32, nq_star);
+            // capacity check per destination queue: uses head/tail, not count (Sec. 5.1.3)
+            int overflow = 0;
+            if (lane < Q) {
+                int npush = ((Q > 1) ? ws.cls_count[lane] : nst) - (lane == qstar ? nkeep : 0);
+                if (npush > 0) {
+                    uint32_t hd = __ldcg(&myq[lane].head);
+                    if (ws.tail[lane] - hd + (uint32_t)npush > cap_mask + 1) overflow = 1;
+                }
+                ws.push_off[lane] = 0;
+            }
+            if (__any_sync(0xffffffffu, overflow)) {
+                if (lane == 0) raise_error(P, GTAP_ERR_DEQUE_OVERFLOW, -1, wid, cap_mask + 1);
+                break;
+            }
+            __syncwarp();
+            int kept = 0;
+            for (int base = 0; base < nst; base += 32) {
+                const int i = base + lane;
+                const bool valid = i < nst;
+                uint32_t id = valid ? ws.staged_id[i] : kNoTask;
+                int q = valid ? (int)ws.staged_q[i] : 0;
+                const bool cand = valid && q == qstar;
+                const uint32_t km = __ballot_sync(0xffffffffu, cand);
+                const int rk = __popc(km & lanemask_lt());
+                const bool keep = cand && (kept + rk) < nkeep;
+                if (keep) { ws.retained[kept + rk] = id; dbg_log(P, id, 9, wid, iter, (unsigned)(kept + rk)); }
+                kept = min(nkeep, kept + __popc(km));
+                const bool push = valid && !keep;
+                const uint32_t key = push ? (uint32_t)q : (0x100u + (uint32_t)lane);
+                const uint32_t grp = __match_any_sync(0xffffffffu, key);
+                const int prk = __popc(grp & lanemask_lt());
+                int off = 0;
+                if (push) off = ws.push_off[q];
+                __syncwarp();
+                if (push) {
+                    uint32_t pos = ws.tail[q] + (uint32_t)(off + prk);
+                    __stcg(&myring[(size_t)q * (cap_mask + 1) + (pos & cap_mask)], id);
+                    dbg_log(P, id, 6, wid, iter, pos & 0xFFFF);
+                    if (prk == 0) ws.push_off[q] = off + __popc(grp);
+                }
+                __syncwarp();
+            }
+            // one fence, then one count increment per destination queue (PushBatch)
+            __threadfence();
+            __syncwarp();
+            if (lane < Q) {
+                int np = ws.push_off[lane];
+                if (np > 0) {
+                    ws.tail[lane] += (uint32_t)np;
+                    atomicAdd(&myq[lane].count, np);
+                }
+            }
+            if (lane == 0) {
+                int tot = 0;
+                for (int q = 0; q < Q; ++q) tot += ws.push_off[q];
+                if (tot > 0) { ++st_pushes; st_pushed += tot; }
+            }
+            __syncwarp();
+            if (lane < nkeep) { tid = ws.retained[lane]; src = 0; }
+            cnt = nkeep;
+            cls = qstar;
+            __syncwarp();
+        }
+    }
+
+    // Give cached frames back so a later run or another worker could use them (best effort).
+    if (lane == 0) {
+        WorkerStats s;
+        s.tasks = st_tasks; s.steps = st_steps; s.pops = st_pops; s.popped = st_popped;
+        s.steal_attempts = st_sa; s.steals = st_steals; s.stolen = st_stolen; s.idle = st_idle;
+        s.pushes = st_pushes; s.pushed = st_pushed; s.spawned = st_spawned;
+        for (int i = 0; i < 5; ++i) s.pad[i] = 0;
+        P.stats[wid] = s;
+    }
+}
+
+
+// ===========================================================================
+// Block mode (Sec. 4.3, Sec. 5.1.3 "Block Mode"): one deque per block, a
+// leader acquires at most one task by single-task pop or steal, and the whole
+// block executes it.  The deque uses the same count-claim protocol as thread
+// mode with claims of one entry.
+struct BlockSh {
+    int* ctrl;          // [0] ftop [2] nstaged [3] state (0 idle, 1 task, 2 exit) [4] join pc+1 [5] completed
+    uint32_t* misc;     // [0] current task [1] retained task [2] own tail
+    FrameHdr* hdr;      // header of the current task
+    uint32_t* fstack;   // [fcap]
+    uint32_t* staged_id;// [scap]
+    char* prog;         // program shared area
+    int fcap, scap;
+};
+
+__device__ __forceinline__ BlockSh carve_block(char* base, int step_max) {
+    BlockSh b;
+    b.fcap = block_fcap(step_max);
+    b.scap = block_scap(step_max);
+    b.ctrl = reinterpret_cast<int*>(base);
+    b.misc = reinterpret_cast<uint32_t*>(base + 32);
+    b.hdr = reinterpret_cast<FrameHdr*>(base + 64);
+    b.fstack = reinterpret_cast<uint32_t*>(base + 128);
+    b.staged_id = b.fstack + b.fcap;
+    b.prog = reinterpret_cast<char*>(b.staged_id + b.scap);
+    return b;
+}
+
+// Block-mode task context: all threads of the block run the same step.
+struct BTaskCtx {
+    const KParams& P;
+    const BlockSh& bs;
+    uint32_t self;
+    FrameHdr h;
+    char* frame;
+    int worker;
+
+    __device__ BTaskCtx(const KParams& p, const BlockSh& b, int wk)
+        : P(p), bs(b), self(b.misc[0]), h(*b.hdr), frame(frame_ptr(p, b.misc[0])), worker(wk) {}
+    __device__ int type() const { return (int)(h.w0 & 0xFF); }
+    __device__ int pc() const { return (int)((h.w0 >> 8) & 0xFF); }
+    template <class T> __device__ T load() const { return ld_obj<T>(frame + kHdrBytes); }
+    template <class T> __device__ T* prog_smem() const { return reinterpret_cast<T*>(bs.prog); }
+    __device__ void fail(int code, unsigned long long detail) { raise_error(P, code, type(), worker, detail); }
+
+    // Per-thread fork (Sec. 4.3: the spawn is performed by each thread that reaches it).
+    template <class A>
+    __device__ void spawn(int type, uint32_t slot8, const A& a) {
+        int t = atomicSub(&bs.ctrl[0], 1) - 1;
+        if (t < 0) { fail(GTAP_ERR_POOL_EXHAUSTED, P.n_frames); return; }
+        uint32_t id = bs.fstack[t];
+        dbg_transition(P, id, 0u, 1u, DBG_DOUBLE_ALLOC, type, worker);
+        char* f = frame_ptr(P, id);
+        FrameHdr ch;
+        ch.w0 = (uint32_t)type;
+        ch.pending = 0;
+        ch.parent = self;
+        ch.w3 = (slot8 & 0xFFFFu) | ((uint32_t)threadIdx.x << 16);  // aux = spawning thread
+        st_obj(f, ch);
+        st_obj(f + kHdrBytes, a);
+        int p = atomicAdd(&bs.ctrl[2], 1);
+        if (p >= bs.scap - 1) { fail(GTAP_ERR_DEQUE_OVERFLOW, (unsigned long long)bs.scap); return; }
+        bs.staged_id[p] = id;
+    }
+    // Block-collective join (taskwait must be reached by all threads, Sec. 4.3).
+    __device__ void join(int pc_next) {
+        if (threadIdx.x == 0) bs.ctrl[4] = pc_next + 1;
+    }
+    // Block-collective completion with per-thread return values: thread i of
+    // the parent observes this task's thread i, and only on the thread that
+    // executed the spawn (Sec. 4.3, "Values across spawn and join").
+    __device__ void ret(unsigned long long v) {
+        const uint32_t parent = h.parent;
+        const uint32_t slot = h.w3 & 0xFFFFu;
+        const uint32_t spawner = h.w3 >> 16;
+        if (parent & kRootBit) {
+            if (threadIdx.x == 0) st_cg64(&P.roots[parent & ~kRootBit].result[0], v);
+        } else if (threadIdx.x == spawner && slot != 0) {
+            st_cg64(frame_ptr(P, parent) + (size_t)slot * 8 + (size_t)spawner * 8, v);
+        }
+        __threadfence();
+        if (threadIdx.x == 0) bs.ctrl[5] = 1;
+    }
+    __device__ void ret_void() {
+        if (threadIdx.x == 0) bs.ctrl[5] = 1;
+    }
+};
+
+template <class Dispatch>
+__device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+    const int bid = (int)blockIdx.x;
+    const uint32_t cap_mask = P.ring_mask;
+    BlockSh bs = carve_block(smem, (int)P.maxspawn);
+    QState* myq = P.qs + bid;
+    uint32_t* myring = P.rings + (size_t)bid * (cap_mask + 1);
+
+    if (t == 0) {
+        for (int i = 0; i < 8; ++i) bs.ctrl[i] = 0;
+        bs.misc[0] = kNoTask;
+        bs.misc[1] = kNoTask;
+        bs.misc[2] = __ldcg(&myq->tail0);
+    }
+    __syncthreads();
+
+    unsigned long long st_tasks = 0, st_pops = 0, st_sa = 0, st_steals = 0, st_idle = 0, st_pushes = 0, st_pushed = 0,
+                       st_spawned = 0;
+    uint64_t rng = P.seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(bid + 1));
+    const uint64_t deadline = global_ns() + P.timeout_ns;
+    int backoff = 32;
+    int ftop = 0;
+    const int fhigh = (int)P.maxspawn + 2 * kChunk;
+
+    for (uint32_t iter = 0;; ++iter) {
+        if (warp == 0) {
+            uint32_t task = kNoTask;
+            int state = 0;
+            if (lane == 0) {
+                if ((iter & 15u) == 0u && abort_requested(P, (iter & 255u) == 0u)) {
+                    state = 2;
+                } else if (bs.misc[1] != kNoTask) {
+                    task = bs.misc[1];
+                    bs.misc[1] = kNoTask;
+                } else {
+                    // single-task pop from the owner end
+                    int old = ld_cg_i32(&myq->count);
+                    for (int it = 0; it < 64 && old > 0; ++it) {
+                        int got = atom_cas_acq_i32(&myq->count, old, old - 1);
+                        if (got == old) {
+                            uint32_t tl = bs.misc[2] - 1u;
+                            bs.misc[2] = tl;
+                            task = __ldcg(&myring[tl & cap_mask]);
+                            ++st_pops;
+                            break;
+                        }
+                        old = got;
+                    }
+                    // single-task steal from a random victim block
+                    if (task == kNoTask && P.n_workers > 1) {
+                        ++st_sa;
+                        rng ^= rng >> 12; rng ^= rng << 25; rng ^= rng >> 27;
+                        uint32_t r = (uint32_t)((rng * 2685821657736338717ull) >> 32);
+                        int victim = (int)(((unsigned long long)r * (P.n_workers - 1)) >> 32);
+                        if (victim >= bid) ++victim;
+                        QState* vq = P.qs + victim;
+                        if (ld_cg_i32(&vq->count) > 0 && atom_cas_acq_i32(&vq->lock, 0, 1) == 0) {
+                            int o = ld_cg_i32(&vq->count);
+                            bool claimed = false;
+                            for (int it = 0; it < 64 && o > 0; ++it) {
+                                int got = atom_cas_acq_i32(&vq->count, o, o - 1);
+                                if (got == o) { claimed = true; break; }
+                                o = got;
+                            }
+                            if (claimed) {
+                                uint32_t hd = __ldcg(&vq->head);
+                                task = __ldcg(&P.rings[(size_t)victim * (cap_mask + 1) + (hd & cap_mask)]);
+                                __threadfence();
+                                __stcg(&vq->head, hd + 1u);
+                                ++st_steals;
+                            }
+                            st_release_i32(&vq->lock, 0);
+                        }
+                    }
+                    if (task == kNoTask) {
+                        ++st_idle;
+                        if (ld_cg64(&P.ctl->roots_remaining.v) == 0ull) state = 2;
+                        else if (global_ns() > deadline) { raise_error(P, GTAP_ERR_TIMEOUT, -1, bid, P.timeout_ns); state = 2; }
+                        else if ((st_idle & 31ull) == 1ull && abort_requested(P, true)) state = 2;
+                    } else {
+                        state = 1;
+                    }
+                }
+                if (task != kNoTask) state = 1;
+            }
+            state = __shfl_sync(0xffffffffu, state, 0);
+            task = __shfl_sync(0xffffffffu, task, 0);
+            if (state == 1) {
+                ftop = pool_refill(P, bs.fstack, ftop, (int)P.maxspawn);
+                if (lane == 0) {
+                    if (P.fstate != nullptr) {
+                        unsigned st = (task < P.n_frames) ? atomicCAS(&P.fstate[task], 3u, 1u) : 99u;  // roots start queued
+                        if (st != 3u && st != 1u)
+                            raise_error(P, GTAP_ERR_TASK_FAILED, (int)st, bid, (DBG_EXEC_NOT_ALLOCATED << 32) | task);
+                    }
+                    bs.misc[0] = task;
+                    *bs.hdr = ld_obj<FrameHdr>(frame_ptr(P, task));
+                    bs.ctrl[0] = ftop;
+                    bs.ctrl[2] = 0;
+                    bs.ctrl[4] = 0;
+                    bs.ctrl[5] = 0;
+                }
+                backoff = 32;
+            } else if (state == 0) {
+                if (lane == 0) __nanosleep(backoff);
+                backoff = min(backoff * 2, 2048);
+            }
+            if (lane == 0) bs.ctrl[3] = state;
+            __syncwarp();
+        }
+        __syncthreads();
+        const int state = bs.ctrl[3];
+        if (state == 2) break;
+        if (state == 1) {
+            BTaskCtx c(P, bs, bid);
+            Dispatch::run(c);
+        }
+        __syncthreads();
+        if (warp == 0 && state == 1) {
+            ++st_tasks;
+            if (lane == 0) {
+                const uint32_t self = bs.misc[0];
+                const FrameHdr h = *bs.hdr;
+                char* f = frame_ptr(P, self);
+                const int jp = bs.ctrl[4];
+                st_spawned += (unsigned long long)bs.ctrl[2];
+                if (jp) {
+                    // waiting-child count stored before any child is published
+                    int k = bs.ctrl[2];
+                    uint32_t w0 = (h.w0 & ~0xFF00u) | ((uint32_t)(jp - 1) << 8);
+                    __stcg(reinterpret_cast<uint2*>(f), make_uint2(w0, (uint32_t)k));
+                    if (k == 0) bs.staged_id[bs.ctrl[2]++] = self;
+                }
+                if (bs.ctrl[5]) {
+                    __threadfence();
+                    if (h.parent & kRootBit) {
+                        RootEntry* r = &P.roots[h.parent & ~kRootBit];
+                        atomicExch(&r->done, 1u);
+                        atomicAdd(&P.ctl->roots_remaining.v, ~0ull);
+                    } else {
+                        uint32_t old = atom_add_acqrel_u32(frame_ptr(P, h.parent) + 4, 0xFFFFFFFFu);
+                        if ((old & 0xFFFFFFu) == 1u) bs.staged_id[bs.ctrl[2]++] = h.parent;
+                    }
+                    dbg_transition(P, self, 1u, 0u, DBG_DOUBLE_FREE, (int)(h.w0 & 0xFF), bid);
+                    int top = max(bs.ctrl[0], 0);
+                    if (top < bs.fcap) { bs.fstack[top] = self; bs.ctrl[0] = top + 1; }
+                }
+            }
+            __syncwarp();
+            ftop = pool_spill(P, bs.fstack, max(bs.ctrl[0], 0), fhigh);
+            // retain the first staged task, push the rest (one fence, one count update)
+            const int nst = bs.ctrl[2];
+            if (nst > 0) {
+                const int npush = nst - 1;
+                int overflow = 0;
+                uint32_t tl = bs.misc[2];
+                if (npush > 0 && lane == 0) {
+                    uint32_t hd = __ldcg(&myq->head);
+                    if (tl - hd + (uint32_t)npush > cap_mask + 1) overflow = 1;
+                }
+                if (__shfl_sync(0xffffffffu, overflow, 0)) {
+                    if (lane == 0) raise_error(P, GTAP_ERR_DEQUE_OVERFLOW, -1, bid, cap_mask + 1);
+                } else {
+                    for (int i = lane; i < npush; i += 32) __stcg(&myring[(tl + (uint32_t)i) & cap_mask], bs.staged_id[1 + i]);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) {
+                        bs.misc[1] = bs.staged_id[0];
+                        if (npush > 0) {
+                            bs.misc[2] = tl + (uint32_t)npush;
+                            atomicAdd(&myq->count, npush);
+                            ++st_pushes;
+                            st_pushed += npush;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (t == 0) {
+        WorkerStats s;
+        s.tasks = st_tasks; s.steps = st_tasks; s.pops = st_pops; s.popped = st_pops;
+        s.steal_attempts = st_sa; s.steals = st_steals; s.stolen = st_steals; s.idle = st_idle;
+        s.pushes = st_pushes; s.pushed = st_pushed; s.spawned = st_spawned;
+        for (int i = 0; i < 5; ++i) s.pad[i] = 0;
+        P.stats[bid] = s;
+    }
+}
+
+}  // namespace gtap

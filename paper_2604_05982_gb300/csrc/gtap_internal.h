@@ -1,0 +1,174 @@
+// Layout shared by the host runtime (capi.cu) and the device runtime.
+#pragma once
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define GTAP_HD __host__ __device__
+#else
+#define GTAP_HD
+#endif
+
+namespace gtap {
+
+constexpr int kWarp = 32;
+constexpr int kMaxQueues = 8;          // DAQ queues per warp
+constexpr int kChunk = 32;             // frame IDs moved per pool chunk
+constexpr uint32_t kRootBit = 0x80000000u;
+constexpr uint32_t kNoTask = 0xFFFFFFFFu;
+constexpr int kRootArgBytes = 64;      // per-root argument block
+constexpr int kHdrBytes = 16;
+
+// Built-in program type IDs (frame header "type" field).  0 is never a valid type.
+enum ProgType : int {
+    T_NONE = 0,
+    // thread mode
+    T_FIB = 1,
+    T_NQUEENS = 2,
+    T_UTS = 3,
+    T_UTS_RANGE = 4,     // spawns a contiguous range of a node's children
+    T_INTEGRATE = 5,
+    T_KCLIQUE_ROOT = 6,  // range of DAG edges
+    T_KCLIQUE_EDGE = 7,  // one edge / a sub-range of a candidate set
+    T_KCLIQUE_SET = 8,
+    // block mode
+    T_MSORT = 16,
+    T_MMERGE = 17,
+    T_INTEGRATE_BLK = 18,
+    T_DTT = 19,
+    T_MAX = 32
+};
+
+// Program-set bits selecting a kernel instantiation (which state machines are compiled in).
+enum ProgSet : unsigned {
+    PS_FIB = 1u << 0,
+    PS_NQUEENS = 1u << 1,
+    PS_UTS = 1u << 2,
+    PS_INTEGRATE = 1u << 3,
+    PS_KCLIQUE = 1u << 4,
+    PS_THREAD_ALL = PS_FIB | PS_NQUEENS | PS_UTS | PS_INTEGRATE | PS_KCLIQUE,
+    PS_MSORT = 1u << 8,
+    PS_INTEGRATE_BLK = 1u << 9,
+    PS_DTT = 1u << 10,
+};
+
+// Frame header flag bits.
+constexpr uint32_t kFlagAccumulate = 1u;  // child result is added (u64) into the parent slot
+
+// Task record header, 16 bytes, at the start of every frame.
+//   w0      = type:8 | pc:8 | flags:8 | unused:8
+//   pending = outstanding children:24 | continuation queue:8
+//   parent  = parent task ID, or kRootBit | root index
+//   w3      = slot:16 (byte offset / 8 of the result slot in the parent record) | aux:16
+struct FrameHdr {
+    uint32_t w0;
+    uint32_t pending;
+    uint32_t parent;
+    uint32_t w3;
+};
+
+// Per-queue shared state, 16 bytes.  head and count are the thief-visible
+// words (Sec. 5.1.3); tail0 hands the owner its initial tail (the live tail is
+// kept in shared memory by the owner).
+struct QState {
+    int count;
+    uint32_t head;
+    int lock;
+    uint32_t tail0;
+};
+
+struct ErrorRecord {
+    int code;
+    int task_type;
+    int worker;
+    int pad;
+    unsigned long long detail;
+};
+
+// Control block.  Hot words sit on their own 128-byte lines.
+struct alignas(128) Line128 { unsigned long long v; char pad[120]; };
+struct DevControl {
+    Line128 roots_remaining;   // decremented when a root completes (termination)
+    Line128 abort_flag;        // nonzero: every worker drains and exits
+    Line128 bump;              // next never-used frame ID
+    Line128 cq_enq;            // chunk-queue enqueue ticket
+    Line128 cq_deq;            // chunk-queue dequeue ticket
+    Line128 scratch_top;       // bytes taken from the scratch arena
+    Line128 inflight;          // serving: roots admitted and not yet completed
+    alignas(128) ErrorRecord err;
+};
+
+struct RootEntry {
+    unsigned long long result[2];
+    unsigned int done;
+    unsigned int type;
+    unsigned int queue;
+    unsigned int pad;
+};
+
+// A root as queued by the host: its initial record payload and a read-only
+// per-root environment (e.g. the device buffers a program works on).
+constexpr int kRootPayloadBytes = 48;
+struct RootDesc {
+    uint32_t type;
+    uint32_t queue;
+    uint32_t flags;
+    uint32_t pad;
+    unsigned char payload[kRootPayloadBytes];
+    unsigned char env[kRootArgBytes];
+};
+
+struct WorkerStats {
+    unsigned long long tasks, steps, pops, popped, steal_attempts, steals, stolen, idle, pushes, pushed, spawned;
+    unsigned long long pad[5];
+};
+
+// Kernel parameters (passed by value).
+struct KParams {
+    char* frames;
+    uint64_t n_frames;
+    uint32_t frame_bytes;
+    uint32_t n_workers;       // warps (thread mode) or blocks (block mode)
+    uint32_t n_queues;        // per worker
+    uint32_t ring_mask;       // ring capacity - 1 (power of two)
+    uint32_t* rings;          // [n_workers * n_queues][capacity]
+    QState* qs;               // [n_workers * n_queues]
+    unsigned long long* cq_seq;  // chunk queue sequence numbers [ncq]
+    uint32_t* cq_ids;         // [ncq][kChunk]
+    uint64_t ncq_mask;
+    DevControl* ctl;
+    RootEntry* roots;
+    const RootDesc* root_desc;
+    uint32_t n_roots;
+    uint32_t maxspawn;        // max children one step stages: per lane (thread mode) / per block (block mode)
+    WorkerStats* stats;
+    volatile int* host_abort; // mapped pinned host word, may be null
+    uint64_t timeout_ns;
+    uint64_t seed;
+    int steal_policy;
+    int pad0;
+    char* scratch;            // scratch arena for programs (k-clique candidate sets)
+    uint64_t scratch_bytes;
+    unsigned int* fstate;     // debug: per-record state (0 free, 1 allocated, 2 running, 3 queued), or null
+    unsigned long long* flog; // debug: last 8 events per record
+    unsigned int* flogn;      // debug: event count per record
+};
+
+// Debug-check failure codes (error detail = code << 32 | record id).
+enum DebugFault : unsigned long long {
+    DBG_DOUBLE_ALLOC = 1, DBG_DOUBLE_FREE = 2, DBG_EXEC_NOT_ALLOCATED = 3, DBG_BAD_ID = 4,
+};
+
+// Shared-memory sizing (thread mode: per warp; block mode: per block, runtime part).
+GTAP_HD constexpr int thread_fcap(int maxspawn) { return 32 * maxspawn + 3 * kChunk + 32; }
+GTAP_HD constexpr int thread_scap(int maxspawn) { return 32 * (maxspawn > 1 ? maxspawn : 1); }
+GTAP_HD constexpr int thread_warp_smem(int maxspawn) {
+    return 128 /*ctrl, cls_count, tail, push_off*/ + 128 + 128 +
+           4 * thread_fcap(maxspawn) + 4 * thread_scap(maxspawn) + ((thread_scap(maxspawn) + 15) / 16) * 16;
+}
+
+// Block mode: step_max = most children one block step can spawn (all threads together).
+GTAP_HD constexpr int block_fcap(int step_max) { return step_max + 3 * kChunk + 32; }
+GTAP_HD constexpr int block_scap(int step_max) { return ((step_max + 2 + 3) / 4) * 4; }
+GTAP_HD constexpr int block_rt_smem(int step_max) { return 128 + 4 * block_fcap(step_max) + 4 * block_scap(step_max); }
+
+}  // namespace gtap

@@ -1,0 +1,88 @@
+// Thread-mode persistent kernels, one instantiation per program set.
+#include "launch.h"
+#include "gtap_device.cuh"
+#include "programs_thread.cuh"
+
+namespace gtap {
+
+template <unsigned PSET>
+struct ThreadDispatch {
+    __device__ static void run(TaskCtx& c) {
+        switch (c.type()) {
+        case T_FIB:
+            if constexpr ((PSET & PS_FIB) != 0) { fib_step(c); return; }
+            break;
+        case T_NQUEENS:
+            if constexpr ((PSET & PS_NQUEENS) != 0) { nqueens_step(c); return; }
+            break;
+        case T_UTS:
+            if constexpr ((PSET & PS_UTS) != 0) { uts_step(c); return; }
+            break;
+        case T_UTS_RANGE:
+            if constexpr ((PSET & PS_UTS) != 0) { uts_range_step(c); return; }
+            break;
+        case T_INTEGRATE:
+            if constexpr ((PSET & PS_INTEGRATE) != 0) { integrate_step(c); return; }
+            break;
+        default:
+            break;
+        }
+        c.fail(GTAP_ERR_UNKNOWN_TASK, (unsigned long long)c.type());
+        // drop the task: completing it would touch a record of unknown layout
+    }
+};
+
+template <unsigned PSET>
+__global__ void __launch_bounds__(256) thread_kernel(KParams P) {
+    extern __shared__ __align__(16) char smem[];
+    const int wib = threadIdx.x >> 5;
+    thread_mode_loop<ThreadDispatch<PSET>>(P, smem + (size_t)wib * thread_warp_smem((int)P.maxspawn));
+}
+
+#define GTAP_THREAD_SETS(X) X(PS_FIB) X(PS_NQUEENS) X(PS_UTS) X(PS_INTEGRATE) X(PS_THREAD_ALL)
+
+static const void* thread_kernel_fn(unsigned pset) {
+    switch (pset) {
+#define X(S) case S: return reinterpret_cast<const void*>(&thread_kernel<S>);
+        GTAP_THREAD_SETS(X)
+#undef X
+    default: return nullptr;
+    }
+}
+
+unsigned thread_kernel_pset(unsigned registered) {
+    const unsigned singles[] = {PS_FIB, PS_NQUEENS, PS_UTS, PS_INTEGRATE};
+    for (unsigned s : singles)
+        if (registered != 0 && (registered & ~s) == 0) return s;
+    return PS_THREAD_ALL;
+}
+
+int thread_kernel_maxspawn(unsigned pset) {
+    int m = 1;
+    if (pset & PS_FIB) m = max(m, 2);
+    if (pset & PS_NQUEENS) m = max(m, 16);
+    if (pset & PS_UTS) m = max(m, 8);
+    if (pset & PS_INTEGRATE) m = max(m, 2);
+    return m;
+}
+
+uint32_t thread_record_bytes(unsigned) { return 64; }
+
+cudaError_t launch_thread_kernel(unsigned pset, const KParams& P, int grid, int block, size_t smem, cudaStream_t s) {
+    const void* fn = thread_kernel_fn(pset);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {const_cast<KParams*>(&P)};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
+}
+
+cudaError_t thread_kernel_occupancy(unsigned pset, int block, size_t smem, int* blocks_per_sm) {
+    const void* fn = thread_kernel_fn(pset);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
+}
+
+}  // namespace gtap

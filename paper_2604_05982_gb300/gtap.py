@@ -1,0 +1,194 @@
+"""Python binding of the C ABI in include/gtap.h (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+work of its own: the fork-join runtime runs entirely in libgtap.so.  A
+non-zero status raises GtapError.  If the native library is missing this
+module raises at import time: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgtap.so")
+
+GTAP_MODE_THREAD = 0
+GTAP_MODE_BLOCK = 1
+GTAP_STEAL_FILL = 0
+GTAP_STEAL_EMPTY = 1
+GTAP_STEAL_HALF = 2
+
+STATUS = {
+    0: "GTAP_OK", 1: "GTAP_ERR_INVALID_ARG", 2: "GTAP_ERR_NO_MEMORY", 3: "GTAP_ERR_POOL_EXHAUSTED",
+    4: "GTAP_ERR_DEQUE_OVERFLOW", 5: "GTAP_ERR_LIST_OVERFLOW", 6: "GTAP_ERR_TIMEOUT", 7: "GTAP_ERR_CUDA",
+    8: "GTAP_ERR_BUSY", 9: "GTAP_ERR_UNKNOWN_TASK", 10: "GTAP_ERR_TASK_FAILED", 11: "GTAP_ERR_NOT_READY",
+}
+globals().update({v: k for k, v in STATUS.items()})
+
+
+class GtapError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class gtap_config(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int), ("threads_per_block", ctypes.c_int),
+                ("deque_capacity", ctypes.c_int), ("steal_policy", ctypes.c_int), ("max_roots", ctypes.c_int),
+                ("frame_bytes", ctypes.c_int), ("device_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
+                ("stream", ctypes.c_void_p), ("timeout_ns", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("scratch_bytes", ctypes.c_size_t), ("grid_blocks", ctypes.c_int), ("debug_checks", ctypes.c_int)]
+
+
+class gtap_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "tasks_executed", "tasks_created", "steps", "pops", "popped", "steal_attempts", "steals", "stolen",
+        "idle_iterations", "pushes", "pushed", "frames_high_water", "scratch_used")] + [
+        ("n_workers", ctypes.c_int), ("grid_blocks", ctypes.c_int), ("threads_per_block", ctypes.c_int),
+        ("kernel_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class gtap_error_info(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int), ("task_type", ctypes.c_int), ("worker", ctypes.c_int),
+                ("pad", ctypes.c_int), ("detail", ctypes.c_uint64)]
+
+
+class gtap_fib_args(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("route", ctypes.c_int32)]
+
+
+class gtap_nqueens_args(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("route", ctypes.c_int32)]
+
+
+class gtap_uts_args(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("threshold", ctypes.c_uint64), ("root_children", ctypes.c_uint32),
+                ("m", ctypes.c_uint32), ("route", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class gtap_integrate_args(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class gtap_mergesort_args(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("tmp", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("leaf", ctypes.c_uint32), ("merge_cutoff", ctypes.c_uint32)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "gtap_init": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(gtap_config),
+                                 ctypes.POINTER(_P)]),
+    "gtap_register_task": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
+    "gtap_spawn_root": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "gtap_run": (ctypes.c_int, [_P]),
+    "gtap_wait": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "gtap_read_result": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t]),
+    "gtap_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gtap_stats)]),
+    "gtap_last_error": (ctypes.c_int, [_P, ctypes.POINTER(gtap_error_info)]),
+    "gtap_clear_roots": (ctypes.c_int, [_P]),
+    "gtap_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gtap_finalize": (ctypes.c_int, [_P]),
+    "gtap_debug_snapshot": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgtap.so (build it first with paper_2604_05982_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"native library not built: {path} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, where: str, ok=(0,)):
+    if status not in ok:
+        raise GtapError(status, where)
+    return status
+
+
+def gtap_status_string(status: int) -> str:
+    return load_library().gtap_status_string(status).decode()
+
+
+def gtap_init(mode: int, n_queues: int, frame_pool_bytes: int, cfg: gtap_config | None = None) -> int:
+    ctx = _P()
+    _check(load_library().gtap_init(mode, n_queues, frame_pool_bytes, ctypes.byref(cfg) if cfg else None,
+                                    ctypes.byref(ctx)), "gtap_init")
+    return ctx.value
+
+
+def gtap_register_task(ctx: int, program: str) -> int:
+    t = ctypes.c_int(0)
+    _check(load_library().gtap_register_task(ctx, program.encode(), ctypes.byref(t)), "gtap_register_task")
+    return t.value
+
+
+def gtap_spawn_root(ctx: int, type_id: int, args: ctypes.Structure, queue: int = 0) -> int:
+    h = ctypes.c_uint64(0)
+    _check(load_library().gtap_spawn_root(ctx, type_id, ctypes.byref(args), ctypes.sizeof(args), queue,
+                                          ctypes.byref(h)), "gtap_spawn_root")
+    return h.value
+
+
+def gtap_run(ctx: int) -> None:
+    _check(load_library().gtap_run(ctx), "gtap_run")
+
+
+def gtap_wait(ctx: int, timeout_ms: int = 0, raise_on_error: bool = True) -> int:
+    s = load_library().gtap_wait(ctx, timeout_ms)
+    if raise_on_error:
+        _check(s, "gtap_wait")
+    return s
+
+
+def gtap_read_result(ctx: int, handle: int, nbytes: int = 8) -> bytes:
+    buf = (ctypes.c_char * nbytes)()
+    _check(load_library().gtap_read_result(ctx, handle, buf, nbytes), "gtap_read_result")
+    return bytes(buf)
+
+
+def gtap_get_stats(ctx: int) -> gtap_stats:
+    st = gtap_stats()
+    _check(load_library().gtap_get_stats(ctx, ctypes.byref(st)), "gtap_get_stats")
+    return st
+
+
+def gtap_last_error(ctx: int) -> gtap_error_info:
+    e = gtap_error_info()
+    _check(load_library().gtap_last_error(ctx, ctypes.byref(e)), "gtap_last_error")
+    return e
+
+
+def gtap_clear_roots(ctx: int) -> None:
+    _check(load_library().gtap_clear_roots(ctx), "gtap_clear_roots")
+
+
+def gtap_finalize(ctx: int) -> None:
+    _check(load_library().gtap_finalize(ctx), "gtap_finalize")
+
+
+def gtap_debug_snapshot(ctx: int) -> dict:
+    buf = (ctypes.c_uint64 * 9)()
+    _check(load_library().gtap_debug_snapshot(ctx, buf, 9), "gtap_debug_snapshot")
+    names = ["roots_remaining", "bump", "cq_enq", "cq_deq", "queued", "nonempty_queues", "locks_held",
+             "max_count", "abort"]
+    return dict(zip(names, list(buf)))

@@ -1,0 +1,129 @@
+"""Convenience calls over the C ABI: one context, one batch of roots, one run.
+
+Marshalling only: each helper creates a context (gtap_init), registers the
+program, queues roots, runs, waits and reads results back.  All compute runs
+in libgtap.so.
+"""
+from __future__ import annotations
+
+import ctypes
+import struct
+from dataclasses import dataclass, field
+
+from . import gtap as G
+
+UTS_THRESHOLD_Q0199 = 199 * 2 ** 64 // 1000   # floor(0.199 * 2^64)
+
+
+@dataclass
+class RunResult:
+    values: list
+    stats: dict = field(default_factory=dict)
+    status: int = 0
+
+
+DEFAULT_TIMEOUT_NS = 20 * 10 ** 9   # device-side deadline of a helper run
+
+
+def make_config(**kw) -> G.gtap_config:
+    cfg = G.gtap_config()
+    cfg.timeout_ns = DEFAULT_TIMEOUT_NS
+    for k, v in kw.items():
+        if v is not None:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class Context:
+    """RAII wrapper of a gtap context (marshalling only)."""
+
+    def __init__(self, mode: int, n_queues: int = 1, pool_bytes: int = 256 << 20, **cfg):
+        self.cfg = make_config(**cfg)
+        self.ctx = G.gtap_init(mode, n_queues, pool_bytes, self.cfg)
+
+    def register(self, program: str) -> int:
+        return G.gtap_register_task(self.ctx, program)
+
+    def spawn(self, type_id: int, args, queue: int = 0) -> int:
+        return G.gtap_spawn_root(self.ctx, type_id, args, queue)
+
+    def run(self, timeout_ms: int = 0, raise_on_error: bool = True) -> int:
+        G.gtap_run(self.ctx)
+        return G.gtap_wait(self.ctx, timeout_ms, raise_on_error)
+
+    def result_u64(self, h: int) -> int:
+        return struct.unpack("<Q", G.gtap_read_result(self.ctx, h, 8))[0]
+
+    def result_i64(self, h: int) -> int:
+        return struct.unpack("<q", G.gtap_read_result(self.ctx, h, 8))[0]
+
+    def result_f64(self, h: int) -> float:
+        return struct.unpack("<d", G.gtap_read_result(self.ctx, h, 8))[0]
+
+    def stats(self) -> dict:
+        return G.gtap_get_stats(self.ctx).as_dict()
+
+    def last_error(self) -> G.gtap_error_info:
+        return G.gtap_last_error(self.ctx)
+
+    def clear(self):
+        G.gtap_clear_roots(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            G.gtap_finalize(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fib(ns, n_queues: int = 1, route: int = 0, **cfg) -> RunResult:
+    ns = [ns] if isinstance(ns, int) else list(ns)
+    with Context(G.GTAP_MODE_THREAD, n_queues, **cfg) as c:
+        t = c.register("fib")
+        hs = [c.spawn(t, G.gtap_fib_args(n, route)) for n in ns]
+        c.run()
+        return RunResult([c.result_i64(h) for h in hs], c.stats())
+
+
+def nqueens(ns, n_queues: int = 1, route: int = 0, **cfg) -> RunResult:
+    ns = [ns] if isinstance(ns, int) else list(ns)
+    with Context(G.GTAP_MODE_THREAD, n_queues, **cfg) as c:
+        t = c.register("nqueens")
+        hs = [c.spawn(t, G.gtap_nqueens_args(n, route)) for n in ns]
+        c.run()
+        return RunResult([c.result_u64(h) for h in hs], c.stats())
+
+
+def uts(seed: int = 42, root_children: int = 2000, m: int = 5, threshold: int = UTS_THRESHOLD_Q0199,
+        n_queues: int = 1, route: int = 0, **cfg) -> RunResult:
+    """Result values: [(nodes, leaves)]."""
+    with Context(G.GTAP_MODE_THREAD, n_queues, **cfg) as c:
+        t = c.register("uts")
+        h = c.spawn(t, G.gtap_uts_args(seed, threshold, root_children, m, route, 0))
+        c.run()
+        v = c.result_u64(h)
+        return RunResult([(v >> 32, v & 0xFFFFFFFF)], c.stats())
+
+
+def integrate(a: float, b: float, eps: float, block: bool = False, **cfg) -> RunResult:
+    mode = G.GTAP_MODE_BLOCK if block else G.GTAP_MODE_THREAD
+    with Context(mode, 1, **cfg) as c:
+        t = c.register("integrate_block" if block else "integrate")
+        h = c.spawn(t, G.gtap_integrate_args(a, b, eps))
+        c.run()
+        return RunResult([c.result_f64(h)], c.stats())
+
+
+def mergesort_ptrs(src: int, dst: int, tmp: int, n: int, leaf: int = 4096, merge_cutoff: int = 4096,
+                   **cfg) -> RunResult:
+    """Sort n uint32 keys at device address src into dst (tmp: n-key scratch)."""
+    with Context(G.GTAP_MODE_BLOCK, 1, **cfg) as c:
+        t = c.register("mergesort")
+        c.spawn(t, G.gtap_mergesort_args(src, dst, tmp, n, leaf, merge_cutoff))
+        c.run()
+        return RunResult([], c.stats())
