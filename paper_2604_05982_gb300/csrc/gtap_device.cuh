@@ -266,6 +266,8 @@ struct WarpSh {
     int* cls_count;     // [kMaxQueues]
     uint32_t* tail;     // [kMaxQueues] owner tails (Sec. 5.1.3: tail kept in shared memory)
     int* push_off;      // [kMaxQueues]
+    int* hint;          // [kMaxQueues] owner's upper bound of count (only the owner increases count)
+    uint32_t* head_lb;  // [kMaxQueues] owner's lower bound of head (heads only grow)
     uint32_t* retained; // [32]
     uint32_t* freed;    // [32]
     uint32_t* fstack;   // [fcap]
@@ -283,9 +285,11 @@ __device__ __forceinline__ WarpSh carve_warp(char* base, int maxspawn) {
     w.cls_count = ints + 8;
     w.tail = reinterpret_cast<uint32_t*>(ints + 16);
     w.push_off = ints + 24;
-    w.retained = reinterpret_cast<uint32_t*>(base + 128);
-    w.freed = reinterpret_cast<uint32_t*>(base + 256);
-    w.fstack = reinterpret_cast<uint32_t*>(base + 384);
+    w.hint = ints + 32;
+    w.head_lb = reinterpret_cast<uint32_t*>(ints + 40);
+    w.retained = reinterpret_cast<uint32_t*>(base + 256);
+    w.freed = reinterpret_cast<uint32_t*>(base + 384);
+    w.fstack = reinterpret_cast<uint32_t*>(base + 512);
     w.staged_id = w.fstack + w.fcap;
     w.staged_q = reinterpret_cast<uint8_t*>(w.staged_id + w.scap);
     return w;
@@ -425,14 +429,18 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
     if (lane < 8) {
         ws.cls_count[lane] = 0;
         ws.push_off[lane] = 0;
-        ws.tail[lane] = (lane < Q) ? __ldcg(&myq[lane].tail0) : 0u;
+        const uint32_t t0 = (lane < Q) ? __ldcg(&myq[lane].tail0) : 0u;
+        ws.tail[lane] = t0;
+        ws.hint[lane] = (int)t0;   // the reset kernel leaves count == tail0 and head == 0
+        ws.head_lb[lane] = 0;
     }
     if (lane == 0) { ws.ctrl[0] = 0; ws.ctrl[1] = 0; ws.ctrl[2] = 0; ws.ctrl[3] = 0; }
     __syncwarp();
 
     unsigned long long st_tasks = 0, st_steps = 0, st_pops = 0, st_popped = 0, st_sa = 0, st_steals = 0,
                        st_stolen = 0, st_idle = 0, st_pushes = 0, st_pushed = 0, st_spawned = 0;
-    uint64_t rng = P.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(wid + 1));
+    // per-lane xorshift state for victim probing
+    uint64_t rng = P.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(wid + 1)) ^ (0xD1B54A32D192ED03ull * (uint64_t)(lane + 1));
     const uint64_t t_start = global_ns();
     const uint64_t deadline = t_start + P.timeout_ns;
     uint32_t tid = kNoTask;  // this lane's task (valid for lane < cnt)
@@ -442,20 +450,21 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
     int backoff = 32;
     int ftop = 0;
     const int fhigh = 32 * (int)P.maxspawn + 2 * kChunk;
+    constexpr int kProbes = 8;   // victims probed in parallel per steal attempt (one lane each)
 
     for (uint32_t iter = 0;; ++iter) {
-        if ((iter & 15u) == 0u) {
+        if ((iter & 63u) == 0u) {
             int ab = 0;
-            if (lane == 0) ab = abort_requested(P, (iter & 255u) == 0u) ? 1 : 0;
+            if (lane == 0) ab = abort_requested(P, (iter & 1023u) == 0u) ? 1 : 0;
             if (__shfl_sync(0xffffffffu, ab, 0)) break;
         }
         // ---- PopBatch (Algorithm 2) from the own queue: the retained class, else the fullest (DAQ).
+        // The owner keeps an upper bound of each count (thieves only lower it), so an empty
+        // queue costs no memory access and the CAS starts from a good guess.
         if (cnt < 32) {
-            int c = (lane < Q) ? ld_cg_i32(&myq[lane].count) : -1;
             int q = cls;
-            if (cnt == 0) {
-                // fullest queue; ties -> lowest index
-                int best = c, bq = lane;
+            if (cnt == 0 && Q > 1) {
+                int best = (lane < Q) ? ws.hint[lane] : -1, bq = lane;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     int oc = __shfl_down_sync(0xffffffffu, best, o);
@@ -464,17 +473,17 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                 }
                 q = __shfl_sync(0xffffffffu, bq, 0);
             }
-            int cq = __shfl_sync(0xffffffffu, c, q);
-            if (cq > 0) {
+            if (ws.hint[q] > 0) {
                 int claim = 0;
                 if (lane == 0) {
-                    int old = cq;
+                    int old = ws.hint[q];
                     for (int it = 0; it < 64 && old > 0; ++it) {
-                        int want = min(32 - cnt, old);
-                        int got = atom_cas_acq_i32(&myq[q].count, old, old - want);
-                        if (got == old) { claim = want; break; }
+                        const int want = min(32 - cnt, old);
+                        const int got = atom_cas_acq_i32(&myq[q].count, old, old - want);
+                        if (got == old) { claim = want; old -= want; break; }
                         old = got;
                     }
+                    ws.hint[q] = max(old, 0);
                 }
                 claim = __shfl_sync(0xffffffffu, claim, 0);
                 if (claim > 0) {
@@ -496,46 +505,52 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                     cls = q;
                     ++st_pops;
                     st_popped += claim;
+                } else {
+                    __syncwarp();
                 }
             }
         }
-        // ---- StealBatch from a random victim.
+        // ---- StealBatch.  SelectVictimQueue probes kProbes random victims at once (one
+        // lane each) and picks the fullest, so an idle warp finds work in one round trip.
         const bool want_steal = (P.steal_policy & GTAP_STEAL_EMPTY) ? (cnt == 0) : (cnt < 32);
         if (want_steal && P.n_workers > 1) {
             ++st_sa;
-            rng ^= rng >> 12; rng ^= rng << 25; rng ^= rng >> 27;
-            uint32_t r = (uint32_t)((rng * 2685821657736338717ull) >> 32);
-            int victim = (int)(((unsigned long long)r * (P.n_workers - 1)) >> 32);
-            if (victim >= wid) ++victim;
-            QState* vq = P.qs + (size_t)victim * Q;
-            int c = (lane < Q) ? ld_cg_i32(&vq[lane].count) : -1;
-            int q = cls;
-            if (cnt == 0) {
-                int best = c, bq = lane;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    int oc = __shfl_down_sync(0xffffffffu, best, o);
-                    int oq = __shfl_down_sync(0xffffffffu, bq, o);
-                    if (oc > best || (oc == best && oq < bq)) { best = oc; bq = oq; }
-                }
-                q = __shfl_sync(0xffffffffu, bq, 0);
+            int c = -1, victim = 0, vqi = cls;
+            if (lane < kProbes) {
+                rng ^= rng >> 12; rng ^= rng << 25; rng ^= rng >> 27;
+                const uint64_t r = rng * 2685821657736338717ull;
+                victim = (int)(((r >> 32) * (unsigned long long)(P.n_workers - 1)) >> 32);
+                if (victim >= wid) ++victim;
+                if (cnt == 0 && Q > 1) vqi = (int)(((r & 0xFFFFFFFFull) * (unsigned long long)Q) >> 32);
+                c = ld_cg_i32(&P.qs[(size_t)victim * Q + vqi].count);
             }
-            int cv = __shfl_sync(0xffffffffu, c, q);
-            if (cv > 0) {
+            int best = c, bl = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                int oc = __shfl_down_sync(0xffffffffu, best, o);
+                int ol = __shfl_down_sync(0xffffffffu, bl, o);
+                if (oc > best) { best = oc; bl = ol; }
+            }
+            bl = __shfl_sync(0xffffffffu, bl, 0);
+            best = __shfl_sync(0xffffffffu, best, 0);
+            victim = __shfl_sync(0xffffffffu, victim, bl);
+            const int q = __shfl_sync(0xffffffffu, vqi, bl);
+            if (best > 0) {
+                QState* vq = P.qs + (size_t)victim * Q + q;
                 int claim = 0;
                 uint32_t h = 0;
                 if (lane == 0) {
-                    if (atom_cas_acq_i32(&vq[q].lock, 0, 1) == 0) {  // try-lock: never wait on a thief
-                        int old = ld_cg_i32(&vq[q].count);
+                    if (atom_cas_acq_i32(&vq->lock, 0, 1) == 0) {  // try-lock: never wait on a thief
+                        int old = best;
                         for (int it = 0; it < 64 && old > 0; ++it) {
                             int want = min(32 - cnt, old);
                             if (P.steal_policy & GTAP_STEAL_HALF) want = min(want, (old + 1) >> 1);
-                            int got = atom_cas_acq_i32(&vq[q].count, old, old - want);
+                            const int got = atom_cas_acq_i32(&vq->count, old, old - want);
                             if (got == old) { claim = want; break; }
                             old = got;
                         }
-                        h = __ldcg(&vq[q].head);
-                        if (claim == 0) st_release_i32(&vq[q].lock, 0);
+                        if (claim > 0) h = __ldcg(&vq->head);
+                        else st_release_i32(&vq->lock, 0);
                     }
                 }
                 claim = __shfl_sync(0xffffffffu, claim, 0);
@@ -552,12 +567,15 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                             if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 2, wid, (DBG_BAD_ID << 32) | was);
                         }
                     }
+                    // every claimed ID is in a register before the head moves (wrap-around safety, Sec. 5.1.3)
+                    const uint32_t used = __reduce_or_sync(0xffffffffu, (lane >= cnt && lane < cnt + claim) ? tid : 0u);
+                    uint32_t zero;
+                    asm volatile("and.b32 %0, %1, 0;" : "=r"(zero) : "r"(used));  // the head store waits for the loads
                     __threadfence();
                     __syncwarp();
-                    // advance head only after the claimed IDs are read (wrap-around safety, Sec. 5.1.3)
                     if (lane == 0) {
-                        __stcg(&vq[q].head, h + (uint32_t)claim);
-                        st_release_i32(&vq[q].lock, 0);
+                        __stcg(&vq->head, h + (uint32_t)claim + zero);
+                        st_release_i32(&vq->lock, 0);
                     }
                     cnt += claim;
                     cls = q;
@@ -570,14 +588,14 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
         if (cnt == 0) {
             ++st_idle;
             int stop = 0;
-            if (lane == 0) {
+            if (lane == 0 && (st_idle & 3ull) == 1ull) {
                 if (ld_cg64(&P.ctl->roots_remaining.v) == 0ull) stop = 1;
-                else if (abort_requested(P, (st_idle & 31ull) == 1ull)) stop = 1;
+                else if (abort_requested(P, (st_idle & 255ull) == 1ull)) stop = 1;
                 else if (global_ns() > deadline) { raise_error(P, GTAP_ERR_TIMEOUT, -1, wid, P.timeout_ns); stop = 1; }
             }
             if (__shfl_sync(0xffffffffu, stop, 0)) break;
             __nanosleep(backoff);
-            backoff = min(backoff * 2, 2048);
+            backoff = min(backoff * 2, 512);
             continue;
         }
         backoff = 32;
@@ -642,8 +660,9 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             int overflow = 0;
             if (lane < Q) {
                 int npush = ((Q > 1) ? ws.cls_count[lane] : nst) - (lane == qstar ? nkeep : 0);
-                if (npush > 0) {
-                    uint32_t hd = __ldcg(&myq[lane].head);
+                if (npush > 0 && ws.tail[lane] - ws.head_lb[lane] + (uint32_t)npush > cap_mask + 1) {
+                    const uint32_t hd = __ldcg(&myq[lane].head);   // refresh the lower bound only when needed
+                    ws.head_lb[lane] = hd;
                     if (ws.tail[lane] - hd + (uint32_t)npush > cap_mask + 1) overflow = 1;
                 }
                 ws.push_off[lane] = 0;
@@ -687,6 +706,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                 int np = ws.push_off[lane];
                 if (np > 0) {
                     ws.tail[lane] += (uint32_t)np;
+                    ws.hint[lane] += np;
                     atomicAdd(&myq[lane].count, np);
                 }
             }

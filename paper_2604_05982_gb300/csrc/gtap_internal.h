@@ -162,7 +162,7 @@ enum DebugFault : unsigned long long {
 GTAP_HD constexpr int thread_fcap(int maxspawn) { return 32 * maxspawn + 3 * kChunk + 32; }
 GTAP_HD constexpr int thread_scap(int maxspawn) { return 32 * (maxspawn > 1 ? maxspawn : 1); }
 GTAP_HD constexpr int thread_warp_smem(int maxspawn) {
-    return 128 /*ctrl, cls_count, tail, push_off*/ + 128 + 128 +
+    return 256 /*ctrl, cls_count, tail, push_off, hint, head_lb*/ + 128 + 128 +
            4 * thread_fcap(maxspawn) + 4 * thread_scap(maxspawn) + ((thread_scap(maxspawn) + 15) / 16) * 16;
 }
 

@@ -37,7 +37,7 @@ def make_config(**kw) -> G.gtap_config:
 class Context:
     """RAII wrapper of a gtap context (marshalling only)."""
 
-    def __init__(self, mode: int, n_queues: int = 1, pool_bytes: int = 256 << 20, **cfg):
+    def __init__(self, mode: int, n_queues: int = 1, pool_bytes: int = 1 << 30, **cfg):
         self.cfg = make_config(**cfg)
         self.ctx = G.gtap_init(mode, n_queues, pool_bytes, self.cfg)
 
