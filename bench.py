@@ -1,0 +1,303 @@
+"""Benchmark of the fork-join runtime on the integer workload set of the paper's evaluation.
+
+One step = one pass of the three workloads of the integer benchmark set,
+each one persistent-kernel run through the C ABI:
+  * N-Queens n=13, thread mode, one task per placed row, DAQ with 4 queues
+    routed by depth mod 4 (4,674,890 tasks);
+  * the unbalanced hashed tree, seed 42, root 2000 children, m=5, q=0.199
+    (173,496 node tasks);
+  * block-mode mergesort of 2^26 uniform uint32 keys, 4096-key leaves
+    (32,767 sort tasks in the recursion tree; merges fork further pieces).
+metric: tasks/s = (N-Queens nodes + tree nodes + sort-tree tasks) per second.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on
+the host cores for the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NQ_N = 13
+NQ_TASKS = 4674890
+UTS_NODES = 173496
+MSORT_LOG2 = 26
+MSORT_LEAF = 4096
+MSORT_SORT_TASKS = 2 * ((1 << MSORT_LOG2) // MSORT_LEAF) - 1
+STEP_TASKS = NQ_TASKS + UTS_NODES + MSORT_SORT_TASKS
+MSORT_BYTES = 8.05e9 * (1 << MSORT_LOG2) / (1 << 26)   # algorithmic HBM bytes: leaf pass + 14 merge levels
+
+CONFIG = {"workload": "integer set: nqueens13 thread DAQ4 (depth mod 4) + hashed tree seed42 (2000, m=5, q=0.199) "
+                      "+ block mergesort 2^26 u32 (4096-key leaves)",
+          "nqueens_n": NQ_N, "tree_seed": 42, "mergesort_keys": 1 << MSORT_LOG2, "mergesort_leaf": MSORT_LEAF,
+          "daq_queues": 4, "l2": "mergesort input 256 MiB > L2 (129 MB); task records re-initialised every run",
+          "parallelism": "replicas"}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                mx = float(s[2])
+                for name, v in zip(names, s[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2604_05982_gb300 import gtap as G
+    from paper_2604_05982_gb300 import inputs, runner
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    G.load_library()
+
+    n = 1 << MSORT_LOG2
+    keys = inputs.keys_u32(n, seed=1)
+    src = torch.from_numpy(keys.view(np.int32)).cuda()
+    dst = torch.empty_like(src)
+    tmp = torch.empty_like(src)
+    torch.cuda.synchronize()
+
+    nq = runner.Context(G.GTAP_MODE_THREAD, 4, pool_bytes=1 << 30)
+    t = nq.register("nqueens")
+    h_nq = nq.spawn(t, G.gtap_nqueens_args(NQ_N, 1))
+    ut = runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=1 << 30)
+    t = ut.register("uts")
+    h_ut = ut.spawn(t, G.gtap_uts_args(42, runner.UTS_THRESHOLD_Q0199, 2000, 5, 0, 0))
+    ms = runner.Context(G.GTAP_MODE_BLOCK, 1, pool_bytes=256 << 20)
+    t = ms.register("mergesort")
+    ms.spawn(t, G.gtap_mergesort_args(src.data_ptr(), dst.data_ptr(), tmp.data_ptr(), n, MSORT_LEAF, 16384))
+    launches_per_step = 6   # each run: reset kernel + persistent scheduler kernel
+
+    def step():
+        t_nq = nq.run()
+        t_ut = ut.run()
+        t_ms = ms.run()
+        return nq.stats()["kernel_ms"], ut.stats()["kernel_ms"], ms.stats()["kernel_ms"]
+
+    for _ in range(args.warmup):
+        step()
+    # parity spot check of this exact launch configuration (outside the timed region)
+    assert nq.result_u64(h_nq) == 73712
+    v = ut.result_u64(h_ut)
+    assert (v >> 32, v & 0xFFFFFFFF) == (UTS_NODES, 139196)
+    out = dst[:: 1 << 12].cpu().numpy().view(np.uint32)
+    assert np.all(out[1:] >= out[:-1])
+
+    per_kernel = {"nqueens": [], "tree": [], "mergesort": []}
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            a, b, c = step()
+            per_kernel["nqueens"].append(a)
+            per_kernel["tree"].append(b)
+            per_kernel["mergesort"].append(c)
+        e1.record()
+        torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        elapsed_ms = float(tt.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = STEP_TASKS * args.steps * world / (elapsed_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of the keys from pinned memory,
+    # the three runs, and D2H of the sorted keys and of the counts (gtap_wait reads them back)
+    pinned_in = torch.from_numpy(keys.view(np.int32)).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(args.steps):
+        src.copy_(pinned_in, non_blocking=True)
+        step()
+        pinned_out.copy_(dst, non_blocking=True)
+    e3.record()
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3) / args.steps
+
+    hbm_peak, peak_kind = _peaks()
+    ms_kernel = sorted(per_kernel["mergesort"])[len(per_kernel["mergesort"]) // 2]
+    achieved = MSORT_BYTES / (ms_kernel / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("mergesort_2pow26_bytes")
+    except (OSError, ValueError):
+        pass
+    line = {
+        "metric": "tasks/s", "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic", "config": CONFIG,
+        "breakdown_ms": {k: sorted(v)[len(v) // 2] for k, v in per_kernel.items()},
+        "roofline": {"bound": "hbm", "kernel": "block_kernel<mergesort> (2^26 keys)", "achieved": achieved,
+                     "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": traffic, "algorithmic_bytes": MSORT_BYTES},
+        "e2e": {"value": STEP_TASKS / (e2e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": n * 4 + 3 * 128, "d2h_bytes_per_step": n * 4 + 3 * 32},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    for c in (nq, ut, ms):
+        c.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _cpu_step():
+    """One bounded pass of the CPU oracle over the same workload (single thread)."""
+    import oracle
+    from paper_2604_05982_gb300 import inputs
+    t0 = time.perf_counter()
+    s, tasks = oracle.nqueens(NQ_N)
+    assert (s, tasks) == (73712, NQ_TASKS)
+    assert oracle.uts(42) == (UTS_NODES, 139196)
+    keys = inputs.keys_u32(1 << MSORT_LOG2, seed=1)
+    t1 = time.perf_counter()
+    oracle.sort_u32(keys)
+    t2 = time.perf_counter()
+    return (t1 - t0) + (t2 - t1)
+
+
+def cpu_baseline():
+    import oracle
+    oracle.build()
+    try:
+        os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    except (AttributeError, OSError):
+        pass
+    secs = _cpu_step()
+    return {"value": STEP_TASKS / secs, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+            "sample": "one full step: oracle N-Queens(13), hashed tree seed 42, std::sort of the same 2^26 keys "
+                      f"(single thread, {secs:.2f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    try:
+        os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    except (AttributeError, OSError):
+        pass
+    for _ in range(args.warmup):
+        _cpu_step()
+    times = [_cpu_step() for _ in range(args.steps)]
+    secs = sum(times)
+    value = STEP_TASKS * args.steps / secs
+    line = {"impl": "reference", "metric": "tasks/s", "value": value, "unit": "tasks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+            "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                             "sample": "full step per iteration, single thread"},
+            "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gtap", choices=["gtap", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -58,7 +58,9 @@ typedef enum { GTAP_MODE_THREAD = 0, GTAP_MODE_BLOCK = 1 } gtap_mode;
 /* Steal policy bits (gtap_config.steal_policy). */
 #define GTAP_STEAL_FILL 0      /* steal whenever the warp batch is not full (Alg. 1) */
 #define GTAP_STEAL_EMPTY 1     /* steal only when the warp has no task at all */
-#define GTAP_STEAL_HALF 2      /* claim at most half of the victim's queue (else up to 32 - cnt) */
+#define GTAP_STEAL_HALF 2      /* thread mode: claim at most half of the victim's queue (else up to 32 - cnt) */
+#define GTAP_STEAL_ONE 4       /* block mode: steal exactly one task (else up to half of the victim's queue,
+                                  at most 16: one runs now, the rest move to the thief's own deque) */
 
 /* Optional configuration; a zero field selects the default.  Pass NULL for
  * all defaults. */
@@ -94,6 +96,9 @@ typedef struct {
     int n_workers;               /* warps (thread mode) or blocks (block mode) in the grid */
     int grid_blocks, threads_per_block;
     float kernel_ms;             /* duration of the last persistent launch (CUDA events) */
+    float pad_;
+    uint64_t cycles_pop, cycles_steal, cycles_exec, cycles_push, cycles_idle;  /* SM cycles per scheduler
+                                    phase, summed over warps (thread mode; tracing counters) */
 } gtap_stats;
 
 /* Structured error report (Sec. 4: capacity exhaustion aborts with a report). */

@@ -161,101 +161,108 @@ __device__ __forceinline__ bool abort_requested(const KParams& P, bool check_hos
 // slots, after Vyukov's bounded queue); never-used IDs come from a bump
 // pointer.  All of it is warp-collective (called by one full warp).
 
-// Enqueue the 32 IDs my_id (one per lane) as one chunk.  The slot is claimed
-// with a fetch-and-add ticket, so contention never makes a push retry; the
-// queue has a slot for every chunk the pool can hold, so the ticket's slot is
-// free as soon as its previous occupant's dequeue has finished (a short,
-// bounded wait).  Returns false only if that wait gives up (an invariant
-// violation, reported as an error).
-__device__ __forceinline__ bool cq_push(const KParams& P, uint32_t my_id) {
+// Chunk queue protocol.  Tickets come from fetch-and-add on cq_enq / cq_deq,
+// so no operation retries under contention.  cq_avail counts the chunks whose
+// enqueue has completed: a dequeuer first reserves chunks from it (undoing an
+// over-reservation), so every dequeue ticket it then takes belongs to an
+// enqueue already in progress, and the wait for that slot's sequence number
+// is short and bounded.  The queue has a slot for every chunk the pool can
+// hold, so an enqueue ticket's slot is free once its previous occupant's
+// dequeue finishes.
+
+// Push k chunks (k * 32 IDs from src[0 .. 32k)) to the global queue (warp-collective).
+__device__ __forceinline__ bool cq_push_many(const KParams& P, const uint32_t* src, int k) {
     const int lane = threadIdx.x & 31;
-    unsigned long long slot = 0;
-    int ok = 0;
-    if (lane == 0) {
-        slot = atomicAdd(&P.ctl->cq_enq.v, 1ull);
-        for (int it = 0; it < (1 << 20); ++it) {
-            if (ld_acquire_u64(&P.cq_seq[slot & P.ncq_mask]) == slot) { ok = 1; break; }
-            __nanosleep(64);
+    unsigned long long t0 = 0;
+    if (lane == 0) t0 = atomicAdd(&P.ctl->cq_enq.v, (unsigned long long)k);
+    t0 = __shfl_sync(0xffffffffu, t0, 0);
+    int ok = 1;
+    for (int j = 0; j < k; ++j) {
+        const unsigned long long slot = t0 + (unsigned long long)j;
+        if (lane == 0) {
+            int ready = 0;
+            for (int it = 0; it < (1 << 20); ++it) {
+                if (ld_acquire_u64(&P.cq_seq[slot & P.ncq_mask]) == slot) { ready = 1; break; }
+                __nanosleep(64);
+            }
+            if (!ready) { raise_error(P, GTAP_ERR_TASK_FAILED, -1, -1, slot); ok = 0; }
         }
-        if (!ok) raise_error(P, GTAP_ERR_TASK_FAILED, -1, -1, slot);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) return false;
+        __stcg(&P.cq_ids[(slot & P.ncq_mask) * kChunk + lane], src[j * kChunk + lane]);
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_u64(&P.cq_seq[slot & P.ncq_mask], slot + 1);
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (!ok) return false;
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    __stcg(&P.cq_ids[(slot & P.ncq_mask) * kChunk + lane], my_id);
-    __threadfence();
     __syncwarp();
-    if (lane == 0) st_release_u64(&P.cq_seq[slot & P.ncq_mask], slot + 1);
+    if (lane == 0) { __threadfence(); atomicAdd(&P.ctl->cq_avail.v, (unsigned long long)k); }
     return true;
 }
 
-// Dequeue one chunk; lane i receives ID i.  Returns false if the queue is empty.
-__device__ __forceinline__ bool cq_pop(const KParams& P, uint32_t* my_id) {
+// Pop up to k chunks into dst[0 .. 32 * got) (warp-collective); returns got.
+__device__ __forceinline__ int cq_pop_many(const KParams& P, uint32_t* dst, int k) {
     const int lane = threadIdx.x & 31;
-    unsigned long long slot = 0;
-    int ok = 0;
+    int got = 0;
+    unsigned long long d0 = 0;
     if (lane == 0) {
-        unsigned long long* deq = &P.ctl->cq_deq.v;
-        unsigned long long pos = ld_cg64(deq);
-        for (int it = 0; it < 1024; ++it) {
-            unsigned long long seq = ld_acquire_u64(&P.cq_seq[pos & P.ncq_mask]);
-            long long dif = (long long)(seq - (pos + 1));
-            if (dif == 0) {
-                unsigned long long got = atomicCAS(deq, pos, pos + 1);
-                if (got == pos) { ok = 1; slot = pos; break; }
-                pos = got;
-            } else if (dif < 0) {
-                break;  // empty
-            } else {
-                pos = ld_cg64(deq);
-            }
-        }
+        const long long a = (long long)atomicAdd(&P.ctl->cq_avail.v, (unsigned long long)(-(long long)k));
+        got = (int)max(0ll, min((long long)k, a));
+        if (got < k) atomicAdd(&P.ctl->cq_avail.v, (unsigned long long)(k - got));
+        if (got > 0) d0 = atomicAdd(&P.ctl->cq_deq.v, (unsigned long long)got);
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (!ok) return false;
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    *my_id = __ldcg(&P.cq_ids[(slot & P.ncq_mask) * kChunk + lane]);
-    __threadfence();
+    got = __shfl_sync(0xffffffffu, got, 0);
+    d0 = __shfl_sync(0xffffffffu, d0, 0);
+    for (int j = 0; j < got; ++j) {
+        const unsigned long long slot = d0 + (unsigned long long)j;
+        int ready = 1;
+        if (lane == 0) {
+            ready = 0;
+            for (int it = 0; it < (1 << 20); ++it) {
+                if (ld_acquire_u64(&P.cq_seq[slot & P.ncq_mask]) == slot + 1) { ready = 1; break; }
+                __nanosleep(64);
+            }
+            if (!ready) raise_error(P, GTAP_ERR_TASK_FAILED, -1, -1, slot);
+        }
+        ready = __shfl_sync(0xffffffffu, ready, 0);
+        if (!ready) return j;
+        dst[j * kChunk + lane] = __ldcg(&P.cq_ids[(slot & P.ncq_mask) * kChunk + lane]);
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_u64(&P.cq_seq[slot & P.ncq_mask], slot + P.ncq_mask + 1);
+    }
     __syncwarp();
-    if (lane == 0) st_release_u64(&P.cq_seq[slot & P.ncq_mask], slot + P.ncq_mask + 1);
-    return true;
+    return got;
 }
 
 // Bring the local free stack up to `need` IDs (warp-collective).  Returns the
 // new top; less than `need` only when the pool is exhausted.
 __device__ __forceinline__ int pool_refill(const KParams& P, uint32_t* fstack, int ftop, int need) {
     const int lane = threadIdx.x & 31;
-    while (ftop < need) {
-        uint32_t id;
-        if (cq_pop(P, &id)) {
-            fstack[ftop + lane] = id;
-            ftop += kChunk;
-            continue;
-        }
+    if (ftop >= need) return ftop;
+    const int k = (need - ftop + kChunk - 1) / kChunk;
+    const int got = cq_pop_many(P, fstack + ftop, k);
+    ftop += got * kChunk;
+    if (got < k) {
+        const int want = (k - got) * kChunk;
         unsigned long long b = 0;
-        if (lane == 0) b = atomicAdd(&P.ctl->bump.v, (unsigned long long)kChunk);
+        if (lane == 0) b = atomicAdd(&P.ctl->bump.v, (unsigned long long)want);
         b = __shfl_sync(0xffffffffu, b, 0);
-        if (b >= P.n_frames) break;
-        unsigned long long avail = P.n_frames - b;
-        int got = avail < (unsigned long long)kChunk ? (int)avail : kChunk;
-        if (lane < got) fstack[ftop + lane] = (uint32_t)(b + lane);
-        ftop += got;
-        if (got < kChunk) break;
+        if (b < P.n_frames) {
+            const int avail = (int)min((unsigned long long)want, P.n_frames - b);
+            for (int i = lane; i < avail; i += 32) fstack[ftop + i] = (uint32_t)(b + i);
+            ftop += avail;
+        }
     }
     __syncwarp();
     return ftop;
 }
 
-// Move chunks beyond `high` back to the global queue (warp-collective).
+// Move whole chunks beyond `high` back to the global queue (warp-collective).
 __device__ __forceinline__ int pool_spill(const KParams& P, uint32_t* fstack, int ftop, int high) {
-    const int lane = threadIdx.x & 31;
-    while (ftop - kChunk >= high) {
-        __syncwarp();
-        uint32_t id = fstack[ftop - kChunk + lane];
-        __syncwarp();
-        if (!cq_push(P, id)) break;
-        ftop -= kChunk;
-    }
+    if (ftop - kChunk < high) return ftop;
+    const int k = (ftop - high) / kChunk;
+    __syncwarp();
+    if (cq_push_many(P, fstack + ftop - k * kChunk, k)) ftop -= k * kChunk;
     return ftop;
 }
 
@@ -451,6 +458,9 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
     int ftop = 0;
     const int fhigh = 32 * (int)P.maxspawn + 2 * kChunk;
     constexpr int kProbes = 8;   // victims probed in parallel per steal attempt (one lane each)
+    // per-phase clock accounting (tracing counters): pop, steal, execute, retain/push, idle
+    unsigned long long cy_pop = 0, cy_steal = 0, cy_exec = 0, cy_push = 0, cy_idle = 0;
+    long long tc0 = clock64();
 
     for (uint32_t iter = 0;; ++iter) {
         if ((iter & 63u) == 0u) {
@@ -510,6 +520,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                 }
             }
         }
+        { const long long t = clock64(); cy_pop += (unsigned long long)(t - tc0); tc0 = t; }
         // ---- StealBatch.  SelectVictimQueue probes kProbes random victims at once (one
         // lane each) and picks the fullest, so an idle warp finds work in one round trip.
         const bool want_steal = (P.steal_policy & GTAP_STEAL_EMPTY) ? (cnt == 0) : (cnt < 32);
@@ -521,8 +532,16 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                 const uint64_t r = rng * 2685821657736338717ull;
                 victim = (int)(((r >> 32) * (unsigned long long)(P.n_workers - 1)) >> 32);
                 if (victim >= wid) ++victim;
-                if (cnt == 0 && Q > 1) vqi = (int)(((r & 0xFFFFFFFFull) * (unsigned long long)Q) >> 32);
-                c = ld_cg_i32(&P.qs[(size_t)victim * Q + vqi].count);
+                if (cnt == 0 && Q > 1) {
+                    // a warp with no batch yet may take any class: read all of the victim's queues
+                    int cc[kMaxQueues];
+#pragma unroll
+                    for (int k = 0; k < kMaxQueues; ++k) cc[k] = (k < Q) ? ld_cg_i32(&P.qs[(size_t)victim * Q + k].count) : -1;
+#pragma unroll
+                    for (int k = 0; k < kMaxQueues; ++k) if (cc[k] > c) { c = cc[k]; vqi = k; }
+                } else {
+                    c = ld_cg_i32(&P.qs[(size_t)victim * Q + vqi].count);
+                }
             }
             int best = c, bl = lane;
 #pragma unroll
@@ -584,11 +603,12 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                 }
             }
         }
+        { const long long t = clock64(); cy_steal += (unsigned long long)(t - tc0); tc0 = t; }
         // ---- Nothing to run: termination test (all roots complete), deadline, backoff.
         if (cnt == 0) {
             ++st_idle;
             int stop = 0;
-            if (lane == 0 && (st_idle & 3ull) == 1ull) {
+            if (lane == 0 && (st_idle & 15ull) == 1ull) {
                 if (ld_cg64(&P.ctl->roots_remaining.v) == 0ull) stop = 1;
                 else if (abort_requested(P, (st_idle & 255ull) == 1ull)) stop = 1;
                 else if (global_ns() > deadline) { raise_error(P, GTAP_ERR_TIMEOUT, -1, wid, P.timeout_ns); stop = 1; }
@@ -596,6 +616,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             if (__shfl_sync(0xffffffffu, stop, 0)) break;
             __nanosleep(backoff);
             backoff = min(backoff * 2, 512);
+            { const long long t = clock64(); cy_idle += (unsigned long long)(t - tc0); tc0 = t; }
             continue;
         }
         backoff = 32;
@@ -625,6 +646,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
         st_spawned += (unsigned)__reduce_add_sync(0xffffffffu, (unsigned)spawned);
         st_tasks += cnt;
         ++st_steps;
+        { const long long t = clock64(); cy_exec += (unsigned long long)(t - tc0); tc0 = t; }
 
         // ---- Return freed records to the local stack; spill the surplus.
         {
@@ -644,7 +666,10 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
         if (nst > 0) {
             int qstar = 0, nq_star = nst;
             if (Q > 1) {
-                int c = (lane < Q) ? ws.cls_count[lane] : -1;
+                // DAQ: the next batch is the class with the most runnable work this warp holds
+                // (staged now plus its own queue), so batches stay both homogeneous and full
+                int c = (lane < Q) ? ws.cls_count[lane] + ws.hint[lane] : -1;
+                if (lane < Q && ws.cls_count[lane] == 0) c = -1;   // only classes with staged tasks can be retained
                 int best = c, bq = lane;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
@@ -653,7 +678,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                     if (oc > best || (oc == best && oq < bq)) { best = oc; bq = oq; }
                 }
                 qstar = __shfl_sync(0xffffffffu, bq, 0);
-                nq_star = __shfl_sync(0xffffffffu, best, 0);
+                nq_star = ws.cls_count[qstar];
             }
             const int nkeep = min(32, nq_star);
             // capacity check per destination queue: uses head/tail, not count (Sec. 5.1.3)
@@ -699,8 +724,10 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                 }
                 __syncwarp();
             }
-            // one fence, then one count increment per destination queue (PushBatch)
-            __threadfence();
+            // one fence, then one count increment per destination queue (PushBatch).  When every
+            // staged task is retained nothing is published to other warps, so no fence is needed:
+            // the warp's own lanes see the records through the warp barrier.
+            if (nkeep < nst) __threadfence();
             __syncwarp();
             if (lane < Q) {
                 int np = ws.push_off[lane];
@@ -721,6 +748,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             cls = qstar;
             __syncwarp();
         }
+        { const long long t = clock64(); cy_push += (unsigned long long)(t - tc0); tc0 = t; }
     }
 
     // Give cached frames back so a later run or another worker could use them (best effort).
@@ -729,7 +757,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
         s.tasks = st_tasks; s.steps = st_steps; s.pops = st_pops; s.popped = st_popped;
         s.steal_attempts = st_sa; s.steals = st_steals; s.stolen = st_stolen; s.idle = st_idle;
         s.pushes = st_pushes; s.pushed = st_pushed; s.spawned = st_spawned;
-        for (int i = 0; i < 5; ++i) s.pad[i] = 0;
+        s.pad[0] = cy_pop; s.pad[1] = cy_steal; s.pad[2] = cy_exec; s.pad[3] = cy_push; s.pad[4] = cy_idle;
         P.stats[wid] = s;
     }
 }
@@ -839,12 +867,14 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
         bs.misc[0] = kNoTask;
         bs.misc[1] = kNoTask;
         bs.misc[2] = __ldcg(&myq->tail0);
+        bs.ctrl[6] = (int)bs.misc[2];   // count upper bound (reset leaves count == tail0)
+        bs.ctrl[7] = 0;                 // head lower bound
     }
     __syncthreads();
 
     unsigned long long st_tasks = 0, st_pops = 0, st_sa = 0, st_steals = 0, st_idle = 0, st_pushes = 0, st_pushed = 0,
                        st_spawned = 0;
-    uint64_t rng = P.seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(bid + 1));
+    uint64_t rng = P.seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(bid + 1)) ^ (0x9E3779B97F4A7C15ull * (uint64_t)(lane + 1));
     const uint64_t deadline = global_ns() + P.timeout_ns;
     int backoff = 32;
     int ftop = 0;
@@ -858,61 +888,124 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
                 if ((iter & 15u) == 0u && abort_requested(P, (iter & 255u) == 0u)) {
                     state = 2;
                 } else if (bs.misc[1] != kNoTask) {
-                    task = bs.misc[1];
+                    task = bs.misc[1];   // the task retained from the previous step
                     bs.misc[1] = kNoTask;
-                } else {
-                    // single-task pop from the owner end
-                    int old = ld_cg_i32(&myq->count);
+                } else if (bs.ctrl[6] > 0) {
+                    // single-task pop from the owner end; ctrl[6] is the owner's upper bound of count
+                    int old = bs.ctrl[6];
                     for (int it = 0; it < 64 && old > 0; ++it) {
-                        int got = atom_cas_acq_i32(&myq->count, old, old - 1);
+                        const int got = atom_cas_acq_i32(&myq->count, old, old - 1);
                         if (got == old) {
-                            uint32_t tl = bs.misc[2] - 1u;
+                            const uint32_t tl = bs.misc[2] - 1u;
                             bs.misc[2] = tl;
                             task = __ldcg(&myring[tl & cap_mask]);
                             ++st_pops;
+                            old -= 1;
                             break;
                         }
                         old = got;
                     }
-                    // single-task steal from a random victim block
-                    if (task == kNoTask && P.n_workers > 1) {
-                        ++st_sa;
-                        rng ^= rng >> 12; rng ^= rng << 25; rng ^= rng >> 27;
-                        uint32_t r = (uint32_t)((rng * 2685821657736338717ull) >> 32);
-                        int victim = (int)(((unsigned long long)r * (P.n_workers - 1)) >> 32);
-                        if (victim >= bid) ++victim;
-                        QState* vq = P.qs + victim;
-                        if (ld_cg_i32(&vq->count) > 0 && atom_cas_acq_i32(&vq->lock, 0, 1) == 0) {
-                            int o = ld_cg_i32(&vq->count);
-                            bool claimed = false;
-                            for (int it = 0; it < 64 && o > 0; ++it) {
-                                int got = atom_cas_acq_i32(&vq->count, o, o - 1);
-                                if (got == o) { claimed = true; break; }
-                                o = got;
-                            }
-                            if (claimed) {
-                                uint32_t hd = __ldcg(&vq->head);
-                                task = __ldcg(&P.rings[(size_t)victim * (cap_mask + 1) + (hd & cap_mask)]);
-                                __threadfence();
-                                __stcg(&vq->head, hd + 1u);
-                                ++st_steals;
-                            }
-                            st_release_i32(&vq->lock, 0);
-                        }
-                    }
-                    if (task == kNoTask) {
-                        ++st_idle;
-                        if (ld_cg64(&P.ctl->roots_remaining.v) == 0ull) state = 2;
-                        else if (global_ns() > deadline) { raise_error(P, GTAP_ERR_TIMEOUT, -1, bid, P.timeout_ns); state = 2; }
-                        else if ((st_idle & 31ull) == 1ull && abort_requested(P, true)) state = 2;
-                    } else {
-                        state = 1;
-                    }
+                    bs.ctrl[6] = max(old, 0);
                 }
-                if (task != kNoTask) state = 1;
             }
             state = __shfl_sync(0xffffffffu, state, 0);
             task = __shfl_sync(0xffffffffu, task, 0);
+            // Steal: warp 0 probes kProbes random victim blocks at once and claims from the
+            // fullest; it keeps one task for this step and moves the rest of its claim
+            // into its own deque (so the work spreads further by stealing from it).
+            if (state == 0 && task == kNoTask && P.n_workers > 1) {
+                constexpr int kProbes = 16;
+                ++st_sa;
+                int c = -1, victim = 0;
+                if (lane < kProbes) {
+                    rng ^= rng >> 12; rng ^= rng << 25; rng ^= rng >> 27;
+                    const uint64_t r = rng * 2685821657736338717ull;
+                    victim = (int)(((r >> 32) * (unsigned long long)(P.n_workers - 1)) >> 32);
+                    if (victim >= bid) ++victim;
+                    c = ld_cg_i32(&P.qs[victim].count);
+                }
+                int best = c, bl = lane;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int oc = __shfl_down_sync(0xffffffffu, best, o);
+                    const int ol = __shfl_down_sync(0xffffffffu, bl, o);
+                    if (oc > best) { best = oc; bl = ol; }
+                }
+                best = __shfl_sync(0xffffffffu, best, 0);
+                bl = __shfl_sync(0xffffffffu, bl, 0);
+                victim = __shfl_sync(0xffffffffu, victim, bl);
+                if (best > 0) {
+                    QState* vq = P.qs + victim;
+                    int claim = 0;
+                    uint32_t hd = 0;
+                    if (lane == 0 && atom_cas_acq_i32(&vq->lock, 0, 1) == 0) {  // try-lock
+                        int old = best;
+                        for (int it = 0; it < 64 && old > 0; ++it) {
+                            const int want = (P.steal_policy & GTAP_STEAL_ONE) ? 1 : min(16, (old + 1) >> 1);
+                            const int got = atom_cas_acq_i32(&vq->count, old, old - want);
+                            if (got == old) { claim = want; break; }
+                            old = got;
+                        }
+                        if (claim > 0) hd = __ldcg(&vq->head);
+                        else st_release_i32(&vq->lock, 0);
+                    }
+                    claim = __shfl_sync(0xffffffffu, claim, 0);
+                    if (claim > 0) {
+                        hd = __shfl_sync(0xffffffffu, hd, 0);
+                        uint32_t v = kNoTask;
+                        if (lane < claim) v = __ldcg(&P.rings[(size_t)victim * (cap_mask + 1) + ((hd + (uint32_t)lane) & cap_mask)]);
+                        const uint32_t used = __reduce_or_sync(0xffffffffu, lane < claim ? v : 0u);
+                        uint32_t zero;
+                        asm volatile("and.b32 %0, %1, 0;" : "=r"(zero) : "r"(used));
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) {
+                            __stcg(&vq->head, hd + (uint32_t)claim + zero);
+                            st_release_i32(&vq->lock, 0);
+                        }
+                        task = __shfl_sync(0xffffffffu, v, 0);
+                        ++st_steals;
+                        if (claim > 1) {
+                            // the own deque is empty here (the pop failed); check room anyway
+                            const uint32_t tl = bs.misc[2];
+                            int room = 1;
+                            if (lane == 0 && tl - (uint32_t)bs.ctrl[7] + (uint32_t)(claim - 1) > cap_mask + 1) {
+                                const uint32_t h2 = __ldcg(&myq->head);
+                                bs.ctrl[7] = (int)h2;
+                                if (tl - h2 + (uint32_t)(claim - 1) > cap_mask + 1) room = 0;
+                            }
+                            room = __shfl_sync(0xffffffffu, room, 0);
+                            if (!room) {
+                                if (lane == 0) raise_error(P, GTAP_ERR_DEQUE_OVERFLOW, -1, bid, cap_mask + 1);
+                                state = 2;
+                            } else {
+                                if (lane >= 1 && lane < claim) __stcg(&myring[(tl + (uint32_t)(lane - 1)) & cap_mask], v);
+                                __threadfence();
+                                __syncwarp();
+                                if (lane == 0) {
+                                    bs.misc[2] = tl + (uint32_t)(claim - 1);
+                                    bs.ctrl[6] += claim - 1;
+                                    atomicAdd(&myq->count, claim - 1);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            if (state == 0 && task == kNoTask) {
+                int st = 0;
+                if (lane == 0) {
+                    ++st_idle;
+                    if ((st_idle & 3ull) == 1ull) {
+                        if (ld_cg64(&P.ctl->roots_remaining.v) == 0ull) st = 2;
+                        else if (global_ns() > deadline) { raise_error(P, GTAP_ERR_TIMEOUT, -1, bid, P.timeout_ns); st = 2; }
+                        else if ((st_idle & 127ull) == 1ull && abort_requested(P, true)) st = 2;
+                    }
+                }
+                state = __shfl_sync(0xffffffffu, st, 0);
+            } else if (task != kNoTask && state != 2) {
+                state = 1;
+            }
             if (state == 1) {
                 ftop = pool_refill(P, bs.fstack, ftop, (int)P.maxspawn);
                 if (lane == 0) {
@@ -931,7 +1024,7 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
                 backoff = 32;
             } else if (state == 0) {
                 if (lane == 0) __nanosleep(backoff);
-                backoff = min(backoff * 2, 2048);
+                backoff = min(backoff * 2, 1024);
             }
             if (lane == 0) bs.ctrl[3] = state;
             __syncwarp();
@@ -982,8 +1075,9 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
                 const int npush = nst - 1;
                 int overflow = 0;
                 uint32_t tl = bs.misc[2];
-                if (npush > 0 && lane == 0) {
-                    uint32_t hd = __ldcg(&myq->head);
+                if (npush > 0 && lane == 0 && tl - (uint32_t)bs.ctrl[7] + (uint32_t)npush > cap_mask + 1) {
+                    const uint32_t hd = __ldcg(&myq->head);
+                    bs.ctrl[7] = (int)hd;
                     if (tl - hd + (uint32_t)npush > cap_mask + 1) overflow = 1;
                 }
                 if (__shfl_sync(0xffffffffu, overflow, 0)) {
@@ -996,6 +1090,7 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
                         bs.misc[1] = bs.staged_id[0];
                         if (npush > 0) {
                             bs.misc[2] = tl + (uint32_t)npush;
+                            bs.ctrl[6] += npush;
                             atomicAdd(&myq->count, npush);
                             ++st_pushes;
                             st_pushed += npush;

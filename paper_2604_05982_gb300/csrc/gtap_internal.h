@@ -94,6 +94,7 @@ struct DevControl {
     Line128 cq_deq;            // chunk-queue dequeue ticket
     Line128 scratch_top;       // bytes taken from the scratch arena
     Line128 inflight;          // serving: roots admitted and not yet completed
+    Line128 cq_avail;          // chunks whose enqueue has completed and that no dequeuer reserved
     alignas(128) ErrorRecord err;
 };
 
@@ -119,7 +120,7 @@ struct RootDesc {
 
 struct WorkerStats {
     unsigned long long tasks, steps, pops, popped, steal_attempts, steals, stolen, idle, pushes, pushed, spawned;
-    unsigned long long pad[5];
+    unsigned long long pad[5];   // thread mode: SM cycles spent in pop, steal, execute, retain/push, idle
 };
 
 // Kernel parameters (passed by value).

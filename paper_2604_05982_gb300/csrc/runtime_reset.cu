@@ -55,6 +55,7 @@ __global__ void reset_kernel(KParams P, int init_cq) {
         P.ctl->bump.v = P.n_roots;
         P.ctl->cq_enq.v = 0;
         P.ctl->cq_deq.v = 0;
+        P.ctl->cq_avail.v = 0;
         P.ctl->scratch_top.v = 0;
         P.ctl->inflight.v = 0;
         P.ctl->err.code = 0;

@@ -18,6 +18,7 @@ GTAP_MODE_BLOCK = 1
 GTAP_STEAL_FILL = 0
 GTAP_STEAL_EMPTY = 1
 GTAP_STEAL_HALF = 2
+GTAP_STEAL_ONE = 4
 
 STATUS = {
     0: "GTAP_OK", 1: "GTAP_ERR_INVALID_ARG", 2: "GTAP_ERR_NO_MEMORY", 3: "GTAP_ERR_POOL_EXHAUSTED",
@@ -46,7 +47,8 @@ class gtap_stats(ctypes.Structure):
         "tasks_executed", "tasks_created", "steps", "pops", "popped", "steal_attempts", "steals", "stolen",
         "idle_iterations", "pushes", "pushed", "frames_high_water", "scratch_used")] + [
         ("n_workers", ctypes.c_int), ("grid_blocks", ctypes.c_int), ("threads_per_block", ctypes.c_int),
-        ("kernel_ms", ctypes.c_float)]
+        ("kernel_ms", ctypes.c_float), ("pad_", ctypes.c_float)] + [
+        (n, ctypes.c_uint64) for n in ("cycles_pop", "cycles_steal", "cycles_exec", "cycles_push", "cycles_idle")]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -1,0 +1,60 @@
+"""Single-workload runs for profiler captures (ncu): python -m paper_2604_05982_gb300.profile_cases CASE ...
+
+Each case runs one workload `--reps` times through the C ABI and prints the
+kernel time of every run.  Used to capture one kernel of one workload with
+ncu at a size that keeps the capture short.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["fib", "nqueens", "tree", "mergesort", "kclique", "fmm"])
+    ap.add_argument("--n", type=int, default=0, help="problem size (fib n, queens n, log2 keys, rmat scale)")
+    ap.add_argument("--queues", type=int, default=1)
+    ap.add_argument("--route", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=2)
+    args = ap.parse_args(argv)
+
+    from . import gtap as G
+    from . import runner
+
+    if args.case == "fib":
+        for _ in range(args.reps):
+            r = runner.fib(args.n or 30, n_queues=args.queues, route=args.route)
+            print("fib", r.values, r.stats["kernel_ms"])
+    elif args.case == "nqueens":
+        for _ in range(args.reps):
+            r = runner.nqueens(args.n or 13, n_queues=args.queues, route=args.route)
+            print("nqueens", r.values, r.stats["kernel_ms"])
+    elif args.case == "tree":
+        for _ in range(args.reps):
+            r = runner.uts(42, n_queues=args.queues, route=args.route)
+            print("tree", r.values, r.stats["kernel_ms"])
+    elif args.case == "mergesort":
+        import numpy as np
+        import torch
+
+        from . import inputs
+        n = 1 << (args.n or 24)
+        keys = inputs.keys_u32(n, seed=1)
+        src = torch.from_numpy(keys.view(np.int32)).cuda()
+        dst = torch.empty_like(src)
+        tmp = torch.empty_like(src)
+        torch.cuda.synchronize()
+        for _ in range(args.reps):
+            r = runner.mergesort_ptrs(src.data_ptr(), dst.data_ptr(), tmp.data_ptr(), n, merge_cutoff=16384)
+            print("mergesort", n, r.stats["kernel_ms"])
+        out = dst.cpu().numpy().view(np.uint32)
+        assert np.all(out[1:] >= out[:-1])
+    else:
+        print(f"case {args.case} is not available in this build", file=sys.stderr)
+        return 2
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

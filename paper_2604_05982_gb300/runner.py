@@ -122,7 +122,7 @@ def integrate(a: float, b: float, eps: float, block: bool = False, **cfg) -> Run
 def mergesort_ptrs(src: int, dst: int, tmp: int, n: int, leaf: int = 4096, merge_cutoff: int = 4096,
                    **cfg) -> RunResult:
     """Sort n uint32 keys at device address src into dst (tmp: n-key scratch)."""
-    with Context(G.GTAP_MODE_BLOCK, 1, **cfg) as c:
+    with Context(G.GTAP_MODE_BLOCK, 1, pool_bytes=256 << 20, **cfg) as c:
         t = c.register("mergesort")
         c.spawn(t, G.gtap_mergesort_args(src, dst, tmp, n, leaf, merge_cutoff))
         c.run()
