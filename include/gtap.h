@@ -210,6 +210,31 @@ typedef struct { double a; double b; double eps; } gtap_integrate_args;
  * Result: none (8 zero bytes). */
 typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; uint32_t leaf; uint32_t merge_cutoff; } gtap_mergesort_args;
 
+/* ------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart to this call.
+ *
+ * gtap_mergesort_noalloc sorts n uint32 keys from src into dst (both device
+ * pointers owned by the caller; src may equal dst) with the block-mode
+ * mergesort above, for callers that cannot allocate device memory: code that
+ * runs while someone else captures a CUDA graph, real-time paths whose memory
+ * is fixed up front, plugins that are handed a stream but own no memory.  All
+ * working memory (key scratch, task records, deques, control words) lives in
+ * one fixed file-scope device array of about 10 MB, which every GPU that loads
+ * the library holds until the process exits; the call makes no cudaMalloc or
+ * cudaFree and uses no allocating library routine.
+ *   - n must be at most 2^20 (1,048,576); larger n returns GTAP_ERR_INVALID_ARG.
+ *   - The first call on a device sets that device up (it looks up the array's
+ *     device address); make that first call before any stream capture.
+ *   - stream is a cudaStream_t (NULL: the legacy default stream).  The call
+ *     returns after the sort has finished on that stream, with the device-side
+ *     status (GTAP_ERR_POOL_EXHAUSTED, GTAP_ERR_DEQUE_OVERFLOW, ...) or GTAP_OK.
+ *   - All calls share the array, which keeps the previous call's contents;
+ *     every run re-initialises what it reads.  Calls whose GPU work overlaps
+ *     (different streams or host threads at the same time) race on the array
+ *     and are not allowed.
+ * ---------------------------------------------------------------------- */
+gtap_status gtap_mergesort_noalloc(const uint32_t* src, uint32_t* dst, uint64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

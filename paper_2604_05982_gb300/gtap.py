@@ -97,6 +97,7 @@ _SIGS = {
     "gtap_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gtap_finalize": (ctypes.c_int, [_P]),
     "gtap_debug_snapshot": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
+    "gtap_mergesort_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P]),
 }
 
 _lib = None
@@ -194,3 +195,11 @@ def gtap_debug_snapshot(ctx: int) -> dict:
     names = ["roots_remaining", "bump", "cq_enq", "cq_deq", "queued", "nonempty_queues", "locks_held",
              "max_count", "abort"]
     return dict(zip(names, list(buf)))
+
+
+def gtap_mergesort_noalloc(src: int, dst: int, n: int, stream: int = 0, raise_on_error: bool = True) -> int:
+    """Sort n uint32 keys (device pointers) without any device allocation; returns the status."""
+    s = load_library().gtap_mergesort_noalloc(src, dst, n, stream or None)
+    if raise_on_error:
+        _check(s, "gtap_mergesort_noalloc")
+    return s
