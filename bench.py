@@ -140,7 +140,7 @@ def run_gpu(args):
     h_ut = ut.spawn(t, G.gtap_uts_args(42, runner.UTS_THRESHOLD_Q0199, 2000, 5, 0, 0))
     ms = runner.Context(G.GTAP_MODE_BLOCK, 1, pool_bytes=256 << 20)
     t = ms.register("mergesort")
-    ms.spawn(t, G.gtap_mergesort_args(src.data_ptr(), dst.data_ptr(), tmp.data_ptr(), n, MSORT_LEAF, 16384))
+    ms.spawn(t, G.gtap_mergesort_args(src.data_ptr(), dst.data_ptr(), tmp.data_ptr(), n, MSORT_LEAF, 65536))
     launches_per_step = 6   # each run: reset kernel + persistent scheduler kernel
 
     def step():

@@ -98,7 +98,9 @@ typedef struct {
     float kernel_ms;             /* duration of the last persistent launch (CUDA events) */
     float pad_;
     uint64_t cycles_pop, cycles_steal, cycles_exec, cycles_push, cycles_idle;  /* SM cycles per scheduler
-                                    phase, summed over warps (thread mode; tracing counters) */
+                                    phase summed over workers (tracing counters); block mode reports
+                                    acquire in cycles_pop, task bodies in cycles_exec, the post-step in
+                                    cycles_push and cycles_steal = 0 */
 } gtap_stats;
 
 /* Structured error report (Sec. 4: capacity exhaustion aborts with a report). */

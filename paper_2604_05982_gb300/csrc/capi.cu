@@ -480,10 +480,10 @@ gtap_status gtap_wait(gtap_ctx* c, uint64_t timeout_ms) {
         st.pushes += x.pushes;
         st.pushed += x.pushed;
         st.tasks_created += x.spawned;
-        if (c->mode == GTAP_MODE_THREAD) {
-            st.cycles_pop += x.pad[0]; st.cycles_steal += x.pad[1]; st.cycles_exec += x.pad[2];
-            st.cycles_push += x.pad[3]; st.cycles_idle += x.pad[4];
-        }
+        // thread mode: pop, steal, execute, retain/push, idle; block mode: acquire (pop or
+        // steal), -, body, post-step, idle
+        st.cycles_pop += x.pad[0]; st.cycles_steal += x.pad[1]; st.cycles_exec += x.pad[2];
+        st.cycles_push += x.pad[3]; st.cycles_idle += x.pad[4];
     }
     st.tasks_created += c->launched_roots;
     st.frames_high_water = std::min<uint64_t>(c->ctl_pinned->bump.v, c->launched_frames);

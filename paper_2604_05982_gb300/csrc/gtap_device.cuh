@@ -880,6 +880,9 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
     int ftop = 0;
     const int fhigh = (int)P.maxspawn + 2 * kChunk;
 
+    // per-phase clock accounting (thread 0): acquire, body, post-step, idle
+    unsigned long long cy_acq = 0, cy_body = 0, cy_post = 0, cy_idle = 0;
+    long long tb0 = clock64();
     for (uint32_t iter = 0;; ++iter) {
         if (warp == 0) {
             uint32_t task = kNoTask;
@@ -1031,12 +1034,18 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
         }
         __syncthreads();
         const int state = bs.ctrl[3];
+        if (t == 0) {
+            const long long tn = clock64();
+            if (state == 1) cy_acq += (unsigned long long)(tn - tb0); else cy_idle += (unsigned long long)(tn - tb0);
+            tb0 = tn;
+        }
         if (state == 2) break;
         if (state == 1) {
             BTaskCtx c(P, bs, bid);
             Dispatch::run(c);
         }
         __syncthreads();
+        if (t == 0 && state == 1) { const long long tn = clock64(); cy_body += (unsigned long long)(tn - tb0); tb0 = tn; }
         if (warp == 0 && state == 1) {
             ++st_tasks;
             if (lane == 0) {
@@ -1099,6 +1108,7 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
                 }
             }
             __syncwarp();
+            if (t == 0) { const long long tn = clock64(); cy_post += (unsigned long long)(tn - tb0); tb0 = tn; }
         }
     }
     if (t == 0) {
@@ -1106,7 +1116,7 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
         s.tasks = st_tasks; s.steps = st_tasks; s.pops = st_pops; s.popped = st_pops;
         s.steal_attempts = st_sa; s.steals = st_steals; s.stolen = st_steals; s.idle = st_idle;
         s.pushes = st_pushes; s.pushed = st_pushed; s.spawned = st_spawned;
-        for (int i = 0; i < 5; ++i) s.pad[i] = 0;
+        s.pad[0] = cy_acq; s.pad[1] = 0; s.pad[2] = cy_body; s.pad[3] = cy_post; s.pad[4] = cy_idle;
         P.stats[bid] = s;
     }
 }

@@ -26,7 +26,7 @@ struct BlockDispatch {
 };
 
 template <unsigned PSET, int BS>
-__global__ void __launch_bounds__(BS) block_kernel(KParams P) {
+__global__ void __launch_bounds__(BS, 768 / BS) block_kernel(KParams P) {
     extern __shared__ __align__(16) char smem[];
     block_mode_loop<BlockDispatch<PSET, BS>>(P, smem, BS);
 }
@@ -58,7 +58,7 @@ int block_kernel_maxspawn(unsigned pset, int bs) {
 
 size_t block_prog_smem(unsigned pset, int bs) {
     size_t b = 0;
-    if (pset & PS_MSORT) b = std::max(b, (size_t)(2 * kMsTile * 4 + 8 * 260));
+    if (pset & PS_MSORT) b = std::max(b, (size_t)(2 * kMsPadded * 4 + 8 * 260));
     if (pset & PS_INTEGRATE_BLK) b = std::max(b, (size_t)(8 * bs));
     return b;
 }

@@ -40,57 +40,117 @@ __device__ __forceinline__ unsigned long long merge_path(unsigned long long na, 
     return lo;
 }
 
-// One block merges A[0,na) and B[0,nb) (na + nb <= BS * 16) into out, via shared memory.
+// Shared-memory index with one pad word per 32, so that a warp accessing
+// element t*ITEMS + k (a stride of ITEMS words) touches 32 different banks.
+__device__ __forceinline__ int padx(int i) { return i + (i >> 5); }
+constexpr int kMsPadded = kMsTile + kMsTile / 32;
+
+// Merge path inside shared memory (padded layout): how many of A's elements
+// precede output position d; equal keys come from A first.
+__device__ __forceinline__ int smem_merge_path(const uint32_t* sa, int na, const uint32_t* sb, int nb, int d,
+                                               int a0, int b0) {
+    int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sa[padx(a0 + mid)] <= sb[padx(b0 + d - 1 - mid)]) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Serially merge `count` outputs starting at (i, j) of runs A = s[a0 .. a0+na),
+// B = s[b0 .. b0+nb) into registers.  Branch-free: each output is a select,
+// and only the run that advanced is read again (one shared load per output).
+template <int ITEMS>
+__device__ __forceinline__ void smem_serial_merge(const uint32_t* s, int a0, int na, int b0, int nb, int i, int j,
+                                                  int count, uint32_t (&out)[ITEMS]) {
+    uint32_t av = (i < na) ? s[padx(a0 + i)] : 0xFFFFFFFFu;
+    uint32_t bv = (j < nb) ? s[padx(b0 + j)] : 0xFFFFFFFFu;
+    bool a_ok = i < na, b_ok = j < nb;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        const bool takeA = a_ok && (!b_ok || av <= bv);
+        out[k] = takeA ? av : bv;
+        i += takeA ? 1 : 0;
+        j += takeA ? 0 : 1;
+        const bool more = takeA ? (i < na) : (j < nb);
+        const int at = takeA ? a0 + i : b0 + j;
+        const uint32_t nv = (more && k + 1 < count) ? s[padx(at)] : 0xFFFFFFFFu;
+        if (takeA) { av = nv; a_ok = more; } else { bv = nv; b_ok = more; }
+    }
+}
+
+// One block merges A[0,na) and B[0,nb) (na + nb <= kMsTile) into out, via shared memory.
 template <int BS>
 __device__ void block_merge_tile(const uint32_t* A, int na, const uint32_t* B, int nb, uint32_t* out, uint32_t* sh) {
     constexpr int kItems = kMsTile / BS;
-    uint32_t* shin = sh;
-    uint32_t* shout = sh + kMsTile;
+    uint32_t* shin = sh;                 // padded: A at [0, na), B at [na, na + nb)
+    uint32_t* shout = sh + kMsPadded;    // padded
     const int t = threadIdx.x;
-    for (int i = t; i < na; i += BS) shin[i] = __ldcg(A + i);
-    for (int i = t; i < nb; i += BS) shin[na + i] = __ldcg(B + i);
+    for (int i = t; i < na; i += BS) shin[padx(i)] = __ldcg(A + i);
+    for (int i = t; i < nb; i += BS) shin[padx(na + i)] = __ldcg(B + i);
     __syncthreads();
     const int total = na + nb;
     const int d0 = min(t * kItems, total), d1 = min(d0 + kItems, total);
-    int lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (shin[mid] <= shin[na + d0 - 1 - mid]) lo = mid + 1; else hi = mid;
-    }
-    int i = lo, j = d0 - lo;
+    const int i = smem_merge_path(shin, na, shin, nb, d0, 0, na);
+    uint32_t v[kItems];
+    smem_serial_merge<kItems>(shin, 0, na, na, nb, i, d0 - i, d1 - d0, v);
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        if (d0 + k < d1) {
-            const bool takeA = (j >= nb) || (i < na && shin[i] <= shin[na + j]);
-            shout[d0 + k] = takeA ? shin[i++] : shin[na + j++];
-        }
-    }
+    for (int k = 0; k < kItems; ++k)
+        if (d0 + k < d1) shout[padx(d0 + k)] = v[k];
     __syncthreads();
-    for (int k = t; k < total; k += BS) out[k] = shout[k];
+    for (int k = t; k < total; k += BS) out[k] = shout[padx(k)];
     __syncthreads();
 }
 
-// Bitonic sort of n <= 4096 keys in shared memory (padded to a power of two).
-template <int BS>
-__device__ void block_sort_leaf(const uint32_t* src, int n, uint32_t* dst, uint32_t* sh) {
-    const int t = threadIdx.x;
-    int np = 1;
-    while (np < n) np <<= 1;
-    for (int i = t; i < np; i += BS) sh[i] = (i < n) ? __ldg(src + i) : 0xFFFFFFFFu;
-    __syncthreads();
-    for (int k = 2; k <= np; k <<= 1) {
+// Sort of n <= 4096 keys by one block: every thread sorts kItems keys in
+// registers with a bitonic network, then log2(BS) rounds of merging pairs of
+// sorted runs in shared memory, each thread producing kItems outputs of a
+// merge located by a merge-path search.
+template <int ITEMS>
+__device__ __forceinline__ void sort_registers(uint32_t (&x)[ITEMS]) {
+#pragma unroll
+    for (int k = 2; k <= ITEMS; k <<= 1) {
+#pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int p = t; p < (np >> 1); p += BS) {
-                const int i = 2 * j * (p / j) + (p % j);
-                const int q = i + j;
-                const uint32_t a = sh[i], b = sh[q];
-                const bool up = (i & k) == 0;
-                if ((a > b) == up) { sh[i] = b; sh[q] = a; }
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const uint32_t a = x[i], b = x[l];
+                    if ((a > b) == up) { x[i] = b; x[l] = a; }
+                }
             }
-            __syncthreads();
         }
     }
-    for (int i = t; i < n; i += BS) dst[i] = sh[i];
+}
+
+template <int BS>
+__device__ void block_sort_leaf(const uint32_t* src, int n, uint32_t* dst, uint32_t* sh) {
+    constexpr int kItems = kMsMaxLeaf / BS;
+    const int t = threadIdx.x;
+    for (int i = t; i < kMsMaxLeaf; i += BS) sh[padx(i)] = (i < n) ? __ldg(src + i) : 0xFFFFFFFFu;
+    __syncthreads();
+    uint32_t x[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) x[k] = sh[padx(t * kItems + k)];
+    sort_registers<kItems>(x);
+    for (int run = kItems; run < kMsMaxLeaf; run <<= 1) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) sh[padx(t * kItems + k)] = x[k];
+        __syncthreads();
+        const int o = t * kItems;
+        const int base = o & ~(2 * run - 1);
+        const int d = o - base;
+        const int i = smem_merge_path(sh, run, sh, run, d, base, base + run);
+        smem_serial_merge<kItems>(sh, base, run, base + run, run, i, d - i, kItems, x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) sh[padx(t * kItems + k)] = x[k];
+    __syncthreads();
+    for (int i = t; i < n; i += BS) dst[i] = sh[padx(i)];
     __syncthreads();
 }
 
@@ -129,7 +189,7 @@ __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uin
                                   unsigned long long a_hi, unsigned long long b_lo, unsigned long long b_hi,
                                   unsigned long long out_lo) {
     uint32_t* sh = c.prog_smem<uint32_t>();
-    unsigned long long* split = reinterpret_cast<unsigned long long*>(sh + 2 * kMsTile);
+    unsigned long long* split = reinterpret_cast<unsigned long long*>(sh + 2 * kMsPadded);
     const uint32_t* X = msort_buf(e, flags & 1u);
     uint32_t* Y = msort_buf(e, flags & 2u);
     const unsigned long long na = a_hi - a_lo, nb = b_hi - b_lo, total = na + nb;
@@ -146,10 +206,60 @@ __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uin
         split[1] = na;
     }
     __syncthreads();
-    for (int k = 0; k < tiles; ++k) {
+    // Software pipeline over the piece's tiles: the next tile's keys are loaded
+    // into registers while the current tile is merged from shared memory, and
+    // merged keys go straight from registers to global memory.
+    constexpr int kItems = kMsTile / BS;
+    const int t = threadIdx.x;
+    uint32_t* buf[2] = {sh, sh + kMsPadded};
+    uint32_t pre[kItems];
+    auto tile_bounds = [&](int k, int& tna, int& tnb, unsigned long long& i0, unsigned long long& j0) {
         const unsigned long long d0 = (unsigned long long)k * kMsTile, d1 = min(total, d0 + kMsTile);
-        const unsigned long long i0 = split[k], i1 = split[k + 1];
-        block_merge_tile<BS>(A + i0, (int)(i1 - i0), B + (d0 - i0), (int)((d1 - i1) - (d0 - i0)), Y + out_lo + d0, sh);
+        i0 = split[k];
+        const unsigned long long i1 = split[k + 1];
+        j0 = d0 - i0;
+        tna = (int)(i1 - i0);
+        tnb = (int)((d1 - i1) - j0);
+    };
+    auto load_tile = [&](int k) {   // element t + r*BS of the tile's input (A part, then B part)
+        int tna, tnb;
+        unsigned long long i0, j0;
+        tile_bounds(k, tna, tnb, i0, j0);
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int e = t + r * BS;
+            pre[r] = (e < tna) ? __ldcg(A + i0 + e) : ((e < tna + tnb) ? __ldcg(B + j0 + (e - tna)) : 0u);
+        }
+    };
+    auto store_tile = [&](uint32_t* dstb) {
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) dstb[padx(t + r * BS)] = pre[r];
+    };
+    load_tile(0);
+    store_tile(buf[0]);
+    __syncthreads();
+    for (int k = 0; k < tiles; ++k) {
+        if (k + 1 < tiles) load_tile(k + 1);   // in flight during this tile's merge
+        int tna, tnb;
+        unsigned long long i0, j0;
+        tile_bounds(k, tna, tnb, i0, j0);
+        const uint32_t* cur = buf[k & 1];
+        const int ttot = tna + tnb;
+        const int d0 = min(t * kItems, ttot), d1 = min(d0 + kItems, ttot);
+        const int i = smem_merge_path(cur, tna, cur, tnb, d0, 0, tna);
+        uint32_t v[kItems];
+        smem_serial_merge<kItems>(cur, 0, tna, tna, tnb, i, d0 - i, d1 - d0, v);
+        uint32_t* o = Y + out_lo + (unsigned long long)k * kMsTile + d0;
+        if (d1 - d0 == kItems && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+#pragma unroll
+            for (int r = 0; r < kItems; r += 4) __stcg(reinterpret_cast<uint4*>(o + r), make_uint4(v[r], v[r + 1], v[r + 2], v[r + 3]));
+        } else {
+#pragma unroll
+            for (int r = 0; r < kItems; ++r)
+                if (d0 + r < d1) o[r] = v[r];
+        }
+        if (k + 1 < tiles) store_tile(buf[(k + 1) & 1]);
+        __syncthreads();
     }
 }
 

@@ -46,7 +46,7 @@ def main(argv=None):
         tmp = torch.empty_like(src)
         torch.cuda.synchronize()
         for _ in range(args.reps):
-            r = runner.mergesort_ptrs(src.data_ptr(), dst.data_ptr(), tmp.data_ptr(), n, merge_cutoff=16384)
+            r = runner.mergesort_ptrs(src.data_ptr(), dst.data_ptr(), tmp.data_ptr(), n, merge_cutoff=65536)
             print("mergesort", n, r.stats["kernel_ms"])
         out = dst.cpu().numpy().view(np.uint32)
         assert np.all(out[1:] >= out[:-1])
