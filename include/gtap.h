@@ -212,6 +212,28 @@ typedef struct { double a; double b; double eps; } gtap_integrate_args;
  * Result: none (8 zero bytes). */
 typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; uint32_t leaf; uint32_t merge_cutoff; } gtap_mergesort_args;
 
+/* k-clique counting by graph orientation (Sec. 6.4.2), thread mode ("kclique").
+ * off/adj/src are the oriented DAG from gtap_kclique_orient (device, caller
+ * owned, read only during the run).  Every DAG edge (u, v) of the root's
+ * range (all edges: [0, m)) counts the
+ * (k-2)-cliques of C = N+(u) n N+(v); a set larger than split_threshold
+ * (<= 32, default 32) is materialised in the context's scratch arena
+ * (gtap_config.scratch_bytes) and forked into child tasks over its branch
+ * range, smaller ones are counted in the lane with 32-bit bitsets.
+ * route 1: queue = recursion depth mod n_queues.  k in [3, 16].  Result: uint64 count. */
+typedef struct { const int64_t* off; const int32_t* adj; const int32_t* src;
+                 int64_t edge_begin, edge_end;   /* the root counts DAG edges [edge_begin, edge_end) */
+                 int32_t k; int32_t split_threshold; int32_t route; int32_t pad; } gtap_kclique_args;
+
+/* Orient an undirected simple graph (each edge once, as m int32 pairs in edges,
+ * device) by the order (degree, id): outputs off[n+1] (int64), adj[m] (out-lists
+ * sorted by id) and src[m] (the source vertex of each DAG edge), all device and
+ * caller owned.  work: device int32 scratch of at least 4*n + 16 elements.
+ * Stream-ordered on stream; returns after completion.  Errors:
+ * GTAP_ERR_INVALID_ARG (bad sizes, or an out-list longer than 8192). */
+gtap_status gtap_kclique_orient(const int32_t* edges, int64_t m, int64_t n, int64_t* off, int32_t* adj,
+                                int32_t* src, int32_t* work, void* stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart to this call.
  *

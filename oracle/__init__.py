@@ -61,6 +61,7 @@ def _load():
                 "orc_kclique": (u64, [i64, P, i64, i32, i32, P]),
                 "orc_orient": (None, [i64, P, i64, i32, P, P]),
                 "orc_kclique_brute": (u64, [i32, P, i64, i32]),
+                "orc_kclique_edge_range": (u64, [i64, P, i64, i32, i32, i64, i64]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -153,3 +154,9 @@ def orient(n: int, edges: np.ndarray, order: str = "degree"):
 def kclique_brute(n: int, edges: np.ndarray, k: int) -> int:
     edges = np.ascontiguousarray(edges, dtype=np.int32)
     return int(_load().orc_kclique_brute(n, _ptr(edges), edges.shape[0], k))
+
+
+def kclique_edge_range(n: int, edges: np.ndarray, k: int, lo: int, hi: int, order: str = "degree") -> int:
+    """Sum of per-DAG-edge k-clique counts over DAG edges [lo, hi)."""
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    return int(_load().orc_kclique_edge_range(n, _ptr(edges), edges.shape[0], k, {"degree": 0, "id": 1}[order], lo, hi))

@@ -323,6 +323,24 @@ uint64_t orc_kclique(int64_t n, const int32_t* edges, int64_t m, int k, int orde
     return total;
 }
 
+// Sum of the per-edge counts over DAG edges [lo, hi) (same edge order as above),
+// so a sample of a large graph can be checked without counting every edge.
+uint64_t orc_kclique_edge_range(int64_t n, const int32_t* edges, int64_t m, int k, int order_mode, int64_t lo,
+                                int64_t hi) {
+    Dag g = orient(n, edges, m, order_mode);
+    uint64_t total = 0;
+    int64_t u = 0;
+    for (int64_t p = lo; p < hi && p < m; ++p) {
+        while (g.off[u + 1] <= p) ++u;
+        int32_t v = g.adj[p];
+        std::vector<int32_t> C = intersect(g.adj.data() + g.off[u], g.off[u + 1] - g.off[u],
+                                           g.adj.data() + g.off[v], g.off[v + 1] - g.off[v]);
+        if (k == 3) total += C.size();
+        else if ((int)C.size() >= k - 2) total += count_in(g, C, k - 2);
+    }
+    return total;
+}
+
 // The oriented DAG itself (CSR), for checking the GPU orientation step.
 // off has n+1 entries, adj has m entries.
 void orc_orient(int64_t n, const int32_t* edges, int64_t m, int order_mode, int64_t* off, int32_t* adj) {

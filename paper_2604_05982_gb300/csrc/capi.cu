@@ -29,6 +29,7 @@ const ProgInfo kPrograms[] = {
     {"nqueens", GTAP_MODE_THREAD, T_NQUEENS, PS_NQUEENS},
     {"uts", GTAP_MODE_THREAD, T_UTS, PS_UTS},
     {"integrate", GTAP_MODE_THREAD, T_INTEGRATE, PS_INTEGRATE},
+    {"kclique", GTAP_MODE_THREAD, T_KCLIQUE_ROOT, PS_KCLIQUE},
     {"mergesort", GTAP_MODE_BLOCK, T_MSORT, PS_MSORT},
     {"integrate_block", GTAP_MODE_BLOCK, T_INTEGRATE_BLK, PS_INTEGRATE_BLK},
 };
@@ -297,6 +298,21 @@ static gtap_status make_root(gtap_ctx* c, int type, const void* args, size_t nby
         if (!(a.eps > 0.0)) return GTAP_ERR_INVALID_ARG;
         double p[4] = {a.a, a.b, a.eps, 0.0};
         put(p, sizeof(p));
+        return GTAP_OK;
+    }
+    case T_KCLIQUE_ROOT: {
+        if (nbytes != sizeof(gtap_kclique_args)) return GTAP_ERR_INVALID_ARG;
+        gtap_kclique_args a;
+        std::memcpy(&a, args, sizeof(a));
+        if (a.split_threshold == 0) a.split_threshold = 32;
+        if (a.k < 3 || a.k > 16 || a.split_threshold < 2 || a.split_threshold > 32 || a.edge_begin < 0 ||
+            a.edge_end < a.edge_begin || a.edge_end >= (1ll << 32) ||
+            (a.edge_end > a.edge_begin && (!a.off || !a.adj || !a.src)))
+            return GTAP_ERR_INVALID_ARG;
+        struct { uint32_t root, lo, hi, pad; unsigned long long acc, local; } p{
+            root_index, (uint32_t)a.edge_begin, (uint32_t)a.edge_end, 0u, 0ull, 0ull};
+        put(&p, sizeof(p));
+        std::memcpy(d->env, &a, sizeof(a));
         return GTAP_OK;
     }
     case T_INTEGRATE_BLK: {

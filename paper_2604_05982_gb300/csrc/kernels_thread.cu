@@ -24,6 +24,12 @@ struct ThreadDispatch {
         case T_INTEGRATE:
             if constexpr ((PSET & PS_INTEGRATE) != 0) { integrate_step(c); return; }
             break;
+        case T_KCLIQUE_ROOT:
+            if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_range_step(c); return; }
+            break;
+        case T_KCLIQUE_SET:
+            if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_set_step(c); return; }
+            break;
         default:
             break;
         }
@@ -39,7 +45,7 @@ __global__ void __launch_bounds__(256) thread_kernel(KParams P) {
     thread_mode_loop<ThreadDispatch<PSET>>(P, smem + (size_t)wib * thread_warp_smem((int)P.maxspawn));
 }
 
-#define GTAP_THREAD_SETS(X) X(PS_FIB) X(PS_NQUEENS) X(PS_UTS) X(PS_INTEGRATE) X(PS_THREAD_ALL)
+#define GTAP_THREAD_SETS(X) X(PS_FIB) X(PS_NQUEENS) X(PS_UTS) X(PS_INTEGRATE) X(PS_KCLIQUE) X(PS_THREAD_ALL)
 
 static const void* thread_kernel_fn(unsigned pset) {
     switch (pset) {
@@ -51,7 +57,7 @@ static const void* thread_kernel_fn(unsigned pset) {
 }
 
 unsigned thread_kernel_pset(unsigned registered) {
-    const unsigned singles[] = {PS_FIB, PS_NQUEENS, PS_UTS, PS_INTEGRATE};
+    const unsigned singles[] = {PS_FIB, PS_NQUEENS, PS_UTS, PS_INTEGRATE, PS_KCLIQUE};
     for (unsigned s : singles)
         if (registered != 0 && (registered & ~s) == 0) return s;
     return PS_THREAD_ALL;
@@ -63,6 +69,7 @@ int thread_kernel_maxspawn(unsigned pset) {
     if (pset & PS_NQUEENS) m = max(m, 16);
     if (pset & PS_UTS) m = max(m, 8);
     if (pset & PS_INTEGRATE) m = max(m, 2);
+    if (pset & PS_KCLIQUE) m = max(m, kKcFan);
     return m;
 }
 

@@ -177,3 +177,227 @@ __device__ __forceinline__ void integrate_step(TaskCtx& c) {
 }
 
 }  // namespace gtap
+
+namespace gtap {
+
+// ---------------------------------------------------------------------------
+// k-clique counting by orientation (Sec. 6.4.2).  For a DAG edge (u, v),
+// C = N+(u) n N+(v); count(S, 1) = |S|, count(S, j) = sum over w in S of
+// count(S n N+(w), j - 1).  A set of at most `thr` (<= 32) vertices is counted
+// inside the lane with 32-bit adjacency bitsets; a larger one is written to
+// the scratch arena and forked over its branch range (the paper's split on the
+// spawn-time estimate |C|).
+//
+// Records (64 bytes):
+//   KC range [16] root, lo, hi, pad   [32] acc  [40] local
+//   KC set   [16] root, j  [24] set pointer  [32] len, lo  [40] hi, pad  [48] acc  [56] local
+struct KcRangeSpawn { uint32_t root, lo, hi, pad; unsigned long long acc, local; };
+struct KcSetSpawn { uint32_t root, j; unsigned long long set; uint32_t len, lo, hi, pad; unsigned long long acc, local; };
+constexpr uint32_t kKcRangeSlotAcc = 4, kKcRangeLocal = 40;
+constexpr uint32_t kKcSetSlotAcc = 6, kKcSetLocal = 56;
+constexpr int kKcFan = 8;          // children per split
+constexpr int kKcMaxThr = 32;      // in-lane sets use 32-bit bitsets
+
+__device__ __forceinline__ const gtap_kclique_args& kc_env(const KParams& P, uint32_t root) {
+    return *reinterpret_cast<const gtap_kclique_args*>(P.root_desc[root].env);
+}
+
+// Read-only adjacency (never written during a run): non-coherent cached loads.
+struct AdjLoad { __device__ int operator()(const int* p) const { return __ldg(p); } };
+// Sets in the scratch arena are written during the run: loads through L2.
+struct SetLoad { __device__ int operator()(const int* p) const { return __ldcg(p); } };
+
+// |a n b| for sorted lists; the first `cap` common elements go to out (if not null).
+template <class LA, class LB>
+static __device__ int kc_intersect(const int* a, int na, LA la, const int* b, int nb, LB lb, int* out, int cap) {
+    int cnt = 0;
+    if (na == 0 || nb == 0) return 0;
+    if ((long long)na * 8 < nb) {
+        // gallop the short list's elements through the long one
+        int lo = 0;
+        for (int i = 0; i < na && lo < nb; ++i) {
+            const int x = la(a + i);
+            int step = 1, hi = lo;
+            while (hi < nb && lb(b + hi) < x) { lo = hi + 1; hi = lo + step; step <<= 1; }
+            if (hi > nb) hi = nb;
+            while (lo < hi) { const int mid = (lo + hi) >> 1; if (lb(b + mid) < x) lo = mid + 1; else hi = mid; }
+            if (lo < nb && lb(b + lo) == x) { if (out && cnt < cap) out[cnt] = x; ++cnt; ++lo; }
+        }
+    } else if ((long long)nb * 8 < na) {
+        int lo = 0;
+        for (int i = 0; i < nb && lo < na; ++i) {
+            const int x = lb(b + i);
+            int step = 1, hi = lo;
+            while (hi < na && la(a + hi) < x) { lo = hi + 1; hi = lo + step; step <<= 1; }
+            if (hi > na) hi = na;
+            while (lo < hi) { const int mid = (lo + hi) >> 1; if (la(a + mid) < x) lo = mid + 1; else hi = mid; }
+            if (lo < na && la(a + lo) == x) { if (out && cnt < cap) out[cnt] = x; ++cnt; ++lo; }
+        }
+    } else {
+        int i = 0, j = 0;
+        int x = la(a), y = lb(b);
+        while (true) {
+            if (x < y) { if (++i == na) break; x = la(a + i); }
+            else if (y < x) { if (++j == nb) break; y = lb(b + j); }
+            else {
+                if (out && cnt < cap) out[cnt] = x;
+                ++cnt;
+                if (++i == na || ++j == nb) break;
+                x = la(a + i); y = lb(b + j);
+            }
+        }
+    }
+    return cnt;
+}
+
+// count(S, j) for |S| <= 32 inside one lane.
+static __device__ unsigned long long kc_count_small(const int* S, int ns, int j, const int64_t* off, const int* adj) {
+    if (j == 1) return (unsigned long long)ns;
+    if (ns < j) return 0;
+    uint32_t row[kKcMaxThr];
+    for (int a = 0; a < ns; ++a) {
+        // row[a] = members of S that are out-neighbours of S[a]
+        const long long b0 = (long long)__ldg(reinterpret_cast<const long long*>(off) + S[a]);
+        const int len = (int)((long long)__ldg(reinterpret_cast<const long long*>(off) + S[a] + 1) - b0);
+        const int* nb = adj + b0;
+        uint32_t bits = 0;
+        if (len > 4 * ns) {
+            int lo = 0;
+            for (int b = 0; b < ns && lo < len; ++b) {
+                const int x = S[b];
+                int hi = len;
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (__ldg(nb + mid) < x) lo = mid + 1; else hi = mid; }
+                if (lo < len && __ldg(nb + lo) == x) { bits |= 1u << b; ++lo; }
+            }
+        } else {
+            int i = 0, b = 0;
+            while (i < len && b < ns) {
+                const int x = __ldg(nb + i), y = S[b];
+                if (x < y) ++i;
+                else if (y < x) ++b;
+                else { bits |= 1u << b; ++i; ++b; }
+            }
+        }
+        row[a] = bits;
+    }
+    const uint32_t full = (ns == 32) ? 0xFFFFFFFFu : ((1u << ns) - 1u);
+    if (j == 2) {
+        unsigned long long t = 0;
+        for (int a = 0; a < ns; ++a) t += (unsigned)__popc(row[a]);
+        return t;
+    }
+    // depth-first over choices; M = candidates at a level, R = those not yet tried there
+    uint32_t M[16], R[16];
+    M[0] = full;
+    R[0] = full;
+    int l = 0;
+    unsigned long long total = 0;
+    while (l >= 0) {
+        if (R[l] == 0) { --l; continue; }
+        const int a = __ffs(R[l]) - 1;
+        R[l] &= R[l] - 1;
+        const uint32_t mn = M[l] & row[a];
+        const int rem = j - l - 1;
+        if (rem == 1) {
+            total += (unsigned)__popc(mn);
+        } else if (rem == 2) {
+            for (uint32_t w = mn; w; w &= w - 1) total += (unsigned)__popc(mn & row[__ffs(w) - 1]);
+        } else if (__popc(mn) >= rem) {
+            ++l;
+            M[l] = mn;
+            R[l] = mn;
+        }
+    }
+    return total;
+}
+
+__device__ __forceinline__ int* kc_scratch_alloc(TaskCtx& c, int n) {
+    const unsigned long long bytes = ((unsigned long long)n * 4 + 15) & ~15ull;
+    const unsigned long long at = atomicAdd(&c.P.ctl->scratch_top.v, bytes);
+    if (at + bytes > c.P.scratch_bytes) { c.fail(GTAP_ERR_TASK_FAILED, at + bytes); return nullptr; }
+    return reinterpret_cast<int*>(c.P.scratch + at);
+}
+
+__device__ __forceinline__ int kc_queue(const gtap_kclique_args& e, int depth) { return e.route ? depth : 0; }
+__device__ __forceinline__ long long kc_off(const gtap_kclique_args& e, long long v) {
+    return __ldg(reinterpret_cast<const long long*>(e.off) + v);
+}
+
+static __device__ void kclique_range_step(TaskCtx& c) {
+    const KcRangeSpawn a = c.load<KcRangeSpawn>();
+    const gtap_kclique_args& e = kc_env(c.P, a.root);
+    if (c.pc() != 0) { c.ret(a.acc + a.local); return; }
+    const uint32_t n = a.hi - a.lo;
+    if (n > (uint32_t)kKcFan) {
+        const uint32_t per = (n + kKcFan - 1) / kKcFan;
+        for (uint32_t s = a.lo; s < a.hi; s += per)
+            c.spawn(T_KCLIQUE_ROOT, kKcRangeSlotAcc, kc_queue(e, 0), KcRangeSpawn{a.root, s, min(a.hi, s + per), 0u, 0ull, 0ull},
+                    kFlagAccumulate);
+        c.join(1, kc_queue(e, 0));
+        return;
+    }
+    const int thr = e.split_threshold;
+    const int need = e.k - 2;
+    unsigned long long local = 0;
+    int C[kKcMaxThr];
+    for (uint32_t ei = a.lo; ei < a.hi; ++ei) {
+        const int u = __ldg(e.src + ei), v = __ldg(e.adj + ei);
+        const long long ou = kc_off(e, u), ov = kc_off(e, v);
+        const int nu = (int)(kc_off(e, u + 1) - ou), nv = (int)(kc_off(e, v + 1) - ov);
+        const int cn = kc_intersect(e.adj + ou, nu, AdjLoad{}, e.adj + ov, nv, AdjLoad{}, C, thr);
+        if (need == 1) { local += (unsigned)cn; continue; }
+        if (cn < need) continue;
+        if (cn <= thr) { local += kc_count_small(C, cn, need, e.off, e.adj); continue; }
+        int* S = kc_scratch_alloc(c, cn);
+        if (!S) return;
+        kc_intersect(e.adj + ou, nu, AdjLoad{}, e.adj + ov, nv, AdjLoad{}, S, cn);
+        // the child adds its count into this range task's accumulator
+        c.spawn(T_KCLIQUE_SET, kKcRangeSlotAcc, kc_queue(e, 1),
+                KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)cn, 0u, (uint32_t)cn, 0u, 0ull, 0ull},
+                kFlagAccumulate);
+    }
+    if (c.nspawned == 0) { c.ret(local); return; }
+    st_cg64(c.frame + kKcRangeLocal, local);
+    c.join(1, kc_queue(e, 0));
+}
+
+static __device__ void kclique_set_step(TaskCtx& c) {
+    const KcSetSpawn a = c.load<KcSetSpawn>();
+    const gtap_kclique_args& e = kc_env(c.P, a.root);
+    if (c.pc() != 0) { c.ret(a.acc + a.local); return; }
+    const int depth = e.k - 2 - (int)a.j + 1;
+    const int* set = reinterpret_cast<const int*>(a.set);
+    const uint32_t n = a.hi - a.lo;
+    if (n > (uint32_t)kKcFan) {
+        const uint32_t per = (n + kKcFan - 1) / kKcFan;
+        for (uint32_t s = a.lo; s < a.hi; s += per)
+            c.spawn(T_KCLIQUE_SET, kKcSetSlotAcc, kc_queue(e, depth),
+                    KcSetSpawn{a.root, a.j, a.set, a.len, s, min(a.hi, s + per), 0u, 0ull, 0ull}, kFlagAccumulate);
+        c.join(1, kc_queue(e, depth));
+        return;
+    }
+    const int thr = e.split_threshold;
+    const int need = (int)a.j - 1;
+    unsigned long long local = 0;
+    int C[kKcMaxThr];
+    for (uint32_t i = a.lo; i < a.hi; ++i) {
+        const int w = __ldcg(set + i);
+        const long long ow = kc_off(e, w);
+        const int nw = (int)(kc_off(e, w + 1) - ow);
+        const int cn = kc_intersect(set, (int)a.len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, C, thr);
+        if (need == 1) { local += (unsigned)cn; continue; }
+        if (cn < need) continue;
+        if (cn <= thr) { local += kc_count_small(C, cn, need, e.off, e.adj); continue; }
+        int* S = kc_scratch_alloc(c, cn);
+        if (!S) return;
+        kc_intersect(set, (int)a.len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, S, cn);
+        c.spawn(T_KCLIQUE_SET, kKcSetSlotAcc, kc_queue(e, depth + 1),
+                KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)cn, 0u, (uint32_t)cn, 0u, 0ull, 0ull},
+                kFlagAccumulate);
+    }
+    if (c.nspawned == 0) { c.ret(local); return; }
+    st_cg64(c.frame + kKcSetLocal, local);
+    c.join(1, kc_queue(e, depth));
+}
+
+}  // namespace gtap

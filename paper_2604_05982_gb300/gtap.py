@@ -76,6 +76,12 @@ class gtap_integrate_args(ctypes.Structure):
     _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
+class gtap_kclique_args(ctypes.Structure):
+    _fields_ = [("off", ctypes.c_void_p), ("adj", ctypes.c_void_p), ("src", ctypes.c_void_p),
+                ("edge_begin", ctypes.c_int64), ("edge_end", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("split_threshold", ctypes.c_int32), ("route", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class gtap_mergesort_args(ctypes.Structure):
     _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("tmp", ctypes.c_void_p),
                 ("n", ctypes.c_uint64), ("leaf", ctypes.c_uint32), ("merge_cutoff", ctypes.c_uint32)]
@@ -98,6 +104,7 @@ _SIGS = {
     "gtap_finalize": (ctypes.c_int, [_P]),
     "gtap_debug_snapshot": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "gtap_mergesort_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P]),
+    "gtap_kclique_orient": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -203,3 +210,8 @@ def gtap_mergesort_noalloc(src: int, dst: int, n: int, stream: int = 0, raise_on
     if raise_on_error:
         _check(s, "gtap_mergesort_noalloc")
     return s
+
+
+def gtap_kclique_orient(edges: int, m: int, n: int, off: int, adj: int, src: int, work: int, stream: int = 0) -> None:
+    """Orient an undirected graph on the GPU (device pointers; see gtap.h)."""
+    _check(load_library().gtap_kclique_orient(edges, m, n, off, adj, src, work, stream or None), "gtap_kclique_orient")

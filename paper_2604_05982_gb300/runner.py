@@ -127,3 +127,40 @@ def mergesort_ptrs(src: int, dst: int, tmp: int, n: int, leaf: int = 4096, merge
         c.spawn(t, G.gtap_mergesort_args(src, dst, tmp, n, leaf, merge_cutoff))
         c.run()
         return RunResult([], c.stats())
+
+
+class DeviceGraph:
+    """An undirected graph oriented on the GPU (gtap_kclique_orient); device buffers held as torch tensors."""
+
+    def __init__(self, n: int, edges, stream: int = 0):
+        import numpy as np
+        import torch
+        e = torch.as_tensor(np.ascontiguousarray(edges, dtype=np.int32)).reshape(-1, 2).cuda()
+        m = int(e.shape[0])
+        self.n, self.m = n, m
+        self.edges = e
+        self.off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        self.adj = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+        self.src = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+        self.work = torch.empty(4 * n + 16, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        G.gtap_kclique_orient(e.data_ptr(), m, n, self.off.data_ptr(), self.adj.data_ptr(), self.src.data_ptr(),
+                              self.work.data_ptr(), stream)
+
+    def args(self, k: int, split_threshold: int = 32, route: int = 0, begin: int = 0, end: int | None = None):
+        return G.gtap_kclique_args(self.off.data_ptr(), self.adj.data_ptr(), self.src.data_ptr(), begin,
+                                   self.m if end is None else end, k, split_threshold, route, 0)
+
+
+def kclique(graphs, k: int, split_threshold: int = 32, n_queues: int = 1, route: int = 0,
+            scratch_bytes: int = 1 << 30, ranges=None, **cfg) -> RunResult:
+    """Count k-cliques of one or more DeviceGraphs in one persistent launch (one root each)."""
+    graphs = [graphs] if isinstance(graphs, DeviceGraph) else list(graphs)
+    with Context(G.GTAP_MODE_THREAD, n_queues, scratch_bytes=scratch_bytes, **cfg) as c:
+        t = c.register("kclique")
+        hs = []
+        for i, g in enumerate(graphs):
+            b, e = (0, g.m) if ranges is None else ranges[i]
+            hs.append(c.spawn(t, g.args(k, split_threshold, route, b, e), queue=0))
+        c.run()
+        return RunResult([c.result_u64(h) for h in hs], c.stats())

@@ -1,0 +1,92 @@
+"""k-clique on the GPU: orientation and counts bit-exact against the oracle (GPU)."""
+import math
+from itertools import combinations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_05982_gb300 import inputs, runner
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _graph(n, edges):
+    return runner.DeviceGraph(n, edges)
+
+
+@pytest.mark.parametrize("scale", [6, 10, 13])
+def test_orientation_matches_oracle(scale):
+    n, e = inputs.rmat_graph(scale, 16, seed=7)
+    g = _graph(n, e)
+    off, adj = oracle.orient(n, e)
+    assert np.array_equal(g.off.cpu().numpy(), off)
+    assert np.array_equal(g.adj[: g.m].cpu().numpy(), adj)
+    src = g.src[: g.m].cpu().numpy()
+    assert np.array_equal(src, np.repeat(np.arange(n), np.diff(off)))
+
+
+def test_orientation_edge_cases():
+    # isolated vertices, a single edge, a star (hub with many leaves: long out-lists of the leaves' side)
+    e = np.array([[0, 5]], dtype=np.int32)
+    g = _graph(8, e)
+    off, adj = oracle.orient(8, e)
+    assert np.array_equal(g.off.cpu().numpy(), off) and np.array_equal(g.adj[:1].cpu().numpy(), adj)
+    star = np.array([[0, i] for i in range(1, 3000)], dtype=np.int32)
+    g = _graph(3000, star)
+    off, adj = oracle.orient(3000, star)
+    assert np.array_equal(g.off.cpu().numpy(), off) and np.array_equal(g.adj[: g.m].cpu().numpy(), adj)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_counts_random_graphs_brute_force(k):
+    for seed in range(3):
+        n, e = inputs.random_graph(26, 0.5, seed)
+        want = oracle.kclique_brute(n, e, k)
+        assert runner.kclique(_graph(n, e), k).values == [want]
+
+
+def test_complete_graph_forces_heavy_splits():
+    n = 48
+    e = np.array(list(combinations(range(n), 2)), dtype=np.int32)
+    g = _graph(n, e)
+    for k, thr in [(4, 32), (5, 8), (6, 4), (7, 32)]:
+        assert runner.kclique(g, k, split_threshold=thr).values == [math.comb(n, k)]
+
+
+@pytest.mark.parametrize("thr,q,route", [(32, 1, 0), (4, 1, 0), (2, 1, 0), (32, 4, 1), (8, 3, 1)])
+def test_rmat_counts(thr, q, route):
+    n, e = inputs.rmat_graph(11, 16, seed=7)
+    g = _graph(n, e)
+    for k in (3, 4, 5):
+        want = oracle.kclique(n, e, k)
+        r = runner.kclique(g, k, split_threshold=thr, n_queues=q, route=route)
+        assert r.values == [want], (k, thr, q)
+
+
+def test_batched_graphs_one_launch():
+    graphs, wants = [], []
+    for i in range(12):
+        scale = 7 + i % 4
+        n, e = inputs.rmat_graph(scale, 16, seed=7 + i)
+        graphs.append(_graph(n, e))
+        wants.append(oracle.kclique(n, e, 4))
+    r = runner.kclique(graphs, 4)
+    assert r.values == wants
+    # each instance alone gives the same count as in the batch
+    assert runner.kclique(graphs[5], 4).values == [wants[5]]
+
+
+def test_scale20_sampled_edge_ranges():
+    n, e = inputs.rmat_graph(20, 16, seed=7)
+    g = _graph(n, e)
+    rng = np.random.default_rng(0)
+    ranges = []
+    for _ in range(4):
+        lo = int(rng.integers(0, g.m - 512))
+        ranges.append((lo, lo + 512))
+    ranges.append((g.m - 300, g.m))   # the last edges (highest-degree sources)
+    r = runner.kclique([g] * len(ranges), 5, ranges=ranges)
+    want = [oracle.kclique_edge_range(n, e, 5, lo, hi) for lo, hi in ranges]
+    assert r.values == want

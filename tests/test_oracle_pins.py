@@ -248,3 +248,12 @@ def test_keys_u32_low_bits():
     k = inputs.keys_u32(4, seed=0)
     want = [int(h, 16) & 0xFFFFFFFF for _, h in _read_golden("splitmix64_seed0.txt")]
     assert k[:3].tolist() == want
+
+
+def test_kclique_edge_range_sums_per_edge_counts():
+    n, edges = inputs.rmat_graph(9, 16, seed=5)
+    total, pe = oracle.kclique(n, edges, 4, per_edge=True)
+    m = len(edges)
+    assert oracle.kclique_edge_range(n, edges, 4, 0, m) == total
+    for lo, hi in [(0, 10), (37, 400), (m - 5, m)]:
+        assert oracle.kclique_edge_range(n, edges, 4, lo, hi) == int(pe[lo:hi].sum())
