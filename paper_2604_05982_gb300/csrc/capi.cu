@@ -304,8 +304,8 @@ static gtap_status make_root(gtap_ctx* c, int type, const void* args, size_t nby
         if (nbytes != sizeof(gtap_kclique_args)) return GTAP_ERR_INVALID_ARG;
         gtap_kclique_args a;
         std::memcpy(&a, args, sizeof(a));
-        if (a.split_threshold == 0) a.split_threshold = 32;
-        if (a.k < 3 || a.k > 16 || a.split_threshold < 2 || a.split_threshold > 32 || a.edge_begin < 0 ||
+        if (a.split_threshold == 0) a.split_threshold = 64;
+        if (a.k < 3 || a.k > 16 || a.split_threshold < 2 || a.split_threshold > 64 || a.edge_begin < 0 ||
             a.edge_end < a.edge_begin || a.edge_end >= (1ll << 32) ||
             (a.edge_end > a.edge_begin && (!a.off || !a.adj || !a.src)))
             return GTAP_ERR_INVALID_ARG;

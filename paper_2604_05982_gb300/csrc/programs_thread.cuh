@@ -196,7 +196,7 @@ struct KcSetSpawn { uint32_t root, j; unsigned long long set; uint32_t len, lo, 
 constexpr uint32_t kKcRangeSlotAcc = 4, kKcRangeLocal = 40;
 constexpr uint32_t kKcSetSlotAcc = 6, kKcSetLocal = 56;
 constexpr int kKcFan = 8;          // children per split
-constexpr int kKcMaxThr = 32;      // in-lane sets use 32-bit bitsets
+constexpr int kKcMaxThr = 64;      // in-lane sets use 64-bit bitsets
 
 __device__ __forceinline__ const gtap_kclique_args& kc_env(const KParams& P, uint32_t root) {
     return *reinterpret_cast<const gtap_kclique_args*>(P.root_desc[root].env);
@@ -250,24 +250,24 @@ static __device__ int kc_intersect(const int* a, int na, LA la, const int* b, in
     return cnt;
 }
 
-// count(S, j) for |S| <= 32 inside one lane.
+// count(S, j) for |S| <= 64 inside one lane, with 64-bit adjacency bitsets.
 static __device__ unsigned long long kc_count_small(const int* S, int ns, int j, const int64_t* off, const int* adj) {
     if (j == 1) return (unsigned long long)ns;
     if (ns < j) return 0;
-    uint32_t row[kKcMaxThr];
+    unsigned long long row[kKcMaxThr];
     for (int a = 0; a < ns; ++a) {
         // row[a] = members of S that are out-neighbours of S[a]
         const long long b0 = (long long)__ldg(reinterpret_cast<const long long*>(off) + S[a]);
         const int len = (int)((long long)__ldg(reinterpret_cast<const long long*>(off) + S[a] + 1) - b0);
         const int* nb = adj + b0;
-        uint32_t bits = 0;
+        unsigned long long bits = 0;
         if (len > 4 * ns) {
             int lo = 0;
             for (int b = 0; b < ns && lo < len; ++b) {
                 const int x = S[b];
                 int hi = len;
                 while (lo < hi) { const int mid = (lo + hi) >> 1; if (__ldg(nb + mid) < x) lo = mid + 1; else hi = mid; }
-                if (lo < len && __ldg(nb + lo) == x) { bits |= 1u << b; ++lo; }
+                if (lo < len && __ldg(nb + lo) == x) { bits |= 1ull << b; ++lo; }
             }
         } else {
             int i = 0, b = 0;
@@ -275,34 +275,34 @@ static __device__ unsigned long long kc_count_small(const int* S, int ns, int j,
                 const int x = __ldg(nb + i), y = S[b];
                 if (x < y) ++i;
                 else if (y < x) ++b;
-                else { bits |= 1u << b; ++i; ++b; }
+                else { bits |= 1ull << b; ++i; ++b; }
             }
         }
         row[a] = bits;
     }
-    const uint32_t full = (ns == 32) ? 0xFFFFFFFFu : ((1u << ns) - 1u);
+    const unsigned long long full = (ns == 64) ? ~0ull : ((1ull << ns) - 1ull);
     if (j == 2) {
         unsigned long long t = 0;
-        for (int a = 0; a < ns; ++a) t += (unsigned)__popc(row[a]);
+        for (int a = 0; a < ns; ++a) t += (unsigned)__popcll(row[a]);
         return t;
     }
     // depth-first over choices; M = candidates at a level, R = those not yet tried there
-    uint32_t M[16], R[16];
+    unsigned long long M[16], R[16];
     M[0] = full;
     R[0] = full;
     int l = 0;
     unsigned long long total = 0;
     while (l >= 0) {
         if (R[l] == 0) { --l; continue; }
-        const int a = __ffs(R[l]) - 1;
+        const int a = __ffsll((long long)R[l]) - 1;
         R[l] &= R[l] - 1;
-        const uint32_t mn = M[l] & row[a];
+        const unsigned long long mn = M[l] & row[a];
         const int rem = j - l - 1;
         if (rem == 1) {
-            total += (unsigned)__popc(mn);
+            total += (unsigned)__popcll(mn);
         } else if (rem == 2) {
-            for (uint32_t w = mn; w; w &= w - 1) total += (unsigned)__popc(mn & row[__ffs(w) - 1]);
-        } else if (__popc(mn) >= rem) {
+            for (unsigned long long w = mn; w; w &= w - 1) total += (unsigned)__popcll(mn & row[__ffsll((long long)w) - 1]);
+        } else if (__popcll(mn) >= rem) {
             ++l;
             M[l] = mn;
             R[l] = mn;

@@ -147,12 +147,12 @@ class DeviceGraph:
         G.gtap_kclique_orient(e.data_ptr(), m, n, self.off.data_ptr(), self.adj.data_ptr(), self.src.data_ptr(),
                               self.work.data_ptr(), stream)
 
-    def args(self, k: int, split_threshold: int = 32, route: int = 0, begin: int = 0, end: int | None = None):
+    def args(self, k: int, split_threshold: int = 64, route: int = 0, begin: int = 0, end: int | None = None):
         return G.gtap_kclique_args(self.off.data_ptr(), self.adj.data_ptr(), self.src.data_ptr(), begin,
                                    self.m if end is None else end, k, split_threshold, route, 0)
 
 
-def kclique(graphs, k: int, split_threshold: int = 32, n_queues: int = 1, route: int = 0,
+def kclique(graphs, k: int, split_threshold: int = 64, n_queues: int = 1, route: int = 0,
             scratch_bytes: int = 1 << 30, ranges=None, **cfg) -> RunResult:
     """Count k-cliques of one or more DeviceGraphs in one persistent launch (one root each)."""
     graphs = [graphs] if isinstance(graphs, DeviceGraph) else list(graphs)
