@@ -95,8 +95,8 @@ typedef struct {
     uint64_t scratch_used;       /* bytes taken from the scratch arena */
     int n_workers;               /* warps (thread mode) or blocks (block mode) in the grid */
     int grid_blocks, threads_per_block;
-    float kernel_ms;             /* duration of the last persistent launch (CUDA events) */
-    float pad_;
+    float kernel_ms;             /* duration of the last persistent kernel (CUDA events on its stream) */
+    float run_ms;                /* the whole last run: root upload + reset kernel + persistent kernel */
     uint64_t cycles_pop, cycles_steal, cycles_exec, cycles_push, cycles_idle;  /* SM cycles per scheduler
                                     phase summed over workers (tracing counters); block mode reports
                                     acquire in cycles_pop, task bodies in cycles_exec, the post-step in
@@ -163,6 +163,16 @@ gtap_status gtap_last_error(gtap_ctx* ctx, gtap_error_info* out);
 
 /* Forget the queued roots (the next gtap_spawn_root starts a new batch). */
 gtap_status gtap_clear_roots(gtap_ctx* ctx);
+
+/* Capture one run of the currently queued roots (root upload, reset kernel,
+ * persistent kernel) as a CUDA graph; later gtap_run calls replay the graph
+ * instead of issuing the steps one by one, until the queued roots change
+ * (gtap_spawn_root or gtap_clear_roots drop the graph).  Capture happens on a
+ * stream the context owns (capture cannot use the legacy default stream);
+ * replays run there too and gtap_wait waits for them.  Batching roots plus
+ * graph replay is the "many instances, one launch" form of the runtime.
+ * Errors: GTAP_ERR_INVALID_ARG (no roots), GTAP_ERR_BUSY, GTAP_ERR_CUDA. */
+gtap_status gtap_capture_graph(gtap_ctx* ctx);
 
 /* Diagnostic snapshot of the device scheduler state after a run (for
  * post-mortem of an error or timeout).  Fills up to n of: [0] roots

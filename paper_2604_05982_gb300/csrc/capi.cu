@@ -90,10 +90,20 @@ struct gtap_ctx {
     uint32_t launched_workers = 0;
     int launched_grid = 0;
     uint64_t launched_frames = 0;
-    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // whole run (root upload, reset, kernel)
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;         // the persistent kernel alone
     gtap_stats last_stats{};
     gtap_error_info last_err{};
     bool cq_initialised = false;
+    // CUDA-graph replay of a captured run
+    cudaStream_t own_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool graph_valid = false;
+    uint32_t graph_roots = 0, graph_workers = 0;
+    int graph_grid = 0;
+    uint64_t graph_frames = 0;
+    cudaStream_t run_stream = nullptr;   // stream of the launch in flight
 };
 
 extern "C" {
@@ -116,7 +126,17 @@ const char* gtap_status_string(gtap_status s) {
     return "unknown status";
 }
 
+static void drop_graph(gtap_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_valid = false;
+}
+
 static gtap_status free_all(gtap_ctx* c) {
+    drop_graph(c);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
     if (c->own_arena && c->arena) cudaFree(c->arena);
     if (c->root_desc_pinned) cudaFreeHost(c->root_desc_pinned);
     if (c->host_abort) cudaFreeHost(c->host_abort);
@@ -125,6 +145,8 @@ static gtap_status free_all(gtap_ctx* c) {
     if (c->stats_pinned) cudaFreeHost(c->stats_pinned);
     if (c->ev_start) cudaEventDestroy(c->ev_start);
     if (c->ev_stop) cudaEventDestroy(c->ev_stop);
+    if (c->ev_k0) cudaEventDestroy(c->ev_k0);
+    if (c->ev_k1) cudaEventDestroy(c->ev_k1);
     delete c;
     return GTAP_OK;
 }
@@ -223,7 +245,8 @@ gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, con
               cudaHostAlloc(reinterpret_cast<void**>(&c->ctl_pinned), sizeof(DevControl), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(reinterpret_cast<void**>(&c->roots_pinned), (size_t)cfg.max_roots * sizeof(RootEntry), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(reinterpret_cast<void**>(&c->stats_pinned), (size_t)c->n_workers_max * sizeof(WorkerStats), cudaHostAllocDefault) == cudaSuccess &&
-              cudaEventCreate(&c->ev_start) == cudaSuccess && cudaEventCreate(&c->ev_stop) == cudaSuccess;
+              cudaEventCreate(&c->ev_start) == cudaSuccess && cudaEventCreate(&c->ev_stop) == cudaSuccess &&
+              cudaEventCreate(&c->ev_k0) == cudaSuccess && cudaEventCreate(&c->ev_k1) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -353,6 +376,7 @@ gtap_status gtap_spawn_root(gtap_ctx* c, int type, const void* args, size_t args
     if (s != GTAP_OK) return s;
     c->pending_roots.push_back(d);
     if (out_handle) *out_handle = idx;
+    drop_graph(c);
     return GTAP_OK;
 }
 
@@ -361,14 +385,88 @@ gtap_status gtap_clear_roots(gtap_ctx* c) {
     if (c->running) return GTAP_ERR_BUSY;
     c->pending_roots.clear();
     c->have_results = false;
+    drop_graph(c);
     return GTAP_OK;
 }
+
+struct LaunchPlan {
+    KParams P;
+    unsigned pset;
+    size_t smem;
+    int grid;
+};
+
+static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp, bool capturing = false);
 
 gtap_status gtap_run(gtap_ctx* c) {
     if (!c) return GTAP_ERR_INVALID_ARG;
     if (c->running) return GTAP_ERR_BUSY;
     const uint32_t nroots = (uint32_t)c->pending_roots.size();
     if (nroots == 0) return GTAP_ERR_INVALID_ARG;
+    if (c->graph_valid) {
+        // replay the captured run (root upload + reset + persistent kernel)
+        *c->host_abort = 0;
+        cudaStream_t s = c->own_stream;
+        cudaEventRecord(c->ev_start, s);
+        if (cudaGraphLaunch(c->graph_exec, s) != cudaSuccess) { cudaGetLastError(); return GTAP_ERR_CUDA; }
+        cudaEventRecord(c->ev_stop, s);
+        c->running = true;
+        c->have_results = false;
+        c->run_stream = s;
+        c->launched_roots = c->graph_roots;
+        c->launched_workers = c->graph_workers;
+        c->launched_grid = c->graph_grid;
+        c->launched_frames = c->graph_frames;
+        return GTAP_OK;
+    }
+    LaunchPlan lp;
+    cudaStream_t s = c->stream;
+    cudaEventRecord(c->ev_start, s);
+    gtap_status st = plan_and_enqueue(c, s, &lp);
+    if (st != GTAP_OK) return st;
+    cudaEventRecord(c->ev_stop, s);
+    c->running = true;
+    c->have_results = false;
+    c->run_stream = s;
+    c->launched_roots = nroots;
+    c->launched_workers = lp.P.n_workers;
+    c->launched_grid = lp.grid;
+    c->launched_frames = lp.P.n_frames;
+    return GTAP_OK;
+}
+
+gtap_status gtap_capture_graph(gtap_ctx* c) {
+    if (!c) return GTAP_ERR_INVALID_ARG;
+    if (c->running) return GTAP_ERR_BUSY;
+    if (c->pending_roots.empty()) return GTAP_ERR_INVALID_ARG;
+    drop_graph(c);
+    if (!c->own_stream && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) return GTAP_ERR_CUDA;
+    // make sure earlier work on the user stream is done before capturing the first replay's inputs
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return GTAP_ERR_CUDA;
+    LaunchPlan lp;
+    if (cudaStreamBeginCapture(c->own_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GTAP_ERR_CUDA;
+    gtap_status st = plan_and_enqueue(c, c->own_stream, &lp, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->own_stream, &g);
+    if (st != GTAP_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess || !g) { cudaGetLastError(); return GTAP_ERR_CUDA; }
+    if (cudaGraphInstantiate(&c->graph_exec, g, 0) != cudaSuccess) { cudaGetLastError(); cudaGraphDestroy(g); return GTAP_ERR_CUDA; }
+    c->graph = g;
+    c->graph_valid = true;
+    c->graph_roots = (uint32_t)c->pending_roots.size();
+    c->graph_workers = lp.P.n_workers;
+    c->graph_grid = lp.grid;
+    c->graph_frames = lp.P.n_frames;
+    return GTAP_OK;
+}
+
+static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp, bool capturing) {
+    // inside a capture the kernel-timing events become event-record nodes of the graph
+    auto record = [&](cudaEvent_t ev) {
+        if (capturing) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+        else cudaEventRecord(ev, s);
+    };
+    const uint32_t nroots = (uint32_t)c->pending_roots.size();
 
     KParams P{};
     unsigned pset;
@@ -431,11 +529,10 @@ gtap_status gtap_run(gtap_ctx* c) {
 
     std::memcpy(c->root_desc_pinned, c->pending_roots.data(), nroots * sizeof(RootDesc));
     *c->host_abort = 0;
-    cudaStream_t s = c->stream;
     if (cudaMemcpyAsync(c->root_desc, c->root_desc_pinned, nroots * sizeof(RootDesc), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return GTAP_ERR_CUDA;
     if (launch_reset(P, 1, s) != cudaSuccess) return GTAP_ERR_CUDA;
-    cudaEventRecord(c->ev_start, s);
+    record(c->ev_k0);
     cudaError_t e = (c->mode == GTAP_MODE_THREAD)
                         ? launch_thread_kernel(pset, P, grid, c->threads_per_block, smem, s)
                         : launch_block_kernel(pset, c->threads_per_block, P, grid, smem, s);
@@ -443,13 +540,11 @@ gtap_status gtap_run(gtap_ctx* c) {
         cudaGetLastError();
         return GTAP_ERR_CUDA;
     }
-    cudaEventRecord(c->ev_stop, s);
-    c->running = true;
-    c->have_results = false;
-    c->launched_roots = nroots;
-    c->launched_workers = P.n_workers;
-    c->launched_grid = grid;
-    c->launched_frames = n_frames;
+    record(c->ev_k1);
+    lp->P = P;
+    lp->pset = pset;
+    lp->smem = smem;
+    lp->grid = grid;
     return GTAP_OK;
 }
 
@@ -474,9 +569,10 @@ gtap_status gtap_wait(gtap_ctx* c, uint64_t timeout_ms) {
         std::this_thread::sleep_for(std::chrono::microseconds(ms < 2 ? 20 : 200));
     }
     c->running = false;
-    float kms = 0.f;
-    cudaEventElapsedTime(&kms, c->ev_start, c->ev_stop);
-    cudaStream_t s = c->stream;
+    float kms = 0.f, rms = 0.f;
+    cudaEventElapsedTime(&kms, c->ev_k0, c->ev_k1);
+    cudaEventElapsedTime(&rms, c->ev_start, c->ev_stop);
+    cudaStream_t s = c->run_stream;
     if (cudaMemcpyAsync(c->ctl_pinned, c->ctl, sizeof(DevControl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(c->roots_pinned, c->roots, c->launched_roots * sizeof(RootEntry), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(c->stats_pinned, c->stats, c->launched_workers * sizeof(WorkerStats), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -508,6 +604,7 @@ gtap_status gtap_wait(gtap_ctx* c, uint64_t timeout_ms) {
     st.grid_blocks = c->launched_grid;
     st.threads_per_block = c->threads_per_block;
     st.kernel_ms = kms;
+    st.run_ms = rms;
     c->last_stats = st;
     c->last_err.code = c->ctl_pinned->err.code;
     c->last_err.task_type = c->ctl_pinned->err.task_type;

@@ -47,7 +47,7 @@ class gtap_stats(ctypes.Structure):
         "tasks_executed", "tasks_created", "steps", "pops", "popped", "steal_attempts", "steals", "stolen",
         "idle_iterations", "pushes", "pushed", "frames_high_water", "scratch_used")] + [
         ("n_workers", ctypes.c_int), ("grid_blocks", ctypes.c_int), ("threads_per_block", ctypes.c_int),
-        ("kernel_ms", ctypes.c_float), ("pad_", ctypes.c_float)] + [
+        ("kernel_ms", ctypes.c_float), ("run_ms", ctypes.c_float)] + [
         (n, ctypes.c_uint64) for n in ("cycles_pop", "cycles_steal", "cycles_exec", "cycles_push", "cycles_idle")]
 
     def as_dict(self):
@@ -100,6 +100,7 @@ _SIGS = {
     "gtap_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gtap_stats)]),
     "gtap_last_error": (ctypes.c_int, [_P, ctypes.POINTER(gtap_error_info)]),
     "gtap_clear_roots": (ctypes.c_int, [_P]),
+    "gtap_capture_graph": (ctypes.c_int, [_P]),
     "gtap_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gtap_finalize": (ctypes.c_int, [_P]),
     "gtap_debug_snapshot": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
@@ -190,6 +191,10 @@ def gtap_last_error(ctx: int) -> gtap_error_info:
 
 def gtap_clear_roots(ctx: int) -> None:
     _check(load_library().gtap_clear_roots(ctx), "gtap_clear_roots")
+
+
+def gtap_capture_graph(ctx: int) -> None:
+    _check(load_library().gtap_capture_graph(ctx), "gtap_capture_graph")
 
 
 def gtap_finalize(ctx: int) -> None:

@@ -69,6 +69,9 @@ class Context:
     def clear(self):
         G.gtap_clear_roots(self.ctx)
 
+    def capture(self):
+        G.gtap_capture_graph(self.ctx)
+
     def close(self):
         if self.ctx:
             G.gtap_finalize(self.ctx)

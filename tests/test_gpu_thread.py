@@ -114,3 +114,18 @@ def test_deque_overflow_reports_error():
         c.spawn(t, G.gtap_nqueens_args(12, 0))
         status = c.run(raise_on_error=False)
         assert status == G.GTAP_ERR_DEQUE_OVERFLOW
+
+
+def test_graph_replay_same_results_and_reset():
+    with runner.Context(G.GTAP_MODE_THREAD, 4) as c:
+        t = c.register("nqueens")
+        hs = [c.spawn(t, G.gtap_nqueens_args(n, 1)) for n in (6, 9, 11, 12)]
+        c.capture()
+        for _ in range(4):
+            c.run()
+            assert [c.result_u64(h) for h in hs] == [oracle.nqueens(n)[0] for n in (6, 9, 11, 12)]
+            assert c.stats()["kernel_ms"] > 0 and c.stats()["run_ms"] >= c.stats()["kernel_ms"]
+        # a new root drops the graph; the next run is a plain launch with the new batch
+        h2 = c.spawn(t, G.gtap_nqueens_args(8, 1))
+        c.run()
+        assert c.result_u64(h2) == 92 and c.result_u64(hs[1]) == 352
