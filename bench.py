@@ -283,6 +283,131 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+SERVE_REQUESTS = 20000
+SERVE_RATE = 5000.0
+
+
+def _serve_trace(n_req, rate, seed=11):
+    """Poisson arrivals and the served mix: fib n in [20,32], N-Queens n in [8,12],
+    4-clique on an R-MAT graph of scale in [10,14], hashed tree with root branching in [100,2000]."""
+    from paper_2604_05982_gb300 import inputs
+    arrivals, u = inputs.poisson_trace(n_req, rate, seed)
+    v = inputs.u01(seed ^ 0x7E57, 0, n_req)
+    kinds = np.minimum((u * 4).astype(int), 3)
+    reqs = []
+    for i in range(n_req):
+        k = int(kinds[i])
+        if k == 0:
+            reqs.append(("fib", 20 + int(v[i] * 13)))
+        elif k == 1:
+            reqs.append(("nqueens", 8 + int(v[i] * 5)))
+        elif k == 2:
+            reqs.append(("kclique", 10 + int(v[i] * 5)))
+        else:
+            reqs.append(("uts", 100 + int(v[i] * 1901)))
+    return arrivals, reqs
+
+
+def run_serve(args):
+    """Served mixed stream into the resident kernel vs one launch per request."""
+    global np
+    import numpy as np
+    import torch
+
+    from paper_2604_05982_gb300 import gtap as G
+    from paper_2604_05982_gb300 import inputs, runner
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    n_req = args.requests
+    arrivals, reqs = _serve_trace(n_req, SERVE_RATE)
+    graphs = {s: runner.DeviceGraph(*inputs.rmat_graph(s, 16, seed=7)) for s in range(10, 15)}
+    progs = ("fib", "nqueens", "kclique", "uts")
+
+    def args_for(ctxtypes, r, i):
+        kind, x = r
+        if kind == "fib":
+            return ctxtypes["fib"], G.gtap_fib_args(x, 0)
+        if kind == "nqueens":
+            return ctxtypes["nqueens"], G.gtap_nqueens_args(x, 0)
+        if kind == "kclique":
+            return ctxtypes["kclique"], graphs[x].args(4)
+        return ctxtypes["uts"], G.gtap_uts_args(1000 + i, runner.UTS_THRESHOLD_Q0199, x, 5, 0, 0)
+
+    pool = 4 << 30
+    # ---- served: one resident kernel, requests through the inbox
+    with runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=pool, scratch_bytes=1 << 30, max_roots=4096) as c:
+        types = {p: c.register(p) for p in progs}
+        G.gtap_serve_start(c.ctx)
+        req_of = {}
+        done_t = np.zeros(n_req)
+        served_val = [None] * n_req
+        t0 = time.perf_counter()
+        nxt, ndone = 0, 0
+        failure = None
+        try:
+            while ndone < n_req:
+                now = time.perf_counter() - t0
+                if now > arrivals[-1] + 120.0:
+                    failure = f"deadline: {ndone} of {n_req} completed"
+                    break
+                while nxt < n_req and arrivals[nxt] <= now:
+                    t, a = args_for(types, reqs[nxt], nxt)
+                    rid = G.gtap_submit(c.ctx, t, a, 0)
+                    if rid is None:
+                        break
+                    req_of[rid] = nxt
+                    nxt += 1
+                for rid, r0, _, st in G.gtap_poll(c.ctx):
+                    i = req_of[rid]
+                    done_t[i] = time.perf_counter() - t0
+                    served_val[i] = r0
+                    ndone += 1
+        except G.GtapError as exc:
+            failure = str(exc)
+        finally:
+            stop_status = G.load_library().gtap_serve_stop(c.ctx, 60000)
+        if failure is not None or stop_status != 0:
+            print(json.dumps({"metric": "served requests/s", "error": failure or G.STATUS.get(stop_status)}), flush=True)
+            return
+    lat_served = (done_t - arrivals) * 1e3
+    span_served = done_t.max() - arrivals[0]
+
+    # ---- one launch per request, same arrival trace and GPU
+    with runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=pool, scratch_bytes=1 << 30) as c:
+        types = {p: c.register(p) for p in progs}
+        done_b = np.zeros(n_req)
+        base_val = [None] * n_req
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            c.clear()
+            t, a = args_for(types, reqs[i], i)
+            h = c.spawn(t, a)
+            c.run()
+            base_val[i] = c.result_u64(h)
+            done_b[i] = time.perf_counter() - t0
+    lat_base = (done_b - arrivals) * 1e3
+    span_base = done_b.max() - arrivals[0]
+    identical = served_val == base_val
+
+    def pct(a, q):
+        return float(np.percentile(a, q))
+
+    line = {"metric": "served requests/s", "value": n_req / span_served, "unit": "req/s", "n_gpus": world,
+            "steps": 1, "warmup": 0, "ms_per_step": span_served * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"served mix: Poisson {SERVE_RATE:.0f} req/s, {n_req} requests of fib n in [20,32], "
+                                   "N-Queens n in [8,12], 4-clique on R-MAT scale [10,14], hashed tree root [100,2000]; "
+                                   "4 GiB record pool", "parallelism": "replicas"},
+            "latency_ms": {"p50": pct(lat_served, 50), "p99": pct(lat_served, 99), "max": float(lat_served.max())},
+            "per_request_launch": {"value": n_req / span_base, "unit": "req/s", "p50_ms": pct(lat_base, 50),
+                                   "p99_ms": pct(lat_base, 99)},
+            "results_identical_alone_and_in_mix": bool(identical)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,11 +415,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gtap", choices=["gtap", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="integer", choices=["integer", "serve"],
+                    help="integer: the default bench line; serve: the served mixed stream")
+    ap.add_argument("--requests", type=int, default=SERVE_REQUESTS)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -76,7 +76,8 @@ typedef struct {
     void* stream;           /* cudaStream_t for runs (default: the legacy default stream) */
     uint64_t timeout_ns;    /* device-side run deadline (default 60 s); exceeded -> GTAP_ERR_TIMEOUT */
     uint64_t seed;          /* victim-selection seed (default 0x5EED) */
-    size_t scratch_bytes;   /* device scratch arena for programs that need it (k-clique), default 0 */
+    size_t scratch_bytes;   /* device scratch arena for programs that need it (k-clique candidate sets):
+                               4 KiB blocks recycled through a free-block queue, default 0 */
     int grid_blocks;        /* explicit persistent grid size (overrides blocks_per_sm x SM count), e.g. 1 */
     int debug_checks;       /* 1: track every record's state (free / allocated / running) and report
                                double allocation, double free or double execution as GTAP_ERR_TASK_FAILED */
@@ -163,6 +164,42 @@ gtap_status gtap_last_error(gtap_ctx* ctx, gtap_error_info* out);
 
 /* Forget the queued roots (the next gtap_spawn_root starts a new batch). */
 gtap_status gtap_clear_roots(gtap_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Serving: a resident persistent kernel fed through a host-to-device inbox
+ * (thread mode).  gtap_serve_start launches the scheduler kernel, which keeps
+ * running; gtap_submit queues a request (a root of a registered program, its
+ * arguments copied now) in a ring of mapped pinned host memory; a device warp
+ * admits it once enough task records are free (at least 1/64 of the pool) and
+ * a root slot and an outbox entry are available, so requests that arrive while
+ * others run start as soon as memory frees up and their work overlaps on the
+ * device; each completion is written to a mapped outbox that gtap_poll reads.
+ * Between gtap_serve_start and gtap_serve_stop no gtap_run is allowed. */
+typedef struct {
+    uint64_t req;        /* the id gtap_submit returned */
+    uint64_t result[2];  /* the root's result (as gtap_read_result would return it) */
+    int32_t status;      /* 0 */
+    int32_t pad;
+} gtap_completion;
+
+/* Launch the resident kernel.  Errors: GTAP_ERR_INVALID_ARG (block mode or no
+ * registered program), GTAP_ERR_BUSY, GTAP_ERR_NO_MEMORY, GTAP_ERR_CUDA. */
+gtap_status gtap_serve_start(gtap_ctx* ctx);
+
+/* Queue one request; never blocks.  Returns GTAP_ERR_BUSY when the inbox ring
+ * (max_roots slots) is full, GTAP_ERR_INVALID_ARG for bad arguments. */
+gtap_status gtap_submit(gtap_ctx* ctx, int type, const void* args, size_t args_bytes, int queue, uint64_t* out_req);
+
+/* Copy up to max completed requests (in completion order) into out; *n gets
+ * the number copied (0 if none is ready).  Also valid after gtap_serve_stop.
+ * Returns the device's error code once the session has failed (the kernel then
+ * drains; call gtap_serve_stop), else GTAP_OK. */
+gtap_status gtap_poll(gtap_ctx* ctx, gtap_completion* out, int max, int* n);
+
+/* Close the inbox: the kernel admits what was submitted, finishes it and
+ * exits; waits at most timeout_ms (0: the device deadline), then raises the
+ * abort word.  Returns the device status. */
+gtap_status gtap_serve_stop(gtap_ctx* ctx, uint64_t timeout_ms);
 
 /* Capture one run of the currently queued roots (root upload, reset kernel,
  * persistent kernel) as a CUDA graph; later gtap_run calls replay the graph

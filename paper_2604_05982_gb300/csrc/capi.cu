@@ -1,6 +1,7 @@
 // Host runtime behind the C ABI (include/gtap.h): context, storage, root
 // queueing, launch, bounded wait, result and statistics readback.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -67,6 +68,11 @@ struct gtap_ctx {
     RootDesc* root_desc = nullptr;
     WorkerStats* stats = nullptr;
     char* scratch = nullptr;
+    unsigned long long* sq_seq = nullptr;
+    uint32_t* sq_ids = nullptr;
+    uint64_t sq_mask = 0;
+    char* blocks = nullptr;
+    uint64_t blocks_bytes = 0;
     unsigned* fstate = nullptr;
     unsigned long long* flog = nullptr;
     unsigned* flogn = nullptr;
@@ -104,6 +110,15 @@ struct gtap_ctx {
     int graph_grid = 0;
     uint64_t graph_frames = 0;
     cudaStream_t run_stream = nullptr;   // stream of the launch in flight
+    // serving
+    bool serving = false;
+    InboxSlot* inbox = nullptr;          // mapped pinned
+    OutboxEntry* outbox = nullptr;
+    HostFlags* hflags = nullptr;
+    InboxSlot* inbox_dev = nullptr;
+    OutboxEntry* outbox_dev = nullptr;
+    HostFlags* hflags_dev = nullptr;
+    uint64_t submitted = 0;
 };
 
 extern "C" {
@@ -136,6 +151,9 @@ static void drop_graph(gtap_ctx* c) {
 
 static gtap_status free_all(gtap_ctx* c) {
     drop_graph(c);
+    if (c->inbox) cudaFreeHost(c->inbox);
+    if (c->outbox) cudaFreeHost(c->outbox);
+    if (c->hflags) cudaFreeHost(c->hflags);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     if (c->own_arena && c->arena) cudaFree(c->arena);
     if (c->root_desc_pinned) cudaFreeHost(c->root_desc_pinned);
@@ -234,6 +252,19 @@ gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, con
     c->root_desc = reinterpret_cast<RootDesc*>(c->arena + o_desc);
     c->stats = reinterpret_cast<WorkerStats*>(c->arena + o_stats);
     c->scratch = cfg.scratch_bytes ? c->arena + o_scratch : nullptr;
+    if (c->scratch) {
+        // the free-block queue sits at the front of the scratch arena, the blocks after it
+        const uint64_t nb0 = cfg.scratch_bytes / kScratchBlock;
+        if (nb0 < 2) { free_all(c); return GTAP_ERR_INVALID_ARG; }
+        const uint64_t nq = next_pow2((uint32_t)std::min<uint64_t>(nb0 + 1, 1ull << 31));
+        const uint64_t qbytes = align_up(nq * (sizeof(unsigned long long) + sizeof(uint32_t)), kScratchBlock);
+        if (qbytes + kScratchBlock > cfg.scratch_bytes) { free_all(c); return GTAP_ERR_INVALID_ARG; }
+        c->sq_seq = reinterpret_cast<unsigned long long*>(c->scratch);
+        c->sq_ids = reinterpret_cast<uint32_t*>(c->scratch + nq * sizeof(unsigned long long));
+        c->sq_mask = nq - 1;
+        c->blocks = c->scratch + qbytes;
+        c->blocks_bytes = (cfg.scratch_bytes - qbytes) / kScratchBlock * kScratchBlock;
+    }
     c->fstate = cfg.debug_checks ? reinterpret_cast<unsigned*>(c->arena + o_fstate) : nullptr;
     c->flog = cfg.debug_checks > 1 ? reinterpret_cast<unsigned long long*>(c->arena + o_flog) : nullptr;
     c->flogn = cfg.debug_checks > 1 ? reinterpret_cast<unsigned*>(c->arena + o_flogn) : nullptr;
@@ -396,11 +427,12 @@ struct LaunchPlan {
     int grid;
 };
 
-static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp, bool capturing = false);
+static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp, bool capturing = false,
+                                    bool serving = false);
 
 gtap_status gtap_run(gtap_ctx* c) {
     if (!c) return GTAP_ERR_INVALID_ARG;
-    if (c->running) return GTAP_ERR_BUSY;
+    if (c->running || c->serving) return GTAP_ERR_BUSY;
     const uint32_t nroots = (uint32_t)c->pending_roots.size();
     if (nroots == 0) return GTAP_ERR_INVALID_ARG;
     if (c->graph_valid) {
@@ -460,13 +492,13 @@ gtap_status gtap_capture_graph(gtap_ctx* c) {
     return GTAP_OK;
 }
 
-static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp, bool capturing) {
+static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp, bool capturing, bool serving) {
     // inside a capture the kernel-timing events become event-record nodes of the graph
     auto record = [&](cudaEvent_t ev) {
         if (capturing) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
         else cudaEventRecord(ev, s);
     };
-    const uint32_t nroots = (uint32_t)c->pending_roots.size();
+    const uint32_t nroots = serving ? 0u : (uint32_t)c->pending_roots.size();
 
     KParams P{};
     unsigned pset;
@@ -520,18 +552,36 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
     P.timeout_ns = c->cfg.timeout_ns;
     P.seed = c->cfg.seed;
     P.steal_policy = c->cfg.steal_policy;
-    P.scratch = c->scratch;
-    P.scratch_bytes = c->cfg.scratch_bytes;
+    P.scratch = c->blocks;
+    P.scratch_bytes = c->blocks_bytes;
+    P.sq_seq = c->sq_seq;
+    P.sq_ids = c->sq_ids;
+    P.sq_mask = c->sq_mask;
     P.fstate = c->fstate;
     P.flog = c->flog;
     P.flogn = c->flogn;
     if (c->flogn) cudaMemsetAsync(c->flogn, 0, c->max_frames * sizeof(unsigned), c->stream);
 
-    std::memcpy(c->root_desc_pinned, c->pending_roots.data(), nroots * sizeof(RootDesc));
     *c->host_abort = 0;
-    if (cudaMemcpyAsync(c->root_desc, c->root_desc_pinned, nroots * sizeof(RootDesc), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return GTAP_ERR_CUDA;
+    if (nroots > 0) {
+        std::memcpy(c->root_desc_pinned, c->pending_roots.data(), nroots * sizeof(RootDesc));
+        if (cudaMemcpyAsync(c->root_desc, c->root_desc_pinned, nroots * sizeof(RootDesc), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return GTAP_ERR_CUDA;
+    }
     if (launch_reset(P, 1, s) != cudaSuccess) return GTAP_ERR_CUDA;
+    if (serving) {
+        // the root table becomes a ring of request slots for the whole session
+        P.serving = 1;
+        P.n_roots = (uint32_t)c->cfg.max_roots;
+        P.inbox = c->inbox_dev;
+        P.inbox_cap = (uint32_t)c->cfg.max_roots;
+        P.outbox = c->outbox_dev;
+        P.outbox_cap = (uint32_t)c->cfg.max_roots;
+        P.hflags = c->hflags_dev;
+        P.host_abort = &c->hflags_dev->abort;
+        P.admit_reserve = std::max<uint64_t>(P.n_frames / 64, 4096);
+    }
     record(c->ev_k0);
     cudaError_t e = (c->mode == GTAP_MODE_THREAD)
                         ? launch_thread_kernel(pset, P, grid, c->threads_per_block, smem, s)
@@ -599,7 +649,7 @@ gtap_status gtap_wait(gtap_ctx* c, uint64_t timeout_ms) {
     }
     st.tasks_created += c->launched_roots;
     st.frames_high_water = std::min<uint64_t>(c->ctl_pinned->bump.v, c->launched_frames);
-    st.scratch_used = c->ctl_pinned->scratch_top.v;
+    st.scratch_used = c->ctl_pinned->scratch_top.v * kScratchBlock;
     st.n_workers = (int)c->launched_workers;
     st.grid_blocks = c->launched_grid;
     st.threads_per_block = c->threads_per_block;
@@ -613,6 +663,97 @@ gtap_status gtap_wait(gtap_ctx* c, uint64_t timeout_ms) {
     c->have_results = true;
     if (timed_out && c->last_err.code == 0) c->last_err.code = GTAP_ERR_TIMEOUT;
     return (gtap_status)c->last_err.code;
+}
+
+gtap_status gtap_serve_start(gtap_ctx* c) {
+    if (!c || c->mode != GTAP_MODE_THREAD || c->registered == 0) return GTAP_ERR_INVALID_ARG;
+    if (c->running || c->serving) return GTAP_ERR_BUSY;
+    const size_t cap = (size_t)c->cfg.max_roots;
+    if (!c->inbox) {
+        if (cudaHostAlloc(reinterpret_cast<void**>(&c->inbox), cap * sizeof(InboxSlot), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc(reinterpret_cast<void**>(&c->outbox), cap * sizeof(OutboxEntry), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc(reinterpret_cast<void**>(&c->hflags), sizeof(HostFlags), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->inbox_dev), c->inbox, 0) != cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->outbox_dev), c->outbox, 0) != cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->hflags_dev), c->hflags, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return GTAP_ERR_NO_MEMORY;
+        }
+    }
+    std::memset(c->inbox, 0, cap * sizeof(InboxSlot));
+    std::memset(c->outbox, 0, cap * sizeof(OutboxEntry));
+    std::memset(c->hflags, 0, sizeof(HostFlags));
+    c->submitted = 0;
+    if (!c->own_stream && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) return GTAP_ERR_CUDA;
+    LaunchPlan lp;
+    cudaStream_t s = c->own_stream;
+    cudaEventRecord(c->ev_start, s);
+    gtap_status st = plan_and_enqueue(c, s, &lp, false, true);
+    if (st != GTAP_OK) return st;
+    cudaEventRecord(c->ev_stop, s);
+    c->serving = true;
+    c->running = true;
+    c->have_results = false;
+    c->run_stream = s;
+    c->launched_roots = 0;
+    c->launched_workers = lp.P.n_workers;
+    c->launched_grid = lp.grid;
+    c->launched_frames = lp.P.n_frames;
+    return GTAP_OK;
+}
+
+gtap_status gtap_submit(gtap_ctx* c, int type, const void* args, size_t args_bytes, int queue, uint64_t* out_req) {
+    if (!c || !c->serving || !args || type <= 0 || type >= T_MAX || !c->registered_type[type]) return GTAP_ERR_INVALID_ARG;
+    if (queue < 0 || queue >= c->n_queues) return GTAP_ERR_INVALID_ARG;
+    const uint64_t cap = (uint64_t)c->cfg.max_roots;
+    volatile HostFlags* hf = c->hflags;
+    if (c->submitted - hf->inbox_consumed >= cap) return GTAP_ERR_BUSY;
+    RootDesc d;
+    gtap_status st = make_root(c, type, args, args_bytes, queue, 0, &d);
+    if (st != GTAP_OK) return st;
+    InboxSlot* slot = c->inbox + (c->submitted % cap);
+    slot->type = d.type;
+    slot->queue = d.queue;
+    std::memcpy(slot->payload, d.payload, sizeof(slot->payload));
+    std::memcpy(slot->env, d.env, sizeof(slot->env));
+    std::atomic_thread_fence(std::memory_order_release);
+    reinterpret_cast<volatile InboxSlot*>(slot)->seq = c->submitted + 1;
+    if (out_req) *out_req = c->submitted;
+    ++c->submitted;
+    return GTAP_OK;
+}
+
+gtap_status gtap_poll(gtap_ctx* c, gtap_completion* out, int max, int* n) {
+    if (!c || !n || max < 0 || (max > 0 && !out) || !c->hflags) return GTAP_ERR_INVALID_ARG;
+    const uint64_t cap = (uint64_t)c->cfg.max_roots;
+    volatile HostFlags* hf = c->hflags;
+    uint64_t oc = hf->out_consumed;
+    int k = 0;
+    while (k < max) {
+        volatile OutboxEntry* e = c->outbox + (oc % cap);
+        if (e->seq != oc + 1) break;
+        std::atomic_thread_fence(std::memory_order_acquire);
+        out[k].req = e->req;
+        out[k].result[0] = e->result[0];
+        out[k].result[1] = e->result[1];
+        out[k].status = e->status;
+        out[k].pad = 0;
+        ++k;
+        ++oc;
+    }
+    std::atomic_thread_fence(std::memory_order_release);
+    hf->out_consumed = oc;
+    *n = k;
+    return (gtap_status)hf->dev_error;
+}
+
+gtap_status gtap_serve_stop(gtap_ctx* c, uint64_t timeout_ms) {
+    if (!c || !c->serving) return GTAP_ERR_INVALID_ARG;
+    std::atomic_thread_fence(std::memory_order_release);
+    reinterpret_cast<volatile HostFlags*>(c->hflags)->shutdown = c->submitted + 1;
+    gtap_status st = gtap_wait(c, timeout_ms);
+    c->serving = false;
+    return st;
 }
 
 gtap_status gtap_read_result(gtap_ctx* c, uint64_t handle, void* out, size_t bytes) {

@@ -123,6 +123,12 @@ static __device__ __noinline__ void raise_error(const KParams& P, int code, int 
     }
     __threadfence();
     atomicExch(reinterpret_cast<unsigned long long*>(&P.ctl->abort_flag.v), 1ull);
+    if (P.serving && P.hflags != nullptr) {
+        // a served session reports the failure through mapped memory, where the host polls
+        volatile int* e = &P.hflags->dev_error;
+        if (*e == 0) *e = code;
+        __threadfence_system();
+    }
 }
 
 // Debug event log: code:4 | lane:5 | worker:15 | iteration:24 | aux:16.
@@ -153,6 +159,55 @@ __device__ __forceinline__ bool abort_requested(const KParams& P, bool check_hos
         return true;
     }
     return false;
+}
+
+// ---------------------------------------------------------------------------
+// Scratch blocks (lane-level).  Programs that need variable-size buffers during
+// a run (k-clique candidate sets) take kScratchBlock-byte blocks: recycled
+// blocks come from a bounded MPMC queue with fetch-and-add tickets and a
+// completed-free counter (the frame pool's chunk-queue protocol, one block per
+// slot), fresh ones from a bump counter.  Buffers larger than one block take
+// consecutive fresh blocks and are not recycled.
+__device__ __forceinline__ char* scratch_alloc(const KParams& P, uint64_t bytes, bool* pooled, int type, int worker) {
+    const uint64_t nblocks = P.scratch_bytes / kScratchBlock;
+    *pooled = bytes <= kScratchBlock;
+    if (*pooled) {
+        const long long a = (long long)atomicAdd(&P.ctl->sc_avail.v, ~0ull);   // reserve one completed free
+        if (a > 0) {
+            const unsigned long long d = atomicAdd(&P.ctl->sc_deq.v, 1ull);
+            for (int it = 0; it < (1 << 20); ++it) {
+                if (ld_acquire_u64(&P.sq_seq[d & P.sq_mask]) == d + 1) {
+                    const uint32_t id = __ldcg(&P.sq_ids[d & P.sq_mask]);
+                    st_release_u64(&P.sq_seq[d & P.sq_mask], d + P.sq_mask + 1);
+                    return P.scratch + (uint64_t)id * kScratchBlock;
+                }
+                __nanosleep(64);
+            }
+            raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, d);
+            return nullptr;
+        }
+        atomicAdd(&P.ctl->sc_avail.v, 1ull);
+    }
+    const uint64_t k = (bytes + kScratchBlock - 1) / kScratchBlock;
+    const unsigned long long b = atomicAdd(&P.ctl->scratch_top.v, (unsigned long long)k);
+    if (b + k > nblocks) { raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, (b + k) * kScratchBlock); return nullptr; }
+    return P.scratch + b * kScratchBlock;
+}
+
+__device__ __forceinline__ void scratch_free(const KParams& P, const void* p, int type, int worker) {
+    const uint32_t id = (uint32_t)((reinterpret_cast<const char*>(p) - P.scratch) / kScratchBlock);
+    const unsigned long long t = atomicAdd(&P.ctl->sc_enq.v, 1ull);
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (ld_acquire_u64(&P.sq_seq[t & P.sq_mask]) == t) {
+            __stcg(&P.sq_ids[t & P.sq_mask], id);
+            __threadfence();
+            st_release_u64(&P.sq_seq[t & P.sq_mask], t + 1);
+            atomicAdd(&P.ctl->sc_avail.v, 1ull);
+            return;
+        }
+        __nanosleep(64);
+    }
+    raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -398,11 +453,25 @@ struct TaskCtx {
         const uint32_t flags = (h.w0 >> 16) & 0xFFu;
         if (parent & kRootBit) {
             RootEntry* r = &P.roots[parent & ~kRootBit];
-            if (flags & kFlagAccumulate) atomicAdd(&r->result[slot & 1], v);
-            else st_cg64(&r->result[slot & 1], v);
-            __threadfence();
-            atomicExch(&r->done, 1u);
-            atomicAdd(&P.ctl->roots_remaining.v, ~0ull);
+            if (P.serving) {
+                // served request: publish the result in the host-mapped outbox
+                const unsigned long long pos = atomicAdd(&P.ctl->out_tail.v, 1ull);
+                volatile OutboxEntry* o = P.outbox + (pos % P.outbox_cap);
+                o->req = ld_cg64(&r->req);
+                o->result[0] = v;
+                o->result[1] = 0;
+                o->status = 0;
+                __threadfence_system();
+                o->seq = pos + 1;
+                __threadfence_system();
+                atomicAdd(&P.ctl->inflight.v, ~0ull);
+            } else {
+                if (flags & kFlagAccumulate) atomicAdd(&r->result[slot & 1], v);
+                else st_cg64(&r->result[slot & 1], v);
+                __threadfence();
+                atomicExch(&r->done, 1u);
+                atomicAdd(&P.ctl->roots_remaining.v, ~0ull);
+            }
         } else {
             char* pf = frame_ptr(P, parent);
             unsigned long long* dst = reinterpret_cast<unsigned long long*>(pf + slot * 8);
@@ -419,6 +488,99 @@ struct TaskCtx {
         freed_self = true;
     }
 };
+
+// ---------------------------------------------------------------------------
+// Serving: warp 0 of the grid is the inbox poller.  It admits a request when
+// enough task records are free and the outbox has room, writes the request's
+// root record (frames from the pool, environment into the root table slot),
+// and pushes it on its own deque, from which the other warps steal it.
+// Requests that arrive while others run are admitted as records and root
+// slots free up, so their work overlaps on the device (continuous batching).
+static __device__ void serve_poller(const KParams& P, const WarpSh& ws, int* ftop_io) {
+    const int lane = threadIdx.x & 31;
+    const int Q = (int)P.n_queues;
+    const uint32_t cap_mask = P.ring_mask;
+    QState* myq = P.qs;                       // warp 0's queues
+    uint32_t* myring = P.rings;
+    int ftop = *ftop_io;
+    unsigned long long next = 0;              // next inbox sequence to take
+    int backoff = 64;
+    for (uint32_t iter = 0;; ++iter) {
+        ftop = pool_refill(P, ws.fstack, ftop, 32);
+        int stop = 0, took = 0;
+        if (lane == 0) {
+            volatile HostFlags* hf = P.hflags;
+            if (ld_cg64(&P.ctl->abort_flag.v) != 0 || hf->abort != 0) {
+                stop = 1;
+            } else {
+                volatile InboxSlot* slot = P.inbox + (next % P.inbox_cap);
+                const unsigned long long sq = slot->seq;
+                if (sq == next + 1) {
+                    __threadfence_system();
+                    const unsigned long long bump = ld_cg64(&P.ctl->bump.v);
+                    const unsigned long long used = bump < P.n_frames ? bump : P.n_frames;
+                    const unsigned long long free_records = (P.n_frames - used) + 32ull * ld_cg64(&P.ctl->cq_avail.v);
+                    const unsigned long long inflight = ld_cg64(&P.ctl->inflight.v);
+                    const unsigned long long unread = ld_cg64(&P.ctl->out_tail.v) - hf->out_consumed;
+                    const uint32_t q = slot->queue % (uint32_t)Q;
+                    const bool room = ws.tail[q] - ws.head_lb[q] + 1u <= cap_mask + 1 ||
+                                      ws.tail[q] - (ws.head_lb[q] = __ldcg(&myq[q].head)) + 1u <= cap_mask + 1;
+                    if (free_records >= P.admit_reserve && ftop > 0 && inflight < P.n_roots &&
+                        inflight + unread < P.outbox_cap && room) {
+                        const unsigned long long adm = ld_cg64(&P.ctl->admitted.v);
+                        const uint32_t r = (uint32_t)(adm % P.n_roots);
+                        const uint32_t id = ws.fstack[--ftop];
+                        const uint32_t type = slot->type;
+                        // root environment (read by programs with per-root buffers)
+                        RootDesc* d = const_cast<RootDesc*>(P.root_desc) + r;
+                        for (int i = 0; i < kRootArgBytes / 4; ++i)
+                            st_cg32(d->env + 4 * i, ((volatile uint32_t*)slot->env)[i]);
+                        char* f = frame_ptr(P, id);
+                        FrameHdr h;
+                        h.w0 = type & 0xFFu;
+                        h.pending = 0;
+                        h.parent = kRootBit | r;
+                        h.w3 = 0;
+                        st_obj(f, h);
+                        for (int i = 0; i < kRootPayloadBytes / 4; ++i) {
+                            uint32_t w = ((volatile uint32_t*)slot->payload)[i];
+                            if (i == 0 && type == T_KCLIQUE_ROOT) w = r;   // programs with a root environment name its slot
+                            st_cg32(f + kHdrBytes + 4 * i, w);
+                        }
+                        RootEntry e;
+                        e.result[0] = 0; e.result[1] = 0; e.done = 0; e.type = type; e.req = next;
+                        st_obj(&P.roots[r], e);
+                        // push on the poller's own deque (one fence, one count increment)
+                        const uint32_t t = ws.tail[q];
+                        __stcg(&myring[(size_t)q * (cap_mask + 1) + (t & cap_mask)], id);
+                        __threadfence();
+                        atomicAdd(&P.ctl->inflight.v, 1ull);
+                        atomicAdd(&P.ctl->admitted.v, 1ull);
+                        ws.tail[q] = t + 1u;
+                        atomicAdd(&myq[q].count, 1);
+                        hf->inbox_consumed = next + 1;
+                        ++next;
+                        took = 1;
+                    }
+                } else {
+                    const unsigned long long sd = hf->shutdown;
+                    if (sd != 0 && next == sd - 1) stop = 1;   // the host closed the inbox and all is taken
+                }
+            }
+        }
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        took = __shfl_sync(0xffffffffu, took, 0);
+        ftop = __shfl_sync(0xffffffffu, ftop, 0);
+        if (stop) break;
+        if (took) {
+            backoff = 64;
+        } else {
+            __nanosleep(backoff);
+            backoff = min(backoff * 2, 1024);
+        }
+    }
+    *ftop_io = ftop;
+}
 
 // ---------------------------------------------------------------------------
 // Thread-mode scheduler loop (Algorithm 1), one instance per warp.
@@ -444,6 +606,12 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
     if (lane == 0) { ws.ctrl[0] = 0; ws.ctrl[1] = 0; ws.ctrl[2] = 0; ws.ctrl[3] = 0; }
     __syncwarp();
 
+    if (P.serving && wid == 0) {
+        int ft = 0;
+        serve_poller(P, ws, &ft);
+        if (lane == 0) { WorkerStats s{}; P.stats[wid] = s; }
+        return;
+    }
     unsigned long long st_tasks = 0, st_steps = 0, st_pops = 0, st_popped = 0, st_sa = 0, st_steals = 0,
                        st_stolen = 0, st_idle = 0, st_pushes = 0, st_pushed = 0, st_spawned = 0;
     // per-lane xorshift state for victim probing
@@ -609,9 +777,14 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             ++st_idle;
             int stop = 0;
             if (lane == 0 && (st_idle & 15ull) == 1ull) {
-                if (ld_cg64(&P.ctl->roots_remaining.v) == 0ull) stop = 1;
+                if (P.serving) {
+                    // served session: done once the host has closed the inbox, every submitted
+                    // request has been admitted and none is in flight
+                    const unsigned long long sd = *(volatile unsigned long long*)&P.hflags->shutdown;
+                    if (sd != 0 && ld_cg64(&P.ctl->admitted.v) == sd - 1 && ld_cg64(&P.ctl->inflight.v) == 0) stop = 1;
+                } else if (ld_cg64(&P.ctl->roots_remaining.v) == 0ull) stop = 1;
                 else if (abort_requested(P, (st_idle & 255ull) == 1ull)) stop = 1;
-                else if (global_ns() > deadline) { raise_error(P, GTAP_ERR_TIMEOUT, -1, wid, P.timeout_ns); stop = 1; }
+                else if (!P.serving && global_ns() > deadline) { raise_error(P, GTAP_ERR_TIMEOUT, -1, wid, P.timeout_ns); stop = 1; }
             }
             if (__shfl_sync(0xffffffffu, stop, 0)) break;
             __nanosleep(backoff);

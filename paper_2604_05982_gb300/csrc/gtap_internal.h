@@ -51,6 +51,8 @@ enum ProgSet : unsigned {
     PS_DTT = 1u << 10,
 };
 
+constexpr uint64_t kScratchBlock = 4096;   // bytes per recycled scratch block
+
 // Frame header flag bits.
 constexpr uint32_t kFlagAccumulate = 1u;  // child result is added (u64) into the parent slot
 
@@ -95,6 +97,9 @@ struct DevControl {
     Line128 scratch_top;       // bytes taken from the scratch arena
     Line128 inflight;          // serving: roots admitted and not yet completed
     Line128 cq_avail;          // chunks whose enqueue has completed and that no dequeuer reserved
+    Line128 sc_enq, sc_deq, sc_avail;   // scratch free-block queue tickets / completed frees
+    Line128 out_tail;          // serving: completions written to the outbox
+    Line128 admitted;          // serving: requests admitted so far
     alignas(128) ErrorRecord err;
 };
 
@@ -102,8 +107,33 @@ struct RootEntry {
     unsigned long long result[2];
     unsigned int done;
     unsigned int type;
-    unsigned int queue;
-    unsigned int pad;
+    unsigned long long req;    // serving: the request's sequence number
+};
+
+// Serving (resident kernel).  The host writes requests into a ring of inbox
+// slots in mapped pinned memory and reads completions from a ring of outbox
+// entries there; both rings are indexed by monotonically increasing sequence
+// numbers, and a slot is valid when its seq field equals its sequence + 1.
+struct InboxSlot {
+    unsigned long long seq;
+    uint32_t type;
+    uint32_t queue;
+    unsigned char payload[48];
+    unsigned char env[64];
+};
+struct OutboxEntry {
+    unsigned long long seq;
+    unsigned long long req;
+    unsigned long long result[2];
+    int status;
+    int pad[3];
+};
+struct HostFlags {            // mapped pinned host memory
+    int abort;                // same role as host_abort in batch runs
+    int dev_error;            // device: first error code of the session (0 = none)
+    unsigned long long shutdown;        // host: no more requests; drain and exit
+    unsigned long long inbox_consumed;  // device: requests taken from the inbox
+    unsigned long long out_consumed;    // host: completions read from the outbox
 };
 
 // A root as queued by the host: its initial record payload and a read-only
@@ -147,8 +177,19 @@ struct KParams {
     uint64_t seed;
     int steal_policy;
     int pad0;
-    char* scratch;            // scratch arena for programs (k-clique candidate sets)
-    uint64_t scratch_bytes;
+    char* scratch;            // scratch blocks for programs (k-clique candidate sets), kScratchBlock bytes each
+    uint64_t scratch_bytes;   // bytes of the block region
+    unsigned long long* sq_seq;   // free-block queue: sequence numbers and block ids
+    uint32_t* sq_ids;
+    uint64_t sq_mask;
+    // serving mode (resident kernel)
+    int serving;
+    uint32_t inbox_cap, outbox_cap;
+    int pad1;
+    InboxSlot* inbox;          // mapped pinned host memory (device pointers)
+    OutboxEntry* outbox;
+    HostFlags* hflags;
+    unsigned long long admit_reserve;   // admit a request only while at least this many records are free
     unsigned int* fstate;     // debug: per-record state (0 free, 1 allocated, 2 running, 3 queued), or null
     unsigned long long* flog; // debug: last 8 events per record
     unsigned int* flogn;      // debug: event count per record

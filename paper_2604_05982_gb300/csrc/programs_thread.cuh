@@ -190,16 +190,19 @@ namespace gtap {
 //
 // Records (64 bytes):
 //   KC range [16] root, lo, hi, pad   [32] acc  [40] local
-//   KC set   [16] root, j  [24] set pointer  [32] len, lo  [40] hi, pad  [48] acc  [56] local
+//   KC set   [16] root, j  [24] set pointer  [32] len, lo  [40] hi, own  [48] acc  [56] local
+//   (own = 1: this task frees the set's scratch block when its subtree is done with it)
 struct KcRangeSpawn { uint32_t root, lo, hi, pad; unsigned long long acc, local; };
-struct KcSetSpawn { uint32_t root, j; unsigned long long set; uint32_t len, lo, hi, pad; unsigned long long acc, local; };
+struct KcSetSpawn { uint32_t root, j; unsigned long long set; uint32_t len, lo, hi, own; unsigned long long acc, local; };
 constexpr uint32_t kKcRangeSlotAcc = 4, kKcRangeLocal = 40;
 constexpr uint32_t kKcSetSlotAcc = 6, kKcSetLocal = 56;
 constexpr int kKcFan = 8;          // children per split
 constexpr int kKcMaxThr = 64;      // in-lane sets use 64-bit bitsets
 
-__device__ __forceinline__ const gtap_kclique_args& kc_env(const KParams& P, uint32_t root) {
-    return *reinterpret_cast<const gtap_kclique_args*>(P.root_desc[root].env);
+// The root environment is read through L2: in a served session the poller
+// writes it while the kernel runs.
+__device__ __forceinline__ gtap_kclique_args kc_env(const KParams& P, uint32_t root) {
+    return ld_obj<gtap_kclique_args>(P.root_desc[root].env);
 }
 
 // Read-only adjacency (never written during a run): non-coherent cached loads.
@@ -311,11 +314,10 @@ static __device__ unsigned long long kc_count_small(const int* S, int ns, int j,
     return total;
 }
 
-__device__ __forceinline__ int* kc_scratch_alloc(TaskCtx& c, int n) {
-    const unsigned long long bytes = ((unsigned long long)n * 4 + 15) & ~15ull;
-    const unsigned long long at = atomicAdd(&c.P.ctl->scratch_top.v, bytes);
-    if (at + bytes > c.P.scratch_bytes) { c.fail(GTAP_ERR_TASK_FAILED, at + bytes); return nullptr; }
-    return reinterpret_cast<int*>(c.P.scratch + at);
+// Candidate sets in the scratch arena: a set that fits one block is recycled
+// when the set task that owns it is done with it.
+__device__ __forceinline__ int* kc_scratch_alloc(TaskCtx& c, int n, bool* pooled) {
+    return reinterpret_cast<int*>(scratch_alloc(c.P, (uint64_t)n * 4, pooled, c.type(), c.worker));
 }
 
 __device__ __forceinline__ int kc_queue(const gtap_kclique_args& e, int depth) { return e.route ? depth : 0; }
@@ -348,12 +350,14 @@ static __device__ void kclique_range_step(TaskCtx& c) {
         if (need == 1) { local += (unsigned)cn; continue; }
         if (cn < need) continue;
         if (cn <= thr) { local += kc_count_small(C, cn, need, e.off, e.adj); continue; }
-        int* S = kc_scratch_alloc(c, cn);
+        bool pooled;
+        int* S = kc_scratch_alloc(c, cn, &pooled);
         if (!S) return;
         kc_intersect(e.adj + ou, nu, AdjLoad{}, e.adj + ov, nv, AdjLoad{}, S, cn);
-        // the child adds its count into this range task's accumulator
+        // the child adds its count into this range task's accumulator and owns the set
         c.spawn(T_KCLIQUE_SET, kKcRangeSlotAcc, kc_queue(e, 1),
-                KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)cn, 0u, (uint32_t)cn, 0u, 0ull, 0ull},
+                KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)cn, 0u, (uint32_t)cn, pooled ? 1u : 0u,
+                           0ull, 0ull},
                 kFlagAccumulate);
     }
     if (c.nspawned == 0) { c.ret(local); return; }
@@ -364,10 +368,15 @@ static __device__ void kclique_range_step(TaskCtx& c) {
 static __device__ void kclique_set_step(TaskCtx& c) {
     const KcSetSpawn a = c.load<KcSetSpawn>();
     const gtap_kclique_args& e = kc_env(c.P, a.root);
-    if (c.pc() != 0) { c.ret(a.acc + a.local); return; }
-    const int depth = e.k - 2 - (int)a.j + 1;
     const int* set = reinterpret_cast<const int*>(a.set);
     const uint32_t n = a.hi - a.lo;
+    if (c.pc() != 0) {
+        // a split owner frees its set once all range children are done with it
+        if (a.own && n > (uint32_t)kKcFan) scratch_free(c.P, set, c.type(), c.worker);
+        c.ret(a.acc + a.local);
+        return;
+    }
+    const int depth = e.k - 2 - (int)a.j + 1;
     if (n > (uint32_t)kKcFan) {
         const uint32_t per = (n + kKcFan - 1) / kKcFan;
         for (uint32_t s = a.lo; s < a.hi; s += per)
@@ -388,13 +397,17 @@ static __device__ void kclique_set_step(TaskCtx& c) {
         if (need == 1) { local += (unsigned)cn; continue; }
         if (cn < need) continue;
         if (cn <= thr) { local += kc_count_small(C, cn, need, e.off, e.adj); continue; }
-        int* S = kc_scratch_alloc(c, cn);
+        bool pooled;
+        int* S = kc_scratch_alloc(c, cn, &pooled);
         if (!S) return;
         kc_intersect(set, (int)a.len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, S, cn);
         c.spawn(T_KCLIQUE_SET, kKcSetSlotAcc, kc_queue(e, depth + 1),
-                KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)cn, 0u, (uint32_t)cn, 0u, 0ull, 0ull},
+                KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)cn, 0u, (uint32_t)cn, pooled ? 1u : 0u,
+                           0ull, 0ull},
                 kFlagAccumulate);
     }
+    // a leaf owner is done with its set here (its children work on their own sets)
+    if (a.own) scratch_free(c.P, set, c.type(), c.worker);
     if (c.nspawned == 0) { c.ret(local); return; }
     st_cg64(c.frame + kKcSetLocal, local);
     c.join(1, kc_queue(e, depth));

@@ -13,6 +13,8 @@ __global__ void reset_kernel(KParams P, int init_cq) {
     const uint32_t cap = P.ring_mask + 1;
     if (init_cq)
         for (size_t i = tid; i <= P.ncq_mask; i += nth) P.cq_seq[i] = i;
+    if (P.sq_seq != nullptr)
+        for (size_t i = tid; i <= P.sq_mask; i += nth) P.sq_seq[i] = i;
     if (P.fstate != nullptr)
         for (size_t i = tid; i < P.n_frames; i += nth) P.fstate[i] = (i < P.n_roots) ? 3u : 0u;
     // root records
@@ -28,7 +30,7 @@ __global__ void reset_kernel(KParams P, int init_cq) {
         for (int i = 0; i < kRootPayloadBytes / 4; ++i)
             reinterpret_cast<uint32_t*>(f + kHdrBytes)[i] = reinterpret_cast<const uint32_t*>(d.payload)[i];
         RootEntry e;
-        e.result[0] = 0; e.result[1] = 0; e.done = 0; e.type = d.type; e.queue = d.queue; e.pad = 0;
+        e.result[0] = 0; e.result[1] = 0; e.done = 0; e.type = d.type; e.req = r;
         P.roots[r] = e;
     }
     // deques: worker w owns roots w, w + W, w + 2W, ...
@@ -56,6 +58,11 @@ __global__ void reset_kernel(KParams P, int init_cq) {
         P.ctl->cq_enq.v = 0;
         P.ctl->cq_deq.v = 0;
         P.ctl->cq_avail.v = 0;
+        P.ctl->sc_enq.v = 0;
+        P.ctl->sc_deq.v = 0;
+        P.ctl->sc_avail.v = 0;
+        P.ctl->out_tail.v = 0;
+        P.ctl->admitted.v = 0;
         P.ctl->scratch_top.v = 0;
         P.ctl->inflight.v = 0;
         P.ctl->err.code = 0;

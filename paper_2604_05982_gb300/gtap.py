@@ -87,6 +87,11 @@ class gtap_mergesort_args(ctypes.Structure):
                 ("n", ctypes.c_uint64), ("leaf", ctypes.c_uint32), ("merge_cutoff", ctypes.c_uint32)]
 
 
+class gtap_completion(ctypes.Structure):
+    _fields_ = [("req", ctypes.c_uint64), ("result", ctypes.c_uint64 * 2), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "gtap_init": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(gtap_config),
@@ -101,6 +106,10 @@ _SIGS = {
     "gtap_last_error": (ctypes.c_int, [_P, ctypes.POINTER(gtap_error_info)]),
     "gtap_clear_roots": (ctypes.c_int, [_P]),
     "gtap_capture_graph": (ctypes.c_int, [_P]),
+    "gtap_serve_start": (ctypes.c_int, [_P]),
+    "gtap_submit": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+    "gtap_poll": (ctypes.c_int, [_P, ctypes.POINTER(gtap_completion), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "gtap_serve_stop": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "gtap_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gtap_finalize": (ctypes.c_int, [_P]),
     "gtap_debug_snapshot": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
@@ -220,3 +229,34 @@ def gtap_mergesort_noalloc(src: int, dst: int, n: int, stream: int = 0, raise_on
 def gtap_kclique_orient(edges: int, m: int, n: int, off: int, adj: int, src: int, work: int, stream: int = 0) -> None:
     """Orient an undirected graph on the GPU (device pointers; see gtap.h)."""
     _check(load_library().gtap_kclique_orient(edges, m, n, off, adj, src, work, stream or None), "gtap_kclique_orient")
+
+
+def gtap_serve_start(ctx: int) -> None:
+    _check(load_library().gtap_serve_start(ctx), "gtap_serve_start")
+
+
+def gtap_submit(ctx: int, type_id: int, args: ctypes.Structure, queue: int = 0):
+    """Queue a request; returns its id, or None if the inbox is full (GTAP_ERR_BUSY)."""
+    r = ctypes.c_uint64(0)
+    s = load_library().gtap_submit(ctx, type_id, ctypes.byref(args), ctypes.sizeof(args), queue, ctypes.byref(r))
+    if s == GTAP_ERR_BUSY:
+        return None
+    _check(s, "gtap_submit")
+    return r.value
+
+
+_poll_buf = (gtap_completion * 4096)()
+
+
+def gtap_poll(ctx: int, max_n: int = 4096):
+    """Completed requests as (req, result0, result1, status) tuples."""
+    n = ctypes.c_int(0)
+    max_n = min(max_n, len(_poll_buf))
+    _check(load_library().gtap_poll(ctx, _poll_buf, max_n, ctypes.byref(n)), "gtap_poll")
+    return [(c.req, c.result[0], c.result[1], c.status) for c in _poll_buf[: n.value]]
+
+
+def gtap_serve_stop(ctx: int, timeout_ms: int = 0) -> int:
+    s = load_library().gtap_serve_stop(ctx, timeout_ms)
+    _check(s, "gtap_serve_stop")
+    return s

@@ -90,3 +90,16 @@ def test_scale20_sampled_edge_ranges():
     r = runner.kclique([g] * len(ranges), 5, ranges=ranges)
     want = [oracle.kclique_edge_range(n, e, 5, lo, hi) for lo, hi in ranges]
     assert r.values == want
+
+
+def test_scratch_blocks_are_recycled():
+    # K_70, k = 5, split threshold 8: every edge and most second-level sets are
+    # materialised (about 2415 * 60 sets of one 4 KiB block, ~600 MB); recycled
+    # blocks keep the fresh-block high-water mark near the peak of live sets
+    n = 70
+    e = np.array(list(combinations(range(n), 2)), dtype=np.int32)
+    g = _graph(n, e)
+    for _ in range(3):
+        r = runner.kclique(g, 5, split_threshold=8, scratch_bytes=256 << 20)
+        assert r.values == [math.comb(n, 5)]
+    assert r.stats["scratch_used"] <= (256 << 20)
