@@ -281,6 +281,17 @@ typedef struct { const int64_t* off; const int32_t* adj; const int32_t* src;
 gtap_status gtap_kclique_orient(const int32_t* edges, int64_t m, int64_t n, int64_t* off, int32_t* adj,
                                 int32_t* src, int32_t* work, void* stream);
 
+/* Atomic-rate microbenchmark (the ceilings of the thread-mode scheduler).  kind:
+ * 0 scattered acq_rel atomic add with return (the join decrement), 1 scattered
+ * fire-and-forget 64-bit add (accumulating joins), 2 CAS on one word per warp
+ * (deque claims), 3 CAS on one shared word (a hot word), 4 scattered L2 loads.
+ * region: device buffer of region_bytes (its contents are overwritten).
+ * Runs one warm-up and one timed launch of blocks x threads threads, each doing
+ * iters operations (kinds 2-3: one lane per warp); *ms_out gets the timed
+ * launch's duration and *ops_out the operations it performed. */
+gtap_status gtap_microbench(int kind, void* region, uint64_t region_bytes, int blocks, int threads, int iters,
+                            float* ms_out, double* ops_out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart to this call.
  *

@@ -107,6 +107,8 @@ _SIGS = {
     "gtap_clear_roots": (ctypes.c_int, [_P]),
     "gtap_capture_graph": (ctypes.c_int, [_P]),
     "gtap_serve_start": (ctypes.c_int, [_P]),
+    "gtap_microbench": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double), _P]),
     "gtap_submit": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "gtap_poll": (ctypes.c_int, [_P, ctypes.POINTER(gtap_completion), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gtap_serve_stop": (ctypes.c_int, [_P, ctypes.c_uint64]),
@@ -260,3 +262,17 @@ def gtap_serve_stop(ctx: int, timeout_ms: int = 0) -> int:
     s = load_library().gtap_serve_stop(ctx, timeout_ms)
     _check(s, "gtap_serve_stop")
     return s
+
+
+MICROBENCH_KINDS = {0: "scattered acq_rel atomic add (join decrement)", 1: "scattered red.add u64 (accumulate)",
+                    2: "per-warp CAS (deque claim)", 3: "single-word CAS (hot word)", 4: "scattered L2 load"}
+
+
+def gtap_microbench(kind: int, region: int, region_bytes: int, blocks: int, threads: int = 256, iters: int = 64,
+                    stream: int = 0):
+    """Returns (ms, ops) of one timed launch."""
+    ms = ctypes.c_float(0)
+    ops = ctypes.c_double(0)
+    _check(load_library().gtap_microbench(kind, region, region_bytes, blocks, threads, iters, ctypes.byref(ms),
+                                          ctypes.byref(ops), stream or None), "gtap_microbench")
+    return ms.value, ops.value
