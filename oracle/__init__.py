@@ -62,6 +62,10 @@ def _load():
                 "orc_orient": (None, [i64, P, i64, i32, P, P]),
                 "orc_kclique_brute": (u64, [i32, P, i64, i32]),
                 "orc_kclique_edge_range": (u64, [i64, P, i64, i32, i32, i64, i64]),
+                "orc_fmm": (i32, [i64, P, P, i32, f64, i32, P, i64, P, P, P, P, P, i64, P, i64]),
+                "orc_fmm_tree": (i64, [i64, P, i32, P, i64, P]),
+                "orc_direct": (None, [i64, P, P, P, i64, P]),
+                "orc_taylor": (i32, [i32, f64, f64, f64, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -160,3 +164,69 @@ def kclique_edge_range(n: int, edges: np.ndarray, k: int, lo: int, hi: int, orde
     """Sum of per-DAG-edge k-clique counts over DAG edges [lo, hi)."""
     edges = np.ascontiguousarray(edges, dtype=np.int32)
     return int(_load().orc_kclique_edge_range(n, _ptr(edges), edges.shape[0], k, {"degree": 0, "id": 1}[order], lo, hi))
+
+
+def fmm(pos: np.ndarray, q: np.ndarray, p: int = 6, theta: float = 0.5, leaf_size: int = 64,
+        lists: bool = False, targets=None):
+    """FP64 FMM potentials (input order, or at ``targets`` only).  With ``lists``: also
+    (m2l, p2p) as (k, 2) int64 arrays of (target cell, source cell) in traversal order,
+    and the cell count."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = q.size
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    phi = np.zeros(n if tg is None else max(tg.size, 1), dtype=np.float64)
+    nc, nm, npp = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    lib = _load()
+    tp, tn = (None, 0) if tg is None else (_ptr(tg), tg.size)
+    if lib.orc_fmm(n, _ptr(pos), _ptr(q), p, theta, leaf_size, tp, tn, _ptr(phi), ctypes.byref(nc),
+                   ctypes.byref(nm), ctypes.byref(npp), None, 0, None, 0) != 0:
+        raise ValueError("orc_fmm: invalid arguments")
+    if tg is not None:
+        phi = phi[:tg.size]
+    if not lists:
+        return phi
+    m2l = np.zeros((max(nm.value, 1), 2), dtype=np.int64)
+    p2p = np.zeros((max(npp.value, 1), 2), dtype=np.int64)
+    lib.orc_fmm(n, _ptr(pos), _ptr(q), p, theta, leaf_size, tp, tn, _ptr(np.zeros_like(phi)), None, None, None,
+                _ptr(m2l), nm.value, _ptr(p2p), npp.value)
+    return phi, m2l[:nm.value], p2p[:npp.value], int(nc.value)
+
+
+def fmm_tree(pos: np.ndarray, leaf_size: int = 64):
+    """(cells, order): cells is (n_cells, 8) float64 rows (level, first, count,
+    child_first, nchild, cx, cy, cz); order maps sorted position -> input index."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n = pos.shape[0]
+    order = np.zeros(n, dtype=np.int64)
+    cap = max(16, 4 * n // max(leaf_size, 1) + 64)
+    while True:
+        cells = np.zeros((cap, 8), dtype=np.float64)
+        nc = int(_load().orc_fmm_tree(n, _ptr(pos), leaf_size, _ptr(cells), cap, _ptr(order)))
+        if nc <= cap:
+            return cells[:nc], order
+        cap = nc
+
+
+def direct(pos: np.ndarray, q: np.ndarray, targets=None) -> np.ndarray:
+    """phi_i = sum_{j != i} q_j / |x_i - x_j| for the given targets (all by default)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = q.size
+    t = np.arange(n, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    out = np.zeros(t.size, dtype=np.float64)
+    _load().orc_direct(n, _ptr(pos), _ptr(q), _ptr(t), t.size, _ptr(out))
+    return out
+
+
+def multi_indices(p: int):
+    """Multi-indices (a, b, c) of degree <= p in the expansions' order."""
+    return [(a, b, k - a - b) for k in range(p + 1) for a in range(k, -1, -1) for b in range(k - a, -1, -1)]
+
+
+def taylor(p: int, r) -> np.ndarray:
+    """T_n(r) = d^n(1/|r|)/n! for |n| <= p, ordered as multi_indices(p)."""
+    out = np.zeros(len(multi_indices(p)), dtype=np.float64)
+    if _load().orc_taylor(p, float(r[0]), float(r[1]), float(r[2]), _ptr(out)) != 0:
+        raise ValueError("orc_taylor: order out of range")
+    return out

@@ -257,3 +257,108 @@ def test_kclique_edge_range_sums_per_edge_counts():
     assert oracle.kclique_edge_range(n, edges, 4, 0, m) == total
     for lo, hi in [(0, 10), (37, 400), (m - 5, m)]:
         assert oracle.kclique_edge_range(n, edges, 4, lo, hi) == int(pe[lo:hi].sum())
+
+
+# ---------------------------------------------------------------------------
+# Laplace FMM (Sec. 6.4.1).  The plain definition is the direct sum
+# phi_i = sum_{j != i} q_j / |x_i - x_j|; the pins below tie the stepwise
+# oracle to it (exactly where the method is exact, by convergence where it
+# approximates) and check the traversal's lists and the tree independently.
+
+def test_taylor_coefficients_closed_forms_and_series():
+    r = np.array([0.7, -0.4, 1.1])
+    x, y, z = r
+    R = np.linalg.norm(r)
+    T = oracle.taylor(4, r)
+    idx = {m: i for i, m in enumerate(oracle.multi_indices(4))}
+    assert T[idx[(0, 0, 0)]] == pytest.approx(1 / R, rel=1e-15)
+    assert T[idx[(1, 0, 0)]] == pytest.approx(-x / R**3, rel=1e-14)
+    assert T[idx[(0, 0, 1)]] == pytest.approx(-z / R**3, rel=1e-14)
+    assert T[idx[(2, 0, 0)]] == pytest.approx((3 * x * x - R * R) / (2 * R**5), rel=1e-13)
+    assert T[idx[(1, 1, 0)]] == pytest.approx(3 * x * y / R**5, rel=1e-13)
+    assert T[idx[(1, 1, 1)]] == pytest.approx(-15 * x * y * z / R**7, rel=1e-13)
+    assert T[idx[(3, 0, 0)]] == pytest.approx(-(5 * x**3 - 3 * x * R * R) / (2 * R**7), rel=1e-13)
+    # generating function: sum_n T_n(r) h^n = 1/|r + h| for |h| < |r|, every order
+    p = 12
+    T = oracle.taylor(p, r)
+    h = np.array([0.05, 0.03, -0.04])
+    s = sum(T[i] * h[0]**a * h[1]**b * h[2]**c for i, (a, b, c) in enumerate(oracle.multi_indices(p)))
+    assert s == pytest.approx(1 / np.linalg.norm(r + h), rel=1e-13)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+def test_fmm_single_leaf_is_the_direct_sum(dist):
+    pos, q = inputs.fmm_points(64, dist)
+    phi, m2l, p2p, nc = oracle.fmm(pos, q, lists=True)
+    assert nc == 1 and len(m2l) == 0 and p2p.tolist() == [[0, 0]]
+    np.testing.assert_allclose(phi, oracle.direct(pos, q), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+def test_fmm_tiny_theta_is_the_direct_sum(dist):
+    pos, q = inputs.fmm_points(1500, dist)
+    phi, m2l, p2p, nc = oracle.fmm(pos, q, theta=1e-9, leaf_size=16, lists=True)
+    assert nc > 50 and len(m2l) == 0
+    d = oracle.direct(pos, q)
+    assert np.abs(phi - d).max() <= 1e-12 * np.abs(d).max()
+
+
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+def test_fmm_error_falls_with_expansion_order(dist):
+    pos, q = inputs.fmm_points(4096, dist)
+    d = oracle.direct(pos, q)
+    errs = [np.linalg.norm(oracle.fmm(pos, q, p=p) - d) / np.linalg.norm(d) for p in (2, 4, 6, 8)]
+    for lo, hi in zip(errs[1:], errs[:-1]):
+        assert lo < hi / 4
+    assert errs[-1] < 3e-6
+
+
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+def test_fmm_lists_cover_every_ordered_pair_once(dist):
+    n, theta = 700, 0.5
+    pos, q = inputs.fmm_points(n, dist)
+    _, m2l, p2p, nc = oracle.fmm(pos, q, p=2, theta=theta, leaf_size=16, lists=True)
+    cells, order = oracle.fmm_tree(pos, leaf_size=16)
+    assert len(cells) == nc
+    side = (pos.max(axis=0) - pos.min(axis=0)).max()
+    members = [order[int(c[1]):int(c[1] + c[2])] for c in cells]
+    cover = np.zeros((n, n), dtype=np.int32)
+    for a, b in m2l:
+        A, B = cells[a], cells[b]
+        hA, hB = side / 2.0 ** (A[0] + 1), side / 2.0 ** (B[0] + 1)
+        dist_ab = np.linalg.norm(A[5:8] - B[5:8])
+        assert (hA + hB) * math.sqrt(3.0) < theta * dist_ab * (1 + 1e-12)
+        cover[np.ix_(members[a], members[b])] += 1
+    for a, b in p2p:
+        assert cells[a, 3] < 0 and cells[b, 3] < 0
+        cover[np.ix_(members[a], members[b])] += 1
+    assert (cover == 1).all()
+
+
+def test_fmm_tree_invariants():
+    pos, q = inputs.fmm_points(5000, "plummer")
+    cells, order = oracle.fmm_tree(pos, leaf_size=64)
+    assert sorted(order.tolist()) == list(range(5000))
+    side = (pos.max(axis=0) - pos.min(axis=0)).max()
+    lvl = cells[:, 0]
+    assert (np.diff(lvl) >= 0).all()                       # breadth-first numbering
+    for i, c in enumerate(cells):
+        level, first, count, child, nchild = int(c[0]), int(c[1]), int(c[2]), int(c[3]), int(c[4])
+        h = side / 2.0 ** (level + 1)
+        pts = pos[order[first:first + count]]
+        assert (np.abs(pts - c[5:8]) <= h * (1 + 1e-12)).all()
+        if child < 0:
+            assert count <= 64 or level == 21
+        else:
+            assert count > 64 and 1 <= nchild <= 8
+            kids = cells[child:child + nchild]
+            assert (kids[:, 0] == level + 1).all()
+            assert kids[0, 1] == first and kids[:, 2].sum() == count
+            assert (kids[1:, 1] == kids[:-1, 1] + kids[:-1, 2]).all()
+
+
+def test_fmm_target_subset_matches_full_run():
+    pos, q = inputs.fmm_points(3000, "uniform")
+    full = oracle.fmm(pos, q)
+    tg = np.array([0, 17, 2999, 1234, 640], dtype=np.int64)
+    np.testing.assert_array_equal(oracle.fmm(pos, q, targets=tg), full[tg])
