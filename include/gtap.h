@@ -264,9 +264,9 @@ typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; 
  * owned, read only during the run).  Every DAG edge (u, v) of the root's
  * range (all edges: [0, m)) counts the
  * (k-2)-cliques of C = N+(u) n N+(v); a set larger than split_threshold
- * (<= 32, default 32) is materialised in the context's scratch arena
+ * (<= 64, default 64) is materialised in the context's scratch arena
  * (gtap_config.scratch_bytes) and forked into child tasks over its branch
- * range, smaller ones are counted in the lane with 32-bit bitsets.
+ * range, smaller ones are counted in the lane with 64-bit bitsets.
  * route 1: queue = recursion depth mod n_queues.  k in [3, 16].  Result: uint64 count. */
 typedef struct { const int64_t* off; const int32_t* adj; const int32_t* src;
                  int64_t edge_begin, edge_end;   /* the root counts DAG edges [edge_begin, edge_end) */
@@ -291,6 +291,91 @@ gtap_status gtap_kclique_orient(const int32_t* edges, int64_t m, int64_t n, int6
  * launch's duration and *ops_out the operations it performed. */
 gtap_status gtap_microbench(int kind, void* region, uint64_t region_bytes, int blocks, int threads, int iters,
                             float* ms_out, double* ops_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Laplace FMM pipeline (Sec. 6.4.1): adaptive octree construction, upward
+ * pass, interaction-list construction by dual-tree traversal (DTT) as
+ * block-mode tasks of the "fmm_dtt" program, then data-parallel M2L, downward
+ * pass and P2P/L2P.  phi_i approximates sum_{j != i} q_j / |x_i - x_j|.
+ *
+ * Readings fixed by this library (the paper leaves them open): the root cell
+ * is the bounding cube of the points; a cell with more than leaf_size points
+ * (and level < 21) splits into its non-empty octants, numbered breadth first
+ * in Morton order; expansions are Cartesian Taylor series of total order p
+ * about cell centres, M2L keeping the terms with |alpha| + |beta| <= p; the
+ * MAC accepts a pair (A, B), A != B, iff (R_A + R_B) < theta |c_A - c_B| with
+ * R the half-diagonal of the cell cube; a rejected pair of two leaves goes to
+ * the P2P list, otherwise the cell of lower level is split (both when the
+ * levels are equal).  Lists hold one-directional (target, source) pairs.
+ * ---------------------------------------------------------------------- */
+#define GTAP_FMM_FP64 0   /* every kernel in FP64 */
+#define GTAP_FMM_MIXED 1  /* P2M, M2L, L2P, P2P and the deeper M2M/L2L in FP32, the M2L and
+                             P2P sums compensated (Kahan); M2M/L2L into cells of the top
+                             fp64_levels levels in FP64.  Expansions are stored in FP64. */
+
+typedef struct {
+    int order;             /* expansion order p, 1..8 (default 6) */
+    int leaf_size;         /* points per leaf, 1..64 (default 64) */
+    double theta;          /* MAC parameter, 0 < theta < 1 (default 0.5) */
+    int precision;         /* GTAP_FMM_FP64 (default) or GTAP_FMM_MIXED */
+    int fp64_levels;       /* mixed form: translations whose parent is on a level below this
+                              number run in FP64 (default 3) */
+    int64_t m2l_capacity;  /* list capacities in entries; 0 = from the tree: ceil(64/theta^3)
+                              per cell and ceil(32/theta^3) per leaf, grown once on overflow */
+    int64_t p2p_capacity;
+    void* stream;          /* cudaStream_t of the data-parallel kernels; use the same stream as
+                              the traversal context (default: the legacy default stream) */
+} gtap_fmm_config;
+
+typedef struct {
+    int64_t n_points, n_cells, n_leaves;
+    int n_levels, order;
+    int64_t n_m2l, n_p2p;              /* entries produced by the last traversal */
+    int64_t m2l_capacity, p2p_capacity;
+    float ms_tree, ms_upward;          /* phases of the last build (CUDA events) */
+    float ms_traverse;                 /* the traversal's persistent kernel */
+    float ms_group, ms_m2l, ms_downward, ms_leaf;   /* phases of the last evaluation */
+} gtap_fmm_info;
+
+typedef struct gtap_fmm gtap_fmm;   /* opaque plan: tree, expansions, lists (device) */
+
+/* "fmm_dtt" root argument (block mode): traverse from the cell pair
+ * (target, source) of a built plan, appending to the plan's lists. */
+typedef struct { const gtap_fmm* plan; int32_t target, source; } gtap_fmm_dtt_args;
+
+/* Create a plan (cfg may be NULL for all defaults).  Builds the expansion
+ * tables; device memory is allocated by gtap_fmm_build as sizes become known.
+ * Errors: GTAP_ERR_INVALID_ARG, GTAP_ERR_NO_MEMORY. */
+gtap_status gtap_fmm_create(const gtap_fmm_config* cfg, gtap_fmm** out);
+/* Build the octree and the multipole expansions (octree, P2M, M2M) for n
+ * points: pos (device, n x 3 FP64, row-major) and q (device, n FP64), both
+ * caller owned and read during the call only.  1 <= n < 2^31; more than 64
+ * points sharing one cell of the deepest level (21) is GTAP_ERR_INVALID_ARG.  Grows the
+ * plan's device buffers when needed (cudaMalloc); returns after completion.
+ * Errors: GTAP_ERR_INVALID_ARG, GTAP_ERR_NO_MEMORY, GTAP_ERR_CUDA. */
+gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int64_t n);
+/* Build the M2L and P2P lists by running "fmm_dtt" from the root pair on ctx,
+ * a block-mode context (gtap_init(GTAP_MODE_BLOCK, 1, ...)); the context's
+ * pending roots are replaced.  On overflow the lists are grown to the sizes
+ * the run counted and the traversal is repeated once.  Errors: those of
+ * gtap_run/gtap_wait, GTAP_ERR_LIST_OVERFLOW, GTAP_ERR_INVALID_ARG (plan not
+ * built, or ctx not in block mode). */
+gtap_status gtap_fmm_traverse(gtap_fmm* f, gtap_ctx* ctx);
+/* M2L, L2L, L2P and P2P: writes phi (device, n FP64, input point order,
+ * caller owned).  Needs a completed traversal.  Returns after completion. */
+gtap_status gtap_fmm_evaluate(gtap_fmm* f, double* phi);
+/* gtap_fmm_build + gtap_fmm_traverse + gtap_fmm_evaluate. */
+gtap_status gtap_fmm_run(gtap_fmm* f, gtap_ctx* ctx, const double* pos, const double* q, int64_t n, double* phi);
+gtap_status gtap_fmm_get_info(const gtap_fmm* f, gtap_fmm_info* out);
+/* Host copies of the tree: info[n_cells][4] = {first, count, child_first or -1,
+ * level << 8 | n_children}, geom[n_cells][4] = {cx, cy, cz, half side} and
+ * order[n] (Morton position -> input index).  Any output may be NULL. */
+gtap_status gtap_fmm_copy_tree(const gtap_fmm* f, int32_t* info, double* geom, int32_t* order);
+/* Host copies of the lists as (target, source) int32 pairs: m2l[n_m2l][2],
+ * p2p[n_p2p][2] (either may be NULL).  GTAP_ERR_LIST_OVERFLOW if the last
+ * traversal overflowed. */
+gtap_status gtap_fmm_copy_lists(const gtap_fmm* f, int32_t* m2l, int32_t* p2p);
+gtap_status gtap_fmm_destroy(gtap_fmm* f);
 
 /* ------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart to this call.

@@ -14,6 +14,7 @@
 #include "gtap.h"
 #include "gtap_internal.h"
 #include "launch.h"
+#include "fmm_internal.h"
 
 using namespace gtap;
 
@@ -33,6 +34,7 @@ const ProgInfo kPrograms[] = {
     {"kclique", GTAP_MODE_THREAD, T_KCLIQUE_ROOT, PS_KCLIQUE},
     {"mergesort", GTAP_MODE_BLOCK, T_MSORT, PS_MSORT},
     {"integrate_block", GTAP_MODE_BLOCK, T_INTEGRATE_BLK, PS_INTEGRATE_BLK},
+    {"fmm_dtt", GTAP_MODE_BLOCK, T_DTT, PS_DTT},
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -376,6 +378,19 @@ static gtap_status make_root(gtap_ctx* c, int type, const void* args, size_t nby
         if (!(a.eps > 0.0)) return GTAP_ERR_INVALID_ARG;
         double p[4] = {a.a, a.b, a.eps, 0.0};
         put(p, sizeof(p));
+        return GTAP_OK;
+    }
+    case T_DTT: {
+        if (nbytes != sizeof(gtap_fmm_dtt_args)) return GTAP_ERR_INVALID_ARG;
+        gtap_fmm_dtt_args a;
+        std::memcpy(&a, args, sizeof(a));
+        fmm::DttEnv env;
+        gtap_status st = fmm::dtt_env(a.plan, a.target, a.source, &env);
+        if (st != GTAP_OK) return st;
+        struct { uint32_t root, n; unsigned long long pr; } p{
+            root_index, 1u, ((unsigned long long)(uint32_t)a.target << 32) | (uint32_t)a.source};
+        put(&p, sizeof(p));
+        std::memcpy(d->env, &env, sizeof(env));
         return GTAP_OK;
     }
     case T_MSORT: {

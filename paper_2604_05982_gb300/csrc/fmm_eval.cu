@@ -1,0 +1,593 @@
+// Data-parallel FMM kernels around the traversal (Sec. 6.4.1): upward pass
+// (P2M at leaves, M2M level by level), M2L over the interaction list grouped
+// by target cell, downward pass (L2L level by level) and the leaf kernel
+// (L2P + P2P over the near-field list).  Cartesian Taylor expansions of total
+// order p about the cell centres:
+//   P2M  M_a  = sum_j q_j (x_j - c)^a
+//   M2M  M_a(c) += sum_{b <= a} C(a, b) (c' - c)^(a-b) M_b(c')      (child c')
+//   M2L  L_b(A) += sum_{|a|+|b| <= p} (-1)^|a| C(a+b, b) T_{a+b}(c_A - c_B) M_a(B)
+//   L2L  L_g(c') += sum_{b >= g} C(b, g) (c' - c)^(b-g) L_b(c)       (child c')
+//   L2P  phi_i += sum_b L_b (x_i - c)^b
+//   P2P  phi_i += sum_{j != i} q_j / |x_i - x_j|
+// with T_n = d^n(1/r)/n! from the recurrence in fmm_internal.h.  R is the
+// arithmetic type: double, or float for the mixed form, where the per-target
+// sums of M2L and P2P are compensated (Kahan) and the translations into the
+// top levels stay in double.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "fmm_internal.h"
+#include "scan.cuh"
+
+namespace gtap {
+namespace fmm {
+namespace {
+
+template <class R> struct Ops;
+template <> struct Ops<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double rsq(double a) { return rsqrt(a); }
+    static __device__ __forceinline__ double coef(const TermEntry& t) { return t.coef64; }
+};
+template <> struct Ops<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float rsq(float a) { return rsqrtf(a); }
+    static __device__ __forceinline__ float coef(const TermEntry& t) { return t.coef32; }
+};
+
+// Compensated accumulator (Kahan) for float; plain sum for double.
+template <class R> struct Acc {
+    R s = 0, c = 0;
+    __device__ __forceinline__ void add(R v) {
+        if constexpr (sizeof(R) == 4) {
+            const R y = Ops<R>::sub(v, c);
+            const R t = Ops<R>::add(s, y);
+            c = Ops<R>::sub(Ops<R>::sub(t, s), y);
+            s = t;
+        } else {
+            s += v;
+        }
+    }
+};
+
+// Index table (a, b, c) -> coefficient, (p+1)^3 shorts, in shared memory.
+__device__ __forceinline__ void load_index(const Tables& tb, short* idx) {
+    const int p1 = tb.p + 1;
+    for (int i = threadIdx.x; i < p1 * p1 * p1; i += blockDim.x) idx[i] = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < tb.nt; i += blockDim.x) {
+        const short3 m = tb.mi[i];
+        idx[(m.x * p1 + m.y) * p1 + m.z] = (short)i;
+    }
+    __syncthreads();
+}
+
+// Monomials x^a y^b z^c of one displacement for every coefficient, by the
+// nested powers (no table of powers needed).
+template <class R>
+__device__ __forceinline__ void monomials(int p, const short* idx, R x, R y, R z, R* out) {
+    const int p1 = p + 1;
+    R xa = 1;
+    for (int a = 0; a <= p; ++a) {
+        R xab = xa;
+        for (int b = 0; a + b <= p; ++b) {
+            R t = xab;
+            for (int c = 0; a + b + c <= p; ++c) {
+                out[idx[(a * p1 + b) * p1 + c]] = t;
+                t = Ops<R>::mul(t, z);
+            }
+            xab = Ops<R>::mul(xab, y);
+        }
+        xa = Ops<R>::mul(xa, x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P2M: one block per leaf.  Point powers in shared memory, one thread per
+// coefficient summing over the leaf's points in order.
+template <class R>
+__global__ void k_p2m(EvalBufs e) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int p = e.p, nt = e.nt, p1 = p + 1;
+    R* pw = reinterpret_cast<R*>(sm_raw);              // [kMaxLeaf][3][p1]
+    R* qv = pw + kMaxLeaf * 3 * p1;                    // [kMaxLeaf]
+    short3* mi = reinterpret_cast<short3*>(qv + kMaxLeaf);
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) mi[i] = e.tab.mi[i];
+    for (int c = blockIdx.x; c < e.n_cells; c += gridDim.x) {
+        const int4 in = e.info[c];
+        if (in.z >= 0) continue;
+        const Dbl4 g = e.geom[c];
+        __syncthreads();
+        for (int k = threadIdx.x; k < in.y; k += blockDim.x) {
+            R d[3];
+            if constexpr (sizeof(R) == 4) {
+                const float4 pl = e.ploc[in.x + k];
+                d[0] = pl.x; d[1] = pl.y; d[2] = pl.z;
+                qv[k] = pl.w;
+            } else {
+                const Dbl4 pt = e.pts[in.x + k];
+                d[0] = __dsub_rn(pt.x, g.x); d[1] = __dsub_rn(pt.y, g.y); d[2] = __dsub_rn(pt.z, g.z);
+                qv[k] = pt.w;
+            }
+            for (int a = 0; a < 3; ++a) {
+                R v = 1;
+                pw[(k * 3 + a) * p1] = v;
+                for (int j = 1; j <= p; ++j) { v = Ops<R>::mul(v, d[a]); pw[(k * 3 + a) * p1 + j] = v; }
+            }
+        }
+        __syncthreads();
+        for (int a = threadIdx.x; a < nt; a += blockDim.x) {
+            const short3 m = mi[a];
+            Acc<R> acc;
+            for (int k = 0; k < in.y; ++k) {
+                const R t = Ops<R>::mul(Ops<R>::mul(Ops<R>::mul(qv[k], pw[(k * 3) * p1 + m.x]), pw[(k * 3 + 1) * p1 + m.y]),
+                                        pw[(k * 3 + 2) * p1 + m.z]);
+                acc.add(t);
+            }
+            e.M[(size_t)c * nt + a] = (double)acc.s - (double)acc.c;
+        }
+    }
+}
+
+// M2M for the parents of one level: one block per parent.
+template <class R>
+__global__ void k_m2m(EvalBufs e, int lo, int hi) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int p = e.p, nt = e.nt, p1 = p + 1;
+    R* mono = reinterpret_cast<R*>(sm_raw);            // [8][nt]
+    R* mc = mono + 8 * nt;                             // [8][nt]
+    short* idx = reinterpret_cast<short*>(mc + 8 * nt);
+    load_index(e.tab, idx);
+    for (int c = lo + blockIdx.x; c < hi; c += gridDim.x) {
+        const int4 in = e.info[c];
+        if (in.z < 0) continue;
+        const int nch = in.w & 0xFF, cf = in.z;
+        const Dbl4 g = e.geom[c];
+        __syncthreads();
+        if ((int)threadIdx.x < nch) {
+            const Dbl4 gc = e.geom[cf + threadIdx.x];
+            monomials<R>(p, idx, (R)__dsub_rn(gc.x, g.x), (R)__dsub_rn(gc.y, g.y), (R)__dsub_rn(gc.z, g.z),
+                         mono + threadIdx.x * nt);
+        }
+        for (int i = threadIdx.x; i < nch * nt; i += blockDim.x) mc[i] = (R)e.M[(size_t)cf * nt + i];
+        __syncthreads();
+        for (int a = threadIdx.x; a < nt; a += blockDim.x) {
+            const int t0 = e.tab.m2m_off[a], t1 = e.tab.m2m_off[a + 1];
+            Acc<R> acc;
+            for (int j = 0; j < nch; ++j) {
+                R s = 0;
+                for (int t = t0; t < t1; ++t) {
+                    const TermEntry te = e.tab.m2m_terms[t];
+                    s += Ops<R>::coef(te) * mono[j * nt + te.b] * mc[j * nt + te.a];
+                }
+                acc.add(s);
+            }
+            e.M[(size_t)c * nt + a] = (double)acc.s - (double)acc.c;
+        }
+    }
+    (void)p1;
+}
+
+// ---------------------------------------------------------------------------
+// M2L: one block per target cell; sources in batches of kSB.  The Taylor
+// coefficients of every source displacement are built degree by degree in
+// shared memory, then each thread owns one item (a run of <= kM2lChunk terms
+// of one output coefficient) and accumulates it over all sources.
+constexpr int kSB = 8;
+
+template <class R>
+__global__ void k_m2l(EvalBufs e) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int p = e.p, nt = e.nt;
+    R* T = reinterpret_cast<R*>(sm_raw);               // [kSB][nt]
+    R* Ms = T + kSB * nt;                              // [kSB][nt]
+    R* dv = Ms + kSB * nt;                             // [kSB][4]: dx, dy, dz, 1/r^2
+    R* accs = dv + kSB * 4;                            // [n_items]
+    R* c1 = accs + e.tab.n_m2l_items;                  // [p + 1]
+    R* c2 = c1 + (p + 1);
+    DerivEntry* der = reinterpret_cast<DerivEntry*>(c2 + (p + 1) + ((p + 1) & 1) + 2);
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) der[i] = e.tab.deriv[i];
+    for (int k = threadIdx.x; k <= p; k += blockDim.x) {
+        c1[k] = k ? (R)(2.0 * k - 1.0) / (R)k : (R)0;
+        c2[k] = k ? (R)(k - 1.0) / (R)k : (R)0;
+    }
+    // this thread's item, its terms cached in registers
+    const int it = threadIdx.x;
+    const bool has_item = it < e.tab.n_m2l_items;
+    int len = 0;
+    R cf[kM2lChunk];
+    uint8_t ta[kM2lChunk], tb[kM2lChunk];
+    if (has_item) {
+        const ItemEntry ie = e.tab.m2l_items[it];
+        len = ie.len;
+#pragma unroll
+        for (int j = 0; j < kM2lChunk; ++j) {
+            if (j < len) {
+                const TermEntry te = e.tab.m2l_terms[ie.first + j];
+                cf[j] = Ops<R>::coef(te);
+                ta[j] = te.a;
+                tb[j] = te.b;
+            } else {
+                cf[j] = 0; ta[j] = 0; tb[j] = 0;
+            }
+        }
+    }
+    for (int c = blockIdx.x; c < e.n_cells; c += gridDim.x) {
+        const int s0 = e.m2l_off[c], s1 = e.m2l_off[c + 1];
+        if (s0 == s1) continue;
+        const Dbl4 g = e.geom[c];
+        Acc<R> acc;
+        for (int b0 = s0; b0 < s1; b0 += kSB) {
+            const int nb = min(kSB, s1 - b0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < nb * nt; i += blockDim.x) {
+                const int s = i / nt, a = i - s * nt;
+                Ms[i] = (R)e.M[(size_t)e.m2l_src[b0 + s] * nt + a];
+            }
+            if ((int)threadIdx.x < nb) {
+                const Dbl4 gs = e.geom[e.m2l_src[b0 + threadIdx.x]];
+                const R x = (R)__dsub_rn(g.x, gs.x), y = (R)__dsub_rn(g.y, gs.y), z = (R)__dsub_rn(g.z, gs.z);
+                const R r2 = x * x + y * y + z * z;
+                R* d = dv + threadIdx.x * 4;
+                d[0] = x; d[1] = y; d[2] = z; d[3] = (R)1 / r2;
+                T[threadIdx.x * nt] = Ops<R>::rsq(r2);
+            }
+            __syncthreads();
+            for (int k = 1; k <= p; ++k) {
+                const int i0 = n_coef(k - 1), cnt = n_coef(k) - i0;
+                for (int w = threadIdx.x; w < nb * cnt; w += blockDim.x) {
+                    const int s = w / cnt, i = i0 + (w - s * cnt);
+                    const DerivEntry de = der[i];
+                    const R* Ts = T + s * nt;
+                    const R* d = dv + s * 4;
+                    R s1v = 0, s2v = 0;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (de.e1[q] >= 0) s1v += d[q] * Ts[de.e1[q]];
+                        if (de.e2[q] >= 0) s2v += Ts[de.e2[q]];
+                    }
+                    T[s * nt + i] = -(c1[k] * s1v + c2[k] * s2v) * d[3];
+                }
+                __syncthreads();
+            }
+            if (has_item) {
+                for (int s = 0; s < nb; ++s) {
+                    R part = 0;
+#pragma unroll
+                    for (int j = 0; j < kM2lChunk; ++j)
+                        if (j < len) part += cf[j] * T[s * nt + tb[j]] * Ms[s * nt + ta[j]];
+                    acc.add(part);
+                }
+            }
+        }
+        if (has_item) accs[it] = Ops<R>::sub(acc.s, acc.c);
+        __syncthreads();
+        for (int b = threadIdx.x; b < nt; b += blockDim.x) {
+            Acc<R> sum;
+            for (int i = e.tab.m2l_item_off[b]; i < e.tab.m2l_item_off[b + 1]; ++i) sum.add(accs[i]);
+            e.L[(size_t)c * nt + b] = (double)sum.s - (double)sum.c;
+        }
+    }
+}
+
+// L2L from the parents of one level into their children: one block per parent.
+template <class R>
+__global__ void k_l2l(EvalBufs e, int lo, int hi) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int p = e.p, nt = e.nt;
+    R* mono = reinterpret_cast<R*>(sm_raw);            // [8][nt]
+    R* lp = mono + 8 * nt;                             // [nt]
+    short* idx = reinterpret_cast<short*>(lp + nt);
+    load_index(e.tab, idx);
+    for (int c = lo + blockIdx.x; c < hi; c += gridDim.x) {
+        const int4 in = e.info[c];
+        if (in.z < 0) continue;
+        const int nch = in.w & 0xFF, cf = in.z;
+        const Dbl4 g = e.geom[c];
+        __syncthreads();
+        if ((int)threadIdx.x < nch) {
+            const Dbl4 gc = e.geom[cf + threadIdx.x];
+            monomials<R>(p, idx, (R)__dsub_rn(gc.x, g.x), (R)__dsub_rn(gc.y, g.y), (R)__dsub_rn(gc.z, g.z),
+                         mono + threadIdx.x * nt);
+        }
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) lp[i] = (R)e.L[(size_t)c * nt + i];
+        __syncthreads();
+        for (int w = threadIdx.x; w < nch * nt; w += blockDim.x) {
+            const int j = w / nt, gi = w - j * nt;
+            const int t0 = e.tab.l2l_off[gi], t1 = e.tab.l2l_off[gi + 1];
+            R s = 0;
+            for (int t = t0; t < t1; ++t) {
+                const TermEntry te = e.tab.l2l_terms[t];
+                s += Ops<R>::coef(te) * mono[j * nt + te.b] * lp[te.a];
+            }
+            e.L[(size_t)(cf + j) * nt + gi] += (double)s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf kernel: one block per leaf.  Threads are (target slot, source part):
+// each thread sums over every parts-th source point of the near-field list,
+// source points staged in shared memory in batches of up to kSrcBatch from
+// consecutive source leaves; then the parts are combined and L2P added.
+constexpr int kLeafBlock = 128;
+constexpr int kSrcBatch = 256;
+
+template <class R>
+__global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int p = e.p, nt = e.nt;
+    using R4 = typename std::conditional<sizeof(R) == 4, float4, Dbl4>::type;
+    R4* sp = reinterpret_cast<R4*>(sm_raw);             // [kSrcBatch] source x, y, z, q
+    int* sid = reinterpret_cast<int*>(sp + kSrcBatch);  // [kSrcBatch] sorted index
+    R* red = reinterpret_cast<R*>(sid + kSrcBatch);     // [kLeafBlock] (and a compensation array)
+    R* redc = red + kLeafBlock;
+    R* lsm = redc + kLeafBlock;                         // [nt]
+    int* bpre = reinterpret_cast<int*>(lsm + nt + (nt & 1));  // [33] prefix of the batch's source counts
+    int* bfirst = bpre + 34;                            // [32]
+    R* boff = reinterpret_cast<R*>(bfirst + 32);        // [32][3] source-centre offsets (mixed)
+    int* bnum = reinterpret_cast<int*>(boff + 96);      // [1]
+    short* idx = reinterpret_cast<short*>(bnum + 4);
+    load_index(e.tab, idx);
+    const int t = threadIdx.x, lane = t & 31;
+    for (int c = blockIdx.x; c < e.n_cells; c += gridDim.x) {
+        const int4 in = e.info[c];
+        if (in.z >= 0) continue;
+        const Dbl4 g = e.geom[c];
+        const int count = in.y;
+        const int tp = count <= 32 ? 32 : 64;
+        const int parts = kLeafBlock / tp;
+        const int slot = t % tp, part = t / tp;
+        const bool active = slot < count;
+        const int ki = in.x + (active ? slot : 0);
+        R xi, yi, zi;
+        if constexpr (sizeof(R) == 4) {
+            const float4 pl = e.ploc[ki];
+            xi = pl.x; yi = pl.y; zi = pl.z;
+        } else {
+            const Dbl4 pt = e.pts[ki];
+            xi = pt.x; yi = pt.y; zi = pt.z;
+        }
+        __syncthreads();
+        for (int i = t; i < nt; i += kLeafBlock) lsm[i] = (R)e.L[(size_t)c * nt + i];
+        Acc<R> acc;
+        const int s0 = e.p2p_off[c], s1 = e.p2p_off[c + 1];
+        int cur = s0;
+        while (cur < s1) {
+            __syncthreads();
+            if (t < 32) {
+                const int j = cur + lane;
+                int cnt = 0, first = 0;
+                Dbl4 gs = make_dbl4(0, 0, 0, 0);
+                if (j < s1) {
+                    const int sc = e.p2p_src[j];
+                    const int4 si = e.info[sc];
+                    cnt = si.y;
+                    first = si.x;
+                    gs = e.geom[sc];
+                }
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const unsigned fit = __ballot_sync(0xffffffffu, j < s1 && incl <= kSrcBatch);
+                const int nfit = max(1, __popc(fit));   // fit is a prefix of lanes; a leaf holds <= 64 points
+                if (lane < nfit) {
+                    bpre[lane + 1] = incl;
+                    bfirst[lane] = first;
+                    if constexpr (sizeof(R) == 4) {
+                        boff[lane * 3 + 0] = (R)__dsub_rn(gs.x, g.x);
+                        boff[lane * 3 + 1] = (R)__dsub_rn(gs.y, g.y);
+                        boff[lane * 3 + 2] = (R)__dsub_rn(gs.z, g.z);
+                    }
+                }
+                if (lane == 0) { bpre[0] = 0; bnum[0] = nfit; }
+            }
+            __syncthreads();
+            const int nfit = bnum[0];
+            const int total = bpre[nfit];
+            for (int i = t; i < total; i += kLeafBlock) {
+                int a = 0, b = nfit - 1;   // last source with bpre[s] <= i
+                while (a < b) {
+                    const int mid = (a + b + 1) >> 1;
+                    if (bpre[mid] <= i) a = mid; else b = mid - 1;
+                }
+                const int k = bfirst[a] + (i - bpre[a]);
+                sid[i] = k;
+                if constexpr (sizeof(R) == 4) {
+                    const float4 pl = e.ploc[k];
+                    sp[i] = make_float4(pl.x + boff[a * 3], pl.y + boff[a * 3 + 1], pl.z + boff[a * 3 + 2], pl.w);
+                } else {
+                    sp[i] = e.pts[k];
+                }
+            }
+            __syncthreads();
+            if (active) {
+                for (int j = part; j < total; j += parts) {
+                    if (sid[j] == ki) continue;
+                    const R4 s = sp[j];
+                    const R dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
+                    const R r2 = dx * dx + dy * dy + dz * dz;
+                    acc.add(s.w * Ops<R>::rsq(r2));
+                }
+            }
+            cur += nfit;
+        }
+        red[t] = acc.s;
+        redc[t] = acc.c;
+        __syncthreads();
+        if (part == 0 && active) {
+            Acc<R> tot;
+            tot.s = red[t];
+            tot.c = redc[t];
+            for (int q = 1; q < parts; ++q) tot.add(Ops<R>::sub(red[q * tp + slot], redc[q * tp + slot]));
+            // L2P
+            R pl = 0;
+            const int p1 = p + 1;
+            R xa = 1;
+            const R dx = (sizeof(R) == 4) ? xi : (R)__dsub_rn((double)xi, g.x);
+            const R dy = (sizeof(R) == 4) ? yi : (R)__dsub_rn((double)yi, g.y);
+            const R dz = (sizeof(R) == 4) ? zi : (R)__dsub_rn((double)zi, g.z);
+            for (int a = 0; a <= p; ++a) {
+                R xab = xa;
+                for (int b = 0; a + b <= p; ++b) {
+                    R m = xab;
+                    for (int cc = 0; a + b + cc <= p; ++cc) {
+                        pl += lsm[idx[(a * p1 + b) * p1 + cc]] * m;
+                        m *= dz;
+                    }
+                    xab *= dy;
+                }
+                xa *= dx;
+            }
+            e.phi[e.order[ki]] = (double)tot.s - (double)tot.c + (double)pl;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_group_count(const unsigned long long* list, long long count, int* cnt) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[(int)(list[i] >> 32)], 1);
+}
+
+__global__ void k_group_fill(const unsigned long long* list, long long count, const int* off, int* cursor, int* src) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long v = list[i];
+        const int tg = (int)(v >> 32);
+        src[off[tg] + atomicAdd(&cursor[tg], 1)] = (int)(v & 0xFFFFFFFFull);
+    }
+}
+
+int grid_for(long long n, int block, int cap) {
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+template <class R>
+size_t p2m_smem(int p, int nt) { return sizeof(R) * (kMaxLeaf * 3 * (p + 1) + kMaxLeaf) + sizeof(short3) * nt + 16; }
+template <class R>
+size_t m2m_smem(int p, int nt) { return sizeof(R) * 16 * nt + sizeof(short) * (p + 1) * (p + 1) * (p + 1) + 16; }
+template <class R>
+size_t l2l_smem(int p, int nt) { return sizeof(R) * 9 * nt + sizeof(short) * (p + 1) * (p + 1) * (p + 1) + 16; }
+template <class R>
+size_t m2l_smem(int p, int nt, int items) {
+    return sizeof(R) * (2 * kSB * nt + 4 * kSB + items + 2 * (p + 1) + ((p + 1) & 1) + 2) + sizeof(DerivEntry) * nt + 16;
+}
+template <class R>
+size_t leaf_smem(int p, int nt) {
+    const size_t r4 = (sizeof(R) == 4) ? sizeof(float4) : sizeof(Dbl4);
+    return r4 * kSrcBatch + sizeof(int) * kSrcBatch + sizeof(R) * (2 * kLeafBlock + nt + (nt & 1)) + sizeof(int) * 66 +
+           sizeof(R) * 96 + sizeof(int) * 4 + sizeof(short) * (p + 1) * (p + 1) * (p + 1) + 16;
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <class R>
+cudaError_t upward_level(const EvalBufs& e, int l, cudaStream_t s) {
+    const int lo = e.lstart[l], hi = e.lstart[l + 1];
+    if (hi <= lo) return cudaSuccess;
+    const size_t sm = m2m_smem<R>(e.p, e.nt);
+    cudaError_t err = set_smem(k_m2m<R>, sm);
+    if (err != cudaSuccess) return err;
+    k_m2m<R><<<grid_for(hi - lo, 1, 1 << 20), 128, sm, s>>>(e, lo, hi);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t downward_level(const EvalBufs& e, int l, cudaStream_t s) {
+    const int lo = e.lstart[l], hi = e.lstart[l + 1];
+    if (hi <= lo) return cudaSuccess;
+    const size_t sm = l2l_smem<R>(e.p, e.nt);
+    cudaError_t err = set_smem(k_l2l<R>, sm);
+    if (err != cudaSuccess) return err;
+    k_l2l<R><<<grid_for(hi - lo, 1, 1 << 20), 128, sm, s>>>(e, lo, hi);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_upward(const EvalBufs& e, bool mixed, int fp64_levels, cudaStream_t s) {
+    cudaError_t err;
+    const int grid = grid_for(e.n_cells, 1, 1 << 20);
+    if (mixed) {
+        const size_t sm = p2m_smem<float>(e.p, e.nt);
+        if ((err = set_smem(k_p2m<float>, sm)) != cudaSuccess) return err;
+        k_p2m<float><<<grid, 128, sm, s>>>(e);
+    } else {
+        const size_t sm = p2m_smem<double>(e.p, e.nt);
+        if ((err = set_smem(k_p2m<double>, sm)) != cudaSuccess) return err;
+        k_p2m<double><<<grid, 128, sm, s>>>(e);
+    }
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    for (int l = e.n_levels - 2; l >= 0; --l) {
+        err = (!mixed || l < fp64_levels) ? upward_level<double>(e, l, s) : upward_level<float>(e, l, s);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_m2l(const EvalBufs& e, bool mixed, cudaStream_t s) {
+    cudaError_t err;
+    const int grid = grid_for(e.n_cells, 1, 1 << 20);
+    const int block = (e.tab.n_m2l_items + 31) / 32 * 32;
+    if (mixed) {
+        const size_t sm = m2l_smem<float>(e.p, e.nt, e.tab.n_m2l_items);
+        if ((err = set_smem(k_m2l<float>, sm)) != cudaSuccess) return err;
+        k_m2l<float><<<grid, block, sm, s>>>(e);
+    } else {
+        const size_t sm = m2l_smem<double>(e.p, e.nt, e.tab.n_m2l_items);
+        if ((err = set_smem(k_m2l<double>, sm)) != cudaSuccess) return err;
+        k_m2l<double><<<grid, block, sm, s>>>(e);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_downward(const EvalBufs& e, bool mixed, int fp64_levels, cudaStream_t s) {
+    for (int l = 0; l + 1 < e.n_levels; ++l) {
+        cudaError_t err = (!mixed || l < fp64_levels) ? downward_level<double>(e, l, s) : downward_level<float>(e, l, s);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_leaf_eval(const EvalBufs& e, bool mixed, cudaStream_t s) {
+    cudaError_t err;
+    const int grid = grid_for(e.n_cells, 1, 1 << 20);
+    if (mixed) {
+        const size_t sm = leaf_smem<float>(e.p, e.nt);
+        if ((err = set_smem(k_leaf<float>, sm)) != cudaSuccess) return err;
+        k_leaf<float><<<grid, kLeafBlock, sm, s>>>(e);
+    } else {
+        const size_t sm = leaf_smem<double>(e.p, e.nt);
+        if ((err = set_smem(k_leaf<double>, sm)) != cudaSuccess) return err;
+        k_leaf<double><<<grid, kLeafBlock, sm, s>>>(e);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group(const unsigned long long* list, long long count, int n_cells, int* cnt, int* off, int* cursor,
+                         int* src, int* tile_sums, cudaStream_t s) {
+    cudaError_t err;
+    if ((err = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n_cells, s)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)n_cells, s)) != cudaSuccess) return err;
+    if (count > 0) k_group_count<<<grid_for(count, 256, 4096), 256, 0, s>>>(list, count, cnt);
+    if ((err = scan::exclusive(cnt, off, nullptr, n_cells, tile_sums, off + n_cells, s)) != cudaSuccess) return err;
+    if (count > 0) k_group_fill<<<grid_for(count, 256, 4096), 256, 0, s>>>(list, count, off, cursor, src);
+    return cudaGetLastError();
+}
+
+}  // namespace fmm
+}  // namespace gtap

@@ -2,6 +2,7 @@
 #include "launch.h"
 #include "gtap_device.cuh"
 #include "programs_block.cuh"
+#include "programs_dtt.cuh"
 
 namespace gtap {
 
@@ -18,6 +19,9 @@ struct BlockDispatch {
         case T_INTEGRATE_BLK:
             if constexpr ((PSET & PS_INTEGRATE_BLK) != 0) { integrate_blk_step<BS>(c); return; }
             break;
+        case T_DTT:
+            if constexpr ((PSET & PS_DTT) != 0) { dtt_step<BS>(c); return; }
+            break;
         default:
             break;
         }
@@ -31,9 +35,9 @@ __global__ void __launch_bounds__(BS, 768 / BS) block_kernel(KParams P) {
     block_mode_loop<BlockDispatch<PSET, BS>>(P, smem, BS);
 }
 
-constexpr unsigned PS_BLOCK_ALL = PS_MSORT | PS_INTEGRATE_BLK;
-#define GTAP_BLOCK_SETS(X) X(PS_MSORT, 256) X(PS_INTEGRATE_BLK, 256) X(PS_BLOCK_ALL, 256) \
-                           X(PS_MSORT, 128) X(PS_INTEGRATE_BLK, 128) X(PS_BLOCK_ALL, 128)
+constexpr unsigned PS_BLOCK_ALL = PS_MSORT | PS_INTEGRATE_BLK | PS_DTT;
+#define GTAP_BLOCK_SETS(X) X(PS_MSORT, 256) X(PS_INTEGRATE_BLK, 256) X(PS_DTT, 256) X(PS_BLOCK_ALL, 256) \
+                           X(PS_MSORT, 128) X(PS_INTEGRATE_BLK, 128) X(PS_DTT, 128) X(PS_BLOCK_ALL, 128)
 
 static const void* block_kernel_fn(unsigned pset, int bs) {
 #define X(S, B) if (pset == (S) && bs == (B)) return reinterpret_cast<const void*>(&block_kernel<(S), (B)>);
@@ -43,16 +47,18 @@ static const void* block_kernel_fn(unsigned pset, int bs) {
 }
 
 unsigned block_kernel_pset(unsigned registered) {
-    const unsigned singles[] = {PS_MSORT, PS_INTEGRATE_BLK};
+    const unsigned singles[] = {PS_MSORT, PS_INTEGRATE_BLK, PS_DTT};
     for (unsigned s : singles)
         if (registered != 0 && (registered & ~s) == 0) return s;
     return PS_BLOCK_ALL;
 }
 
-// Most children one block step can spawn: a forked merge spawns one piece per thread.
+// Most children one block step can spawn: a forked merge spawns one piece per
+// thread, a traversal task one child per kDttGroup frontier pairs.
 int block_kernel_maxspawn(unsigned pset, int bs) {
     int m = 2;
     if (pset & PS_MSORT) m = std::max(m, bs);
+    if (pset & PS_DTT) m = std::max(m, kDttMaxSpawn + 1);
     return m;
 }
 
@@ -60,12 +66,14 @@ size_t block_prog_smem(unsigned pset, int bs) {
     size_t b = 0;
     if (pset & PS_MSORT) b = std::max(b, (size_t)(2 * kMsPadded * 4 + 8 * 260));
     if (pset & PS_INTEGRATE_BLK) b = std::max(b, (size_t)(8 * bs));
+    if (pset & PS_DTT) b = std::max(b, sizeof(DttShared) + 16);
     return b;
 }
 
 uint32_t block_record_bytes(unsigned pset, int bs) {
     uint32_t r = 64;
     if (pset & PS_INTEGRATE_BLK) r = std::max<uint32_t>(r, bs == 128 ? integ_blk_record<128>() : integ_blk_record<256>());
+    if (pset & PS_DTT) r = std::max<uint32_t>(r, (uint32_t)(kHdrBytes + sizeof(fmm::DttSpawn)));
     return (r + 63u) & ~63u;
 }
 

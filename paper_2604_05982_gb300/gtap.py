@@ -87,6 +87,31 @@ class gtap_mergesort_args(ctypes.Structure):
                 ("n", ctypes.c_uint64), ("leaf", ctypes.c_uint32), ("merge_cutoff", ctypes.c_uint32)]
 
 
+class gtap_fmm_config(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("leaf_size", ctypes.c_int), ("theta", ctypes.c_double),
+                ("precision", ctypes.c_int), ("fp64_levels", ctypes.c_int), ("m2l_capacity", ctypes.c_int64),
+                ("p2p_capacity", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+
+
+class gtap_fmm_info(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_levels", ctypes.c_int), ("order", ctypes.c_int), ("n_m2l", ctypes.c_int64),
+                ("n_p2p", ctypes.c_int64), ("m2l_capacity", ctypes.c_int64), ("p2p_capacity", ctypes.c_int64)] + [
+        (n, ctypes.c_float) for n in ("ms_tree", "ms_upward", "ms_traverse", "ms_group", "ms_m2l", "ms_downward",
+                                      "ms_leaf")]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class gtap_fmm_dtt_args(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("target", ctypes.c_int32), ("source", ctypes.c_int32)]
+
+
+GTAP_FMM_FP64 = 0
+GTAP_FMM_MIXED = 1
+
+
 class gtap_completion(ctypes.Structure):
     _fields_ = [("req", ctypes.c_uint64), ("result", ctypes.c_uint64 * 2), ("status", ctypes.c_int32),
                 ("pad", ctypes.c_int32)]
@@ -117,6 +142,15 @@ _SIGS = {
     "gtap_debug_snapshot": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "gtap_mergesort_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P]),
     "gtap_kclique_orient": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P]),
+    "gtap_fmm_create": (ctypes.c_int, [ctypes.POINTER(gtap_fmm_config), ctypes.POINTER(_P)]),
+    "gtap_fmm_build": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
+    "gtap_fmm_traverse": (ctypes.c_int, [_P, _P]),
+    "gtap_fmm_evaluate": (ctypes.c_int, [_P, _P]),
+    "gtap_fmm_run": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    "gtap_fmm_get_info": (ctypes.c_int, [_P, ctypes.POINTER(gtap_fmm_info)]),
+    "gtap_fmm_copy_tree": (ctypes.c_int, [_P, _P, _P, _P]),
+    "gtap_fmm_copy_lists": (ctypes.c_int, [_P, _P, _P]),
+    "gtap_fmm_destroy": (ctypes.c_int, [_P]),
 }
 
 _lib = None
@@ -276,3 +310,47 @@ def gtap_microbench(kind: int, region: int, region_bytes: int, blocks: int, thre
     _check(load_library().gtap_microbench(kind, region, region_bytes, blocks, threads, iters, ctypes.byref(ms),
                                           ctypes.byref(ops), stream or None), "gtap_microbench")
     return ms.value, ops.value
+
+
+def gtap_fmm_create(cfg: gtap_fmm_config | None = None) -> int:
+    f = _P()
+    _check(load_library().gtap_fmm_create(ctypes.byref(cfg) if cfg else None, ctypes.byref(f)), "gtap_fmm_create")
+    return f.value
+
+
+def gtap_fmm_build(f: int, pos: int, q: int, n: int) -> None:
+    _check(load_library().gtap_fmm_build(f, pos, q, n), "gtap_fmm_build")
+
+
+def gtap_fmm_traverse(f: int, ctx: int) -> None:
+    _check(load_library().gtap_fmm_traverse(f, ctx), "gtap_fmm_traverse")
+
+
+def gtap_fmm_evaluate(f: int, phi: int) -> None:
+    _check(load_library().gtap_fmm_evaluate(f, phi), "gtap_fmm_evaluate")
+
+
+def gtap_fmm_run(f: int, ctx: int, pos: int, q: int, n: int, phi: int) -> None:
+    _check(load_library().gtap_fmm_run(f, ctx, pos, q, n, phi), "gtap_fmm_run")
+
+
+def gtap_fmm_get_info(f: int) -> gtap_fmm_info:
+    out = gtap_fmm_info()
+    _check(load_library().gtap_fmm_get_info(f, ctypes.byref(out)), "gtap_fmm_get_info")
+    return out
+
+
+def gtap_fmm_copy_tree(f: int, info, geom, order) -> None:
+    """Host numpy outputs (int32 [n_cells, 4], float64 [n_cells, 4], int32 [n]); any may be None."""
+    ptr = (lambda a: None if a is None else a.ctypes.data_as(_P))
+    _check(load_library().gtap_fmm_copy_tree(f, ptr(info), ptr(geom), ptr(order)), "gtap_fmm_copy_tree")
+
+
+def gtap_fmm_copy_lists(f: int, m2l, p2p) -> None:
+    """Host numpy outputs (int32 [n_m2l, 2], int32 [n_p2p, 2]); either may be None."""
+    ptr = (lambda a: None if a is None else a.ctypes.data_as(_P))
+    _check(load_library().gtap_fmm_copy_lists(f, ptr(m2l), ptr(p2p)), "gtap_fmm_copy_lists")
+
+
+def gtap_fmm_destroy(f: int) -> None:
+    _check(load_library().gtap_fmm_destroy(f), "gtap_fmm_destroy")

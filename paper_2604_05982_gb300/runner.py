@@ -167,3 +167,76 @@ def kclique(graphs, k: int, split_threshold: int = 64, n_queues: int = 1, route:
             hs.append(c.spawn(t, g.args(k, split_threshold, route, b, e), queue=0))
         c.run()
         return RunResult([c.result_u64(h) for h in hs], c.stats())
+
+
+class Fmm:
+    """A Laplace FMM plan plus the block-mode context its traversal runs on (marshalling only).
+
+    ``run(pos, q)`` takes host or CUDA arrays (n x 3 and n, FP64) and returns the
+    potentials as a CUDA float64 tensor in input order."""
+
+    def __init__(self, order: int = 6, leaf_size: int = 64, theta: float = 0.5, mixed: bool = False,
+                 fp64_levels: int = 3, threads_per_block: int = 128, pool_bytes: int = 1 << 30,
+                 deque_capacity: int = 4096, **cfg):
+        fc = G.gtap_fmm_config()
+        fc.order, fc.leaf_size, fc.theta = order, leaf_size, theta
+        fc.precision = G.GTAP_FMM_MIXED if mixed else G.GTAP_FMM_FP64
+        fc.fp64_levels = fp64_levels
+        self.plan = G.gtap_fmm_create(fc)
+        self.ctx = Context(G.GTAP_MODE_BLOCK, 1, pool_bytes=pool_bytes, threads_per_block=threads_per_block,
+                           deque_capacity=deque_capacity, **cfg)
+
+    def build(self, pos, q):
+        import torch
+        self.pos = torch.as_tensor(pos, dtype=torch.float64).reshape(-1, 3).contiguous().cuda()
+        self.q = torch.as_tensor(q, dtype=torch.float64).reshape(-1).contiguous().cuda()
+        self.n = int(self.q.shape[0])
+        torch.cuda.synchronize()
+        G.gtap_fmm_build(self.plan, self.pos.data_ptr(), self.q.data_ptr(), self.n)
+
+    def traverse(self):
+        G.gtap_fmm_traverse(self.plan, self.ctx.ctx)
+
+    def evaluate(self):
+        import torch
+        phi = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        G.gtap_fmm_evaluate(self.plan, phi.data_ptr())
+        return phi
+
+    def run(self, pos, q):
+        self.build(pos, q)
+        self.traverse()
+        return self.evaluate()
+
+    def info(self) -> dict:
+        return G.gtap_fmm_get_info(self.plan).as_dict()
+
+    def tree(self):
+        import numpy as np
+        inf = self.info()
+        nc = int(inf["n_cells"])
+        info = np.zeros((nc, 4), dtype=np.int32)
+        geom = np.zeros((nc, 4), dtype=np.float64)
+        order = np.zeros(self.n, dtype=np.int32)
+        G.gtap_fmm_copy_tree(self.plan, info, geom, order)
+        return info, geom, order
+
+    def lists(self):
+        import numpy as np
+        inf = self.info()
+        m2l = np.zeros((int(inf["n_m2l"]), 2), dtype=np.int32)
+        p2p = np.zeros((int(inf["n_p2p"]), 2), dtype=np.int32)
+        G.gtap_fmm_copy_lists(self.plan, m2l, p2p)
+        return m2l, p2p
+
+    def close(self):
+        if self.plan:
+            G.gtap_fmm_destroy(self.plan)
+            self.plan = None
+        self.ctx.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

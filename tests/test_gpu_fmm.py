@@ -1,0 +1,157 @@
+"""Laplace FMM on the GPU against the FP64 oracle FMM (GPU).
+
+The tree (cells, centres, point order) and the traversal's lists (as
+multisets of (target, source) pairs) must equal the oracle's exactly; the
+potentials must agree within the stated precision of each form: FP64 within
+1e-12 relative L2 (only summation order differs), the mixed form (FP32 M2L
+and P2P with compensated sums) within 1e-5 relative L2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_05982_gb300 import inputs, runner
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-5
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _pairs(a):
+    a = np.asarray(a, dtype=np.int64).reshape(-1, 2)
+    return np.sort(a[:, 0] << 32 | a[:, 1])
+
+
+def _check_tree(f, pos, leaf):
+    info, geom, order = f.tree()
+    cells, ref_order = oracle.fmm_tree(pos, leaf_size=leaf)
+    assert info.shape[0] == cells.shape[0]
+    assert np.array_equal(order, ref_order.astype(np.int32))
+    assert np.array_equal(info[:, 0], cells[:, 1].astype(np.int32))          # first
+    assert np.array_equal(info[:, 1], cells[:, 2].astype(np.int32))          # count
+    assert np.array_equal(info[:, 2], cells[:, 3].astype(np.int32))          # first child
+    assert np.array_equal(info[:, 3] >> 8, cells[:, 0].astype(np.int32))     # level
+    assert np.array_equal(info[:, 3] & 0xFF, cells[:, 4].astype(np.int32))   # children
+    assert np.array_equal(geom[:, :3], cells[:, 5:8])                        # centres, bit for bit
+
+
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_fmm_matches_oracle(dist, mixed):
+    n, p, theta, leaf = 20000, 6, 0.5, 64
+    pos, q = inputs.fmm_points(n, dist)
+    ref, m2l, p2p, nc = oracle.fmm(pos, q, p=p, theta=theta, leaf_size=leaf, lists=True)
+    with runner.Fmm(order=p, leaf_size=leaf, theta=theta, mixed=mixed) as f:
+        phi = f.run(pos, q).cpu().numpy()
+        _check_tree(f, pos, leaf)
+        g_m2l, g_p2p = f.lists()
+        assert np.array_equal(_pairs(g_m2l), _pairs(m2l))
+        assert np.array_equal(_pairs(g_p2p), _pairs(p2p))
+        info = f.info()
+        assert info["n_cells"] == nc and info["n_m2l"] == len(m2l) and info["n_p2p"] == len(p2p)
+    err = _rel_l2(phi, ref)
+    assert err <= (MIXED_TOL if mixed else FP64_TOL), err
+
+
+@pytest.mark.parametrize("p", [1, 3, 8])
+def test_fmm_other_orders(p):
+    pos, q = inputs.fmm_points(6000, "plummer")
+    ref = oracle.fmm(pos, q, p=p, theta=0.5, leaf_size=32)
+    for mixed in (False, True):
+        with runner.Fmm(order=p, leaf_size=32, theta=0.5, mixed=mixed) as f:
+            phi = f.run(pos, q).cpu().numpy()
+        assert _rel_l2(phi, ref) <= (MIXED_TOL if mixed else FP64_TOL)
+
+
+@pytest.mark.parametrize("n", [1, 2, 64, 65, 129, 1000])
+def test_fmm_small_and_ragged(n):
+    pos, q = inputs.fmm_points(n, "uniform", seed=11)
+    ref = oracle.fmm(pos, q, p=4, theta=0.5, leaf_size=16)
+    with runner.Fmm(order=4, leaf_size=16, theta=0.5) as f:
+        phi = f.run(pos, q).cpu().numpy()
+        _check_tree(f, pos, 16)
+    if n == 1:
+        assert phi[0] == 0.0
+    else:
+        assert _rel_l2(phi, ref) <= FP64_TOL
+
+
+def test_fmm_deep_traversal_small_theta_and_leaf():
+    pos, q = inputs.fmm_points(8000, "plummer", seed=5)
+    ref, m2l, p2p, _ = oracle.fmm(pos, q, p=4, theta=0.3, leaf_size=8, lists=True)
+    for tpb in (128, 256):
+        with runner.Fmm(order=4, leaf_size=8, theta=0.3, threads_per_block=tpb) as f:
+            phi = f.run(pos, q).cpu().numpy()
+            g_m2l, g_p2p = f.lists()
+        assert np.array_equal(_pairs(g_m2l), _pairs(m2l))
+        assert np.array_equal(_pairs(g_p2p), _pairs(p2p))
+        assert _rel_l2(phi, ref) <= FP64_TOL
+
+
+def test_fmm_list_capacity_overflow_is_regrown():
+    import ctypes
+    from paper_2604_05982_gb300 import gtap as G
+    pos, q = inputs.fmm_points(20000, "uniform")
+    ref, m2l, p2p, _ = oracle.fmm(pos, q, p=4, theta=0.5, lists=True)
+    cfg = G.gtap_fmm_config()
+    cfg.order, cfg.leaf_size, cfg.theta = 4, 64, 0.5
+    cfg.m2l_capacity, cfg.p2p_capacity = 100, 50
+    plan = G.gtap_fmm_create(cfg)
+    ctx = runner.Context(G.GTAP_MODE_BLOCK, 1, pool_bytes=1 << 28, threads_per_block=128, deque_capacity=4096)
+    try:
+        pt = torch.as_tensor(pos).cuda()
+        qt = torch.as_tensor(q).cuda()
+        phi = torch.empty(len(q), dtype=torch.float64, device="cuda")
+        G.gtap_fmm_run(plan, ctx.ctx, pt.data_ptr(), qt.data_ptr(), len(q), phi.data_ptr())
+        info = G.gtap_fmm_get_info(plan)
+        assert info.n_m2l == len(m2l) and info.m2l_capacity >= len(m2l) and info.p2p_capacity >= len(p2p)
+        assert _rel_l2(phi.cpu().numpy(), ref) <= FP64_TOL
+    finally:
+        G.gtap_fmm_destroy(plan)
+        ctx.close()
+
+
+def test_fmm_rejects_bad_arguments():
+    from paper_2604_05982_gb300 import gtap as G
+    for field, val in (("order", 9), ("leaf_size", 65), ("theta", 1.5), ("precision", 7)):
+        cfg = G.gtap_fmm_config()
+        setattr(cfg, field, val)
+        with pytest.raises(G.GtapError):
+            G.gtap_fmm_create(cfg)
+    # traversal on a thread-mode context is refused
+    with runner.Fmm(order=2) as f:
+        pos, q = inputs.fmm_points(500, "uniform")
+        f.build(pos, q)
+        tctx = runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=1 << 24)
+        try:
+            with pytest.raises(G.GtapError):
+                G.gtap_fmm_traverse(f.plan, tctx.ctx)
+        finally:
+            tctx.close()
+
+
+@pytest.mark.parametrize("dist", ["uniform", "plummer"])
+def test_fmm_full_size_sampled(dist):
+    """N = 2^20, p = 6, theta = 0.5, leaf 64: the whole tree and both lists equal
+    the oracle's; potentials at 256 sampled targets against the oracle FMM
+    evaluated at those targets (FP64 and mixed)."""
+    n = 1 << 20
+    pos, q = inputs.fmm_points(n, dist)
+    _, m2l, p2p, nc = oracle.fmm(pos, q, p=0, theta=0.5, leaf_size=64, lists=True, targets=np.array([0]))
+    tg = np.arange(0, n, n // 256, dtype=np.int64)
+    ref = oracle.fmm(pos, q, p=6, theta=0.5, leaf_size=64, targets=tg)
+    for mixed in (False, True):
+        with runner.Fmm(order=6, leaf_size=64, theta=0.5, mixed=mixed) as f:
+            phi = f.run(pos, q).cpu().numpy()
+            if not mixed:
+                _check_tree(f, pos, 64)
+                g_m2l, g_p2p = f.lists()
+                assert np.array_equal(_pairs(g_m2l), _pairs(m2l))
+                assert np.array_equal(_pairs(g_p2p), _pairs(p2p))
+        assert _rel_l2(phi[tg], ref) <= (MIXED_TOL if mixed else FP64_TOL)
