@@ -152,7 +152,7 @@ struct gtap_fmm {
     int cell_cap = 0;
     const uint32_t* order = nullptr;
     // expansions and lists
-    DBuf M, L, m2l, p2p, counters, gcnt, gcur, m2l_off, m2l_src, p2p_off, p2p_src;
+    DBuf M, L, m2l, p2p, counters, gcnt, gcur, m2l_off, m2l_src, p2p_off, p2p_src, ms;
     long long m2l_cap = 0, p2p_cap = 0;
 
     long long n = 0;
@@ -166,7 +166,7 @@ struct gtap_fmm {
     ~gtap_fmm() {
         DBuf* all[] = {&tab_dev, &keys0, &keys1, &vals0, &vals1, &pts, &ploc, &hist, &hist_scan, &tile_sums, &box,
                        &bbox_part, &geom, &info, &lstart, &lvl_n, &lvl_total, &cnt, &off, &bounds, &flags, &M, &L,
-                       &m2l, &p2p, &counters, &gcnt, &gcur, &m2l_off, &m2l_src, &p2p_off, &p2p_src};
+                       &m2l, &p2p, &counters, &gcnt, &gcur, &m2l_off, &m2l_src, &p2p_off, &p2p_src, &ms};
         for (DBuf* b : all) b->release();
         for (cudaEvent_t& e : ev)
             if (e) cudaEventDestroy(e);
@@ -213,6 +213,7 @@ EvalBufs eval_bufs(gtap_fmm* f, double* phi) {
     e.p2p_off = f->p2p_off.as<int>();
     e.p2p_src = f->p2p_src.as<int>();
     e.phi = phi;
+    e.m2l_ms = f->ms.p;
     return e;
 }
 
@@ -460,7 +461,8 @@ gtap_status gtap_fmm_evaluate(gtap_fmm* f, double* phi) {
         !f->m2l_off.ensure(sizeof(int) * (nc + 1)) || !f->p2p_off.ensure(sizeof(int) * (nc + 1)) ||
         !f->m2l_src.ensure(sizeof(int) * (size_t)std::max(f->n_m2l, 1ll)) ||
         !f->p2p_src.ensure(sizeof(int) * (size_t)std::max(f->n_p2p, 1ll)) ||
-        !f->tile_sums.ensure(sizeof(int) * (size_t)scan::tiles_for((long long)nc)))
+        !f->tile_sums.ensure(sizeof(int) * (size_t)scan::tiles_for((long long)nc)) ||
+        !f->ms.ensure(m2l_scratch_bytes(f->p, f->n_cells, f->mixed)))
         return GTAP_ERR_NO_MEMORY;
     cudaEventRecord(f->ev[3], f->s);
     if (launch_group(f->m2l.as<unsigned long long>(), f->n_m2l, f->n_cells, f->gcnt.as<int>(), f->m2l_off.as<int>(),

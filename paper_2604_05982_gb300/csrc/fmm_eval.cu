@@ -275,6 +275,241 @@ __global__ void k_m2l(EvalBufs e) {
     }
 }
 
+// M2L in FP32 with the whole expansion in registers, one warp per target
+// cell and one source cell per lane.  In the scaled variables
+//   Tt_n = n! T_n,   Mt_a = (-1)^|a| M_a / a!,   Lt_b = b! L_b
+// the translation is a plain correlation, Lt_b = sum_a Tt_{a+b} Mt_a, one FMA
+// per term, and the recurrence for Tt has compile-time coefficients:
+//   |n| r^2 Tt_n = -(2|n|-1) sum_i n_i x_i Tt_{n-e_i} - (|n|-1) sum_i n_i (n_i-1) Tt_{n-2e_i}.
+// The order P is a template parameter so that every index is a constant and
+// the compiler keeps Tt and Lt in registers.
+__host__ __device__ constexpr int cidx(int a, int b, int c) {
+    return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
+}
+__host__ __device__ constexpr float cfact(int n) { return n <= 1 ? 1.f : (float)n * cfact(n - 1); }
+__host__ __device__ constexpr int row_stride(int p) { return (n_coef(p) + 3) / 4 * 4; }
+
+template <int P>
+__device__ __forceinline__ void taylor_scaled(float x, float y, float z, float* T) {
+    const float r2 = x * x + y * y + z * z;
+    const float ir2 = 1.f / r2;
+    T[0] = rsqrtf(r2);
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {
+        const float ck = -(2.f * k - 1.f) / (float)k, dk = -((float)k - 1.f) / (float)k;
+#pragma unroll
+        for (int a = k; a >= 0; --a) {
+#pragma unroll
+            for (int b = k - a; b >= 0; --b) {
+                const int c = k - a - b;
+                float acc = 0.f;
+                if (a > 0) acc += (ck * a) * x * T[cidx(a - 1, b, c)];
+                if (b > 0) acc += (ck * b) * y * T[cidx(a, b - 1, c)];
+                if (c > 0) acc += (ck * c) * z * T[cidx(a, b, c - 1)];
+                if (a > 1) acc += (dk * a * (a - 1)) * T[cidx(a - 2, b, c)];
+                if (b > 1) acc += (dk * b * (b - 1)) * T[cidx(a, b - 2, c)];
+                if (c > 1) acc += (dk * c * (c - 1)) * T[cidx(a, b, c - 2)];
+                T[cidx(a, b, c)] = acc * ir2;
+            }
+        }
+    }
+}
+
+// Ms[cell][row_stride(P)] = (-1)^|a| M_a / a! in FP32.
+template <int P>
+__global__ void k_scale_m(const double* M, int n_cells, float* Ms) {
+    constexpr int N = n_coef(P), S = row_stride(P);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n_cells * S;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i / S), j = (int)(i - (long long)c * S);
+        float v = 0.f;
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int a = k; a >= 0; --a)
+#pragma unroll
+                for (int b = k - a; b >= 0; --b)
+                    if (j == cidx(a, b, k - a - b))
+                        v = (float)(M[(size_t)c * N + j] / (double)(cfact(a) * cfact(b) * cfact(k - a - b))) *
+                            ((k & 1) ? -1.f : 1.f);
+        Ms[i] = v;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_m2l_reg(EvalBufs e, const float* __restrict__ Ms) {
+    constexpr int N = n_coef(P), S = row_stride(P);
+    const int lane = threadIdx.x & 31;
+    const int tgt = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (tgt >= e.n_cells) return;
+    const int s0 = e.m2l_off[tgt], s1 = e.m2l_off[tgt + 1];
+    if (s0 == s1) return;
+    const Dbl4 g = e.geom[tgt];
+    float L[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[i] = 0.f;
+    for (int base = s0; base < s1; base += 32) {
+        const int s = base + lane;
+        const bool valid = s < s1;
+        const int src = valid ? e.m2l_src[s] : e.m2l_src[s0];
+        const Dbl4 gs = e.geom[src];
+        float x = (float)__dsub_rn(g.x, gs.x), y = (float)__dsub_rn(g.y, gs.y), z = (float)__dsub_rn(g.z, gs.z);
+        float T[N];
+        taylor_scaled<P>(x, y, z, T);
+        const float wgt = valid ? 1.f : 0.f;
+        const float4* row = reinterpret_cast<const float4*>(Ms + (size_t)src * S);
+        float4 mv = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k1 = 0; k1 <= P; ++k1)
+#pragma unroll
+            for (int a1 = k1; a1 >= 0; --a1)
+#pragma unroll
+                for (int b1 = k1 - a1; b1 >= 0; --b1) {
+                    const int c1 = k1 - a1 - b1;
+                    const int ia = cidx(a1, b1, c1);
+                    if ((ia & 3) == 0) mv = __ldg(row + ia / 4);
+                    const float m = wgt * ((ia & 3) == 0 ? mv.x : (ia & 3) == 1 ? mv.y : (ia & 3) == 2 ? mv.z : mv.w);
+#pragma unroll
+                    for (int k2 = 0; k2 <= P - k1; ++k2)
+#pragma unroll
+                        for (int a2 = k2; a2 >= 0; --a2)
+#pragma unroll
+                            for (int b2 = k2 - a2; b2 >= 0; --b2) {
+                                const int c2 = k2 - a2 - b2;
+                                L[cidx(a2, b2, c2)] = fmaf(T[cidx(a1 + a2, b1 + b2, c1 + c2)], m, L[cidx(a2, b2, c2)]);
+                            }
+                }
+    }
+    // sum the lanes' partial expansions, then lane (b mod 32) writes L_b = Lt_b / b!
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float v = L[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        L[i] = v;
+    }
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int a = k; a >= 0; --a)
+#pragma unroll
+            for (int b = k - a; b >= 0; --b) {
+                const int i = cidx(a, b, k - a - b);
+                if ((i & 31) == lane)
+                    e.L[(size_t)tgt * N + i] = (double)L[i] / (double)(cfact(a) * cfact(b) * cfact(k - a - b));
+            }
+}
+
+// FP64 M2L in the same scaled form: the local expansion stays in registers,
+// the Taylor coefficients of each lane's source go to the lane's column of a
+// shared-memory table (FP64 registers cannot hold both).  The FP64 pipe, not
+// the shared-memory bandwidth, bounds this kernel.
+template <int P>
+__global__ void k_scale_m64(const double* M, int n_cells, double* Ms) {
+    constexpr int N = n_coef(P), S = row_stride(P);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n_cells * S;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i / S), j = (int)(i - (long long)c * S);
+        double v = 0.0;
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int a = k; a >= 0; --a)
+#pragma unroll
+                for (int b = k - a; b >= 0; --b)
+                    if (j == cidx(a, b, k - a - b))
+                        v = M[(size_t)c * N + j] / ((double)cfact(a) * (double)cfact(b) * (double)cfact(k - a - b)) *
+                            ((k & 1) ? -1.0 : 1.0);
+        Ms[i] = v;
+    }
+}
+
+constexpr int kM2l64Warps = 4;
+
+template <int P>
+__global__ void __launch_bounds__(32 * kM2l64Warps) k_m2l_reg64(EvalBufs e, const double* __restrict__ Ms) {
+    constexpr int N = n_coef(P), S = row_stride(P);
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double* T = reinterpret_cast<double*>(sm_raw) + (size_t)wib * N * 32 + lane;   // T[i * 32]
+    const int tgt = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (tgt >= e.n_cells) return;
+    const int s0 = e.m2l_off[tgt], s1 = e.m2l_off[tgt + 1];
+    if (s0 == s1) return;
+    const Dbl4 g = e.geom[tgt];
+    double L[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[i] = 0.0;
+    for (int base = s0; base < s1; base += 32) {
+        const int s = base + lane;
+        const bool valid = s < s1;
+        const int src = valid ? e.m2l_src[s] : e.m2l_src[s0];
+        const Dbl4 gs = e.geom[src];
+        const double x = __dsub_rn(g.x, gs.x), y = __dsub_rn(g.y, gs.y), z = __dsub_rn(g.z, gs.z);
+        const double r2 = x * x + y * y + z * z;
+        const double ir2 = 1.0 / r2;
+        T[0] = rsqrt(r2);
+#pragma unroll
+        for (int k = 1; k <= P; ++k) {
+            const double ck = -(2.0 * k - 1.0) / (double)k, dk = -((double)k - 1.0) / (double)k;
+#pragma unroll
+            for (int a = k; a >= 0; --a)
+#pragma unroll
+                for (int b = k - a; b >= 0; --b) {
+                    const int c = k - a - b;
+                    double acc = 0.0;
+                    if (a > 0) acc += (ck * a) * x * T[32 * cidx(a - 1, b, c)];
+                    if (b > 0) acc += (ck * b) * y * T[32 * cidx(a, b - 1, c)];
+                    if (c > 0) acc += (ck * c) * z * T[32 * cidx(a, b, c - 1)];
+                    if (a > 1) acc += (dk * a * (a - 1)) * T[32 * cidx(a - 2, b, c)];
+                    if (b > 1) acc += (dk * b * (b - 1)) * T[32 * cidx(a, b - 2, c)];
+                    if (c > 1) acc += (dk * c * (c - 1)) * T[32 * cidx(a, b, c - 2)];
+                    T[32 * cidx(a, b, c)] = acc * ir2;
+                }
+        }
+        const double wgt = valid ? 1.0 : 0.0;
+        const double2* row = reinterpret_cast<const double2*>(Ms + (size_t)src * S);
+        double2 mv = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int k1 = 0; k1 <= P; ++k1)
+#pragma unroll
+            for (int a1 = k1; a1 >= 0; --a1)
+#pragma unroll
+                for (int b1 = k1 - a1; b1 >= 0; --b1) {
+                    const int c1 = k1 - a1 - b1;
+                    const int ia = cidx(a1, b1, c1);
+                    if ((ia & 1) == 0) mv = __ldg(row + ia / 2);
+                    const double m = wgt * ((ia & 1) == 0 ? mv.x : mv.y);
+#pragma unroll
+                    for (int k2 = 0; k2 <= P - k1; ++k2)
+#pragma unroll
+                        for (int a2 = k2; a2 >= 0; --a2)
+#pragma unroll
+                            for (int b2 = k2 - a2; b2 >= 0; --b2) {
+                                const int c2 = k2 - a2 - b2;
+                                L[cidx(a2, b2, c2)] = fma(T[32 * cidx(a1 + a2, b1 + b2, c1 + c2)], m, L[cidx(a2, b2, c2)]);
+                            }
+                }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double v = L[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        L[i] = v;
+    }
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+        for (int a = k; a >= 0; --a)
+#pragma unroll
+            for (int b = k - a; b >= 0; --b) {
+                const int i = cidx(a, b, k - a - b);
+                if ((i & 31) == lane)
+                    e.L[(size_t)tgt * N + i] = L[i] / ((double)cfact(a) * (double)cfact(b) * (double)cfact(k - a - b));
+            }
+}
+
 // L2L from the parents of one level into their children: one block per parent.
 template <class R>
 __global__ void k_l2l(EvalBufs e, int lo, int hi) {
@@ -539,8 +774,42 @@ cudaError_t launch_upward(const EvalBufs& e, bool mixed, int fp64_levels, cudaSt
     return cudaSuccess;
 }
 
+template <int P>
+cudaError_t launch_m2l_reg(const EvalBufs& e, float* ms, cudaStream_t s) {
+    k_scale_m<P><<<grid_for((long long)e.n_cells * row_stride(P), 256, 4096), 256, 0, s>>>(e.M, e.n_cells, ms);
+    k_m2l_reg<P><<<grid_for((long long)e.n_cells * 32, 128, 1 << 30), 128, 0, s>>>(e, ms);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_m2l_reg64(const EvalBufs& e, double* ms, cudaStream_t s) {
+    k_scale_m64<P><<<grid_for((long long)e.n_cells * row_stride(P), 256, 4096), 256, 0, s>>>(e.M, e.n_cells, ms);
+    const size_t sm = sizeof(double) * n_coef(P) * 32 * kM2l64Warps;
+    cudaError_t err = set_smem(k_m2l_reg64<P>, sm);
+    if (err != cudaSuccess) return err;
+    k_m2l_reg64<P><<<grid_for((long long)e.n_cells * 32, 32 * kM2l64Warps, 1 << 30), 32 * kM2l64Warps, sm, s>>>(e, ms);
+    return cudaGetLastError();
+}
+
+// Scratch for the scaled multipoles: FP32 rows (mixed) or FP64 rows, in bytes.
+size_t m2l_scratch_bytes(int p, int n_cells, bool mixed) {
+    return (size_t)n_cells * row_stride(p) * (mixed ? sizeof(float) : sizeof(double));
+}
+
 cudaError_t launch_m2l(const EvalBufs& e, bool mixed, cudaStream_t s) {
     cudaError_t err;
+    if (e.m2l_ms != nullptr && e.p <= 6) {
+        float* f32 = static_cast<float*>(e.m2l_ms);
+        double* f64 = static_cast<double*>(e.m2l_ms);
+        switch (e.p) {
+        case 1: return mixed ? launch_m2l_reg<1>(e, f32, s) : launch_m2l_reg64<1>(e, f64, s);
+        case 2: return mixed ? launch_m2l_reg<2>(e, f32, s) : launch_m2l_reg64<2>(e, f64, s);
+        case 3: return mixed ? launch_m2l_reg<3>(e, f32, s) : launch_m2l_reg64<3>(e, f64, s);
+        case 4: return mixed ? launch_m2l_reg<4>(e, f32, s) : launch_m2l_reg64<4>(e, f64, s);
+        case 5: return mixed ? launch_m2l_reg<5>(e, f32, s) : launch_m2l_reg64<5>(e, f64, s);
+        default: return mixed ? launch_m2l_reg<6>(e, f32, s) : launch_m2l_reg64<6>(e, f64, s);
+        }
+    }
     const int grid = grid_for(e.n_cells, 1, 1 << 20);
     const int block = (e.tab.n_m2l_items + 31) / 32 * 32;
     if (mixed) {

@@ -155,7 +155,9 @@ struct EvalBufs {
     const int* p2p_off;
     const int* p2p_src;
     double* phi;                  // output, input order
+    void* m2l_ms;                 // scaled multipoles for M2L (FP32 rows mixed, FP64 rows otherwise)
 };
+size_t m2l_scratch_bytes(int p, int n_cells, bool mixed);
 cudaError_t launch_upward(const EvalBufs& e, bool mixed, int fp64_levels, cudaStream_t s);
 cudaError_t launch_m2l(const EvalBufs& e, bool mixed, cudaStream_t s);
 cudaError_t launch_downward(const EvalBufs& e, bool mixed, int fp64_levels, cudaStream_t s);
