@@ -258,9 +258,31 @@ def cpu_baseline():
                       f"(single thread, {secs:.2f} s)"}
 
 
+def run_reference_fmm(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(min(args.warmup, 1)):
+        _fmm_cpu_sample()
+    times = [_fmm_cpu_sample() for _ in range(args.steps)]
+    secs = sum(times) / len(times)
+    value = secs * 1e3 * FMM_N / FMM_CPU_SAMPLE_N
+    line = {"impl": "reference", "metric": "FMM time", "value": value, "unit": "ms/instance", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2 * value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Laplace FMM N=2^20, p={FMM_P}, theta={FMM_THETA}, leaf {FMM_LEAF} (oracle)"},
+            "cpu_baseline": {"value": value, "unit": "ms/instance", "cores": 1, "kind": "oracle",
+                             "sample": "oracle FMM on the first 2^16 uniform points per step, scaled x16"},
+            "e2e": {"value": value, "unit": "ms/instance", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
+        return
+    if args.workload == "fmm":
+        run_reference_fmm(args)
         return
     import oracle
     oracle.build()
@@ -281,6 +303,189 @@ def run_reference(args):
                              "sample": "full step per iteration, single thread"},
             "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+FMM_N = 1 << 20
+FMM_P = 6
+FMM_THETA = 0.5
+FMM_LEAF = 64
+FMM_SETS = ("uniform", "plummer")
+FMM_CPU_SAMPLE_N = 1 << 16
+FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (GB300)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64, nominal
+
+
+def m2l_flops_per_pair(p: int) -> int:
+    """Arithmetic of one M2L translation as the kernel performs it: the Taylor
+    recurrence (3 flops per first-order term, 2 per second-order term, 1 for the
+    final scaling, plus r^2, 1/r^2 and 1/r) and one FMA per (alpha, beta) term."""
+    fl = 7
+    for k in range(1, p + 1):
+        for a in range(k, -1, -1):
+            for b in range(k - a, -1, -1):
+                n = (a, b, k - a - b)
+                fl += 3 * sum(1 for x in n if x > 0) + 2 * sum(1 for x in n if x > 1) + 1
+    terms = sum(1 for k1 in range(p + 1) for _ in range((k1 + 1) * (k1 + 2) // 2)
+                for k2 in range(p - k1 + 1) for _ in range((k2 + 1) * (k2 + 2) // 2))
+    return fl + 2 * terms
+
+
+def _fmm_kernels_per_instance(n_levels: int, mixed: bool) -> int:
+    tree = 2 + 1 + 8 * 5 + 21 * 5 + 1 + (1 if mixed else 0)
+    upward = 1 + max(n_levels - 1, 0)
+    traverse = 2
+    evaluate = 2 * 5 + 2 + max(n_levels - 1, 0) + 1
+    return tree + upward + traverse + evaluate
+
+
+def run_fmm(args):
+    import numpy as np
+    import torch
+
+    from paper_2604_05982_gb300 import gtap as G
+    from paper_2604_05982_gb300 import inputs, runner
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    mixed = args.fmm_precision == "mixed"
+    sets = {}
+    for dist in FMM_SETS:
+        pos, q = inputs.fmm_points(FMM_N, dist, seed=3)
+        f = runner.Fmm(order=FMM_P, leaf_size=FMM_LEAF, theta=FMM_THETA, mixed=mixed)
+        sets[dist] = dict(pos_h=pos, q_h=q, f=f, pos=torch.from_numpy(pos).cuda(), q=torch.from_numpy(q).cuda(),
+                          phi=torch.empty(FMM_N, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+
+    def instance(d):
+        f = d["f"]
+        G.gtap_fmm_build(f.plan, d["pos"].data_ptr(), d["q"].data_ptr(), FMM_N)
+        G.gtap_fmm_traverse(f.plan, f.ctx.ctx)
+        G.gtap_fmm_evaluate(f.plan, d["phi"].data_ptr())
+
+    def step():
+        for d in sets.values():
+            instance(d)
+
+    for _ in range(args.warmup):
+        step()
+    # parity spot check of this exact configuration (outside the timed region): 64 sampled
+    # targets against the FP64 oracle FMM evaluated at those targets
+    import oracle
+    tg = np.arange(0, FMM_N, FMM_N // 64, dtype=np.int64)
+    errs = {}
+    for dist, d in sets.items():
+        ref = oracle.fmm(d["pos_h"], d["q_h"], p=FMM_P, theta=FMM_THETA, leaf_size=FMM_LEAF, targets=tg)
+        got = d["phi"].cpu().numpy()[tg]
+        errs[dist] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        assert errs[dist] <= (1e-5 if mixed else 1e-12), errs
+    phases = {dist: [] for dist in sets}
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            for dist, d in sets.items():
+                instance(d)
+                phases[dist].append(d["f"].info())
+        e1.record()
+        torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    ms_per_instance = elapsed_ms / (args.steps * len(sets))
+
+    # end to end through the public calls with host buffers: pinned H2D of positions and
+    # charges, the three calls, D2H of the potentials
+    pinned = {dist: (torch.from_numpy(d["pos_h"]).pin_memory(), torch.from_numpy(d["q_h"]).pin_memory(),
+                     torch.empty(FMM_N, dtype=torch.float64).pin_memory()) for dist, d in sets.items()}
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(args.steps):
+        for dist, d in sets.items():
+            ph, qh, out = pinned[dist]
+            d["pos"].copy_(ph, non_blocking=True)
+            d["q"].copy_(qh, non_blocking=True)
+            instance(d)
+            out.copy_(d["phi"], non_blocking=True)
+    e3.record()
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3) / (args.steps * len(sets))
+
+    def med(dist, key):
+        v = sorted(x[key] for x in phases[dist])
+        return v[len(v) // 2]
+
+    keys = ("ms_tree", "ms_upward", "ms_traverse", "ms_group", "ms_m2l", "ms_downward", "ms_leaf")
+    breakdown = {dist: {k: med(dist, k) for k in keys} for dist in sets}
+    info = {dist: phases[dist][-1] for dist in sets}
+    # roofline of the dominant kernel (M2L): ALU bound, peak from unit counts and the maximum clock
+    fl = m2l_flops_per_pair(FMM_P)
+    pairs = sum(info[dd]["n_m2l"] for dd in sets)
+    m2l_ms = sum(breakdown[dd]["ms_m2l"] for dd in sets)
+    achieved = pairs * fl / (m2l_ms / 1e3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            sm_mhz = float(json.load(fh)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        sm_mhz = 2070.0
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    if mixed:
+        peak = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        peak_kind = f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_mhz:.0f} MHz"
+    else:
+        peak = FP64_NOMINAL_TFLOPS
+        peak_kind = "nominal GB300 FP64"
+    launches = sum(_fmm_kernels_per_instance(info[dd]["n_levels"], mixed) for dd in sets) * args.steps
+    line = {
+        "metric": "FMM time", "value": ms_per_instance, "unit": "ms/instance", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"Laplace FMM N=2^20 (uniform cube and Plummer a=1 r<=10, seed 3, q~U(-1,1)), "
+                               f"p={FMM_P}, theta={FMM_THETA}, leaf {FMM_LEAF}, block-mode DTT; "
+                               f"{'mixed: FP32 P2P/M2L, FP64 top-level M2M/L2L' if mixed else 'plain FP64'}; "
+                               "one step = both point sets end to end (tree, upward, DTT, M2L, downward, P2P/L2P)",
+                   "l2": "positions 24 MiB + lists ~300 MiB per instance; the tree and lists are rebuilt every instance",
+                   "parallelism": "replicas"},
+        "breakdown_ms": breakdown,
+        "dtt_ms": {dd: breakdown[dd]["ms_traverse"] for dd in sets},
+        "lists": {dd: {"m2l": info[dd]["n_m2l"], "p2p": info[dd]["n_p2p"], "cells": info[dd]["n_cells"],
+                       "levels": info[dd]["n_levels"]} for dd in sets},
+        "rel_l2_vs_oracle_fmm_64_targets": errs,
+        "roofline": {"bound": "alu", "kernel": "k_m2l_reg (M2L)", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_flops_per_pair": fl},
+        "e2e": {"value": e2e_ms, "unit": "ms/instance", "h2d_bytes_per_step": len(sets) * FMM_N * 32,
+                "d2h_bytes_per_step": len(sets) * FMM_N * 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs = _fmm_cpu_sample()
+        line["cpu_baseline"] = {"value": secs * 1e3 * FMM_N / FMM_CPU_SAMPLE_N, "unit": "ms/instance", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"oracle FMM (FP64, same p/theta/leaf) on the first 2^16 points of the "
+                                          f"uniform set, {secs:.2f} s single thread, scaled x16 to N=2^20 "
+                                          "(cost linear in N at fixed leaf size)"}
+    for d in sets.values():
+        d["f"].close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _fmm_cpu_sample():
+    import oracle
+    from paper_2604_05982_gb300 import inputs
+    oracle.build()
+    try:
+        os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    except (AttributeError, OSError):
+        pass
+    pos, q = inputs.fmm_points(FMM_N, "uniform", seed=3)
+    pos, q = pos[:FMM_CPU_SAMPLE_N].copy(), q[:FMM_CPU_SAMPLE_N].copy()
+    t0 = time.perf_counter()
+    oracle.fmm(pos, q, p=FMM_P, theta=FMM_THETA, leaf_size=FMM_LEAF)
+    return time.perf_counter() - t0
 
 
 SERVE_REQUESTS = 20000
@@ -415,9 +620,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gtap", choices=["gtap", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="integer", choices=["integer", "serve"],
-                    help="integer: the default bench line; serve: the served mixed stream")
+    ap.add_argument("--workload", default="integer", choices=["integer", "serve", "fmm"],
+                    help="integer: the default bench line; serve: the served mixed stream; fmm: Laplace FMM")
     ap.add_argument("--requests", type=int, default=SERVE_REQUESTS)
+    ap.add_argument("--fmm-precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -425,6 +631,8 @@ def main():
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "fmm":
+        run_fmm(args)
     else:
         run_gpu(args)
 

@@ -147,8 +147,9 @@ struct gtap_fmm {
     DBuf tab_dev;
 
     // tree
-    DBuf keys0, keys1, vals0, vals1, pts, ploc, hist, hist_scan, tile_sums, box, bbox_part, geom, info, lstart, lvl_n,
-        lvl_total, cnt, off, bounds, flags;
+    DBuf keys0, keys1, vals0, vals1, pts, ploc, hist, hist_scan, tile_sums, box, bbox_part, geom, info, lat, lstart,
+        lvl_n, lvl_total, cnt, off, bounds, flags;
+    double box_h[8] = {};
     int cell_cap = 0;
     const uint32_t* order = nullptr;
     // expansions and lists
@@ -165,7 +166,7 @@ struct gtap_fmm {
 
     ~gtap_fmm() {
         DBuf* all[] = {&tab_dev, &keys0, &keys1, &vals0, &vals1, &pts, &ploc, &hist, &hist_scan, &tile_sums, &box,
-                       &bbox_part, &geom, &info, &lstart, &lvl_n, &lvl_total, &cnt, &off, &bounds, &flags, &M, &L,
+                       &bbox_part, &geom, &info, &lat, &lstart, &lvl_n, &lvl_total, &cnt, &off, &bounds, &flags, &M, &L,
                        &m2l, &p2p, &counters, &gcnt, &gcur, &m2l_off, &m2l_src, &p2p_off, &p2p_src, &ms};
         for (DBuf* b : all) b->release();
         for (cudaEvent_t& e : ev)
@@ -201,6 +202,8 @@ EvalBufs eval_bufs(gtap_fmm* f, double* phi) {
     e.n = f->n;
     e.geom = f->geom.as<Dbl4>();
     e.info = f->info.as<int4>();
+    e.lat = f->lat.as<int4>();
+    e.lat_unit = (float)(f->box_h[3] / 4194304.0);
     e.lstart = f->lstart_h;
     e.pts = f->pts.as<Dbl4>();
     e.ploc = f->ploc.as<float4>();
@@ -322,7 +325,8 @@ gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int6
     for (int attempt = 0;; ++attempt) {
         if (cap >= (1ll << 31) / 9) return GTAP_ERR_NO_MEMORY;
         const size_t C = (size_t)cap;
-        if (!f->geom.ensure(sizeof(Dbl4) * C) || !f->info.ensure(sizeof(int4) * C) || !f->cnt.ensure(sizeof(int) * C) ||
+        if (!f->geom.ensure(sizeof(Dbl4) * C) || !f->info.ensure(sizeof(int4) * C) || !f->lat.ensure(sizeof(int4) * C) ||
+            !f->cnt.ensure(sizeof(int) * C) ||
             !f->off.ensure(sizeof(int) * C) || !f->bounds.ensure(sizeof(int) * 9 * C) ||
             !f->tile_sums.ensure(sizeof(int) * (size_t)scan::tiles_for(std::max<long long>(cap, 256ll * ntiles))))
             return GTAP_ERR_NO_MEMORY;
@@ -343,6 +347,7 @@ gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int6
         b.tile_sums = f->tile_sums.as<int>();
         b.geom = f->geom.as<Dbl4>();
         b.info = f->info.as<int4>();
+        b.lat = f->lat.as<int4>();
         b.cap_cells = (int)cap;
         b.lstart = f->lstart.as<int>();
         b.lvl_n = f->lvl_n.as<int>();
@@ -357,6 +362,7 @@ gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int6
         int flags[4] = {0, 0, 0, 0};
         if (cudaMemcpyAsync(flags, f->flags.p, sizeof(flags), cudaMemcpyDeviceToHost, f->s) != cudaSuccess ||
             cudaMemcpyAsync(f->lstart_h, f->lstart.p, sizeof(f->lstart_h), cudaMemcpyDeviceToHost, f->s) != cudaSuccess ||
+            cudaMemcpyAsync(f->box_h, f->box.p, sizeof(f->box_h), cudaMemcpyDeviceToHost, f->s) != cudaSuccess ||
             cudaStreamSynchronize(f->s) != cudaSuccess)
             return GTAP_ERR_CUDA;
         f->order = b.order;

@@ -292,8 +292,9 @@ __host__ __device__ constexpr int row_stride(int p) { return (n_coef(p) + 3) / 4
 template <int P>
 __device__ __forceinline__ void taylor_scaled(float x, float y, float z, float* T) {
     const float r2 = x * x + y * y + z * z;
-    const float ir2 = 1.f / r2;
-    T[0] = rsqrtf(r2);
+    const float ir = rsqrtf(r2);
+    const float ir2 = ir * ir;
+    T[0] = ir;
 #pragma unroll
     for (int k = 1; k <= P; ++k) {
         const float ck = -(2.f * k - 1.f) / (float)k, dk = -((float)k - 1.f) / (float)k;
@@ -344,7 +345,9 @@ __global__ void __launch_bounds__(128) k_m2l_reg(EvalBufs e, const float* __rest
     if (tgt >= e.n_cells) return;
     const int s0 = e.m2l_off[tgt], s1 = e.m2l_off[tgt + 1];
     if (s0 == s1) return;
-    const Dbl4 g = e.geom[tgt];
+    // exact integer displacement on the level-21 lattice, one FP32 scaling
+    const int4 lt = e.lat[tgt];
+    const float u = e.lat_unit;
     float L[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) L[i] = 0.f;
@@ -352,8 +355,8 @@ __global__ void __launch_bounds__(128) k_m2l_reg(EvalBufs e, const float* __rest
         const int s = base + lane;
         const bool valid = s < s1;
         const int src = valid ? e.m2l_src[s] : e.m2l_src[s0];
-        const Dbl4 gs = e.geom[src];
-        float x = (float)__dsub_rn(g.x, gs.x), y = (float)__dsub_rn(g.y, gs.y), z = (float)__dsub_rn(g.z, gs.z);
+        const int4 ls = __ldg(e.lat + src);
+        const float x = (float)(lt.x - ls.x) * u, y = (float)(lt.y - ls.y) * u, z = (float)(lt.z - ls.z) * u;
         float T[N];
         taylor_scaled<P>(x, y, z, T);
         const float wgt = valid ? 1.f : 0.f;

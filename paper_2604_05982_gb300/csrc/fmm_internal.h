@@ -116,6 +116,7 @@ struct TreeBufs {
     int* tile_sums;               // scan scratch
     Dbl4* geom;
     int4* info;
+    int4* lat;                    // cell centre on the level-21 lattice: (2i+1) << (21 - level) per axis, level
     int cap_cells;
     int* lstart;                  // [kMaxLevel + 3]: first cell of each level
     int* lvl_n;                   // [kMaxLevel + 1]: cells per level
@@ -142,6 +143,8 @@ struct EvalBufs {
     long long n;
     const Dbl4* geom;
     const int4* info;
+    const int4* lat;              // lattice centres (see TreeBufs)
+    float lat_unit;               // side / 2^22: length of one lattice step
     const int* lstart;            // host copy of the level starts
     const Dbl4* pts;
     const float4* ploc;

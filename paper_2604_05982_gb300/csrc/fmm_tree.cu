@@ -49,7 +49,7 @@ __global__ void k_bbox_partial(const double* pos, long long n, double* part) {
 
 // box = {lo x, lo y, lo z, side, scale}; root cell written here too.
 __global__ void k_bbox_final(const double* part, int nparts, long long n, double* box, Dbl4* geom, int4* info,
-                             int* lstart, int* flags) {
+                             int4* lat, int* lstart, int* flags) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double mn[3], mx[3];
     for (int d = 0; d < 3; ++d) { mn[d] = part[d]; mx[d] = part[3 + d]; }
@@ -69,6 +69,7 @@ __global__ void k_bbox_final(const double* part, int nparts, long long n, double
     box[4] = __ddiv_rn(2097152.0, side);
     geom[0] = make_dbl4(c[0], c[1], c[2], half);
     info[0] = make_int4(0, (int)n, -1, 0);
+    lat[0] = make_int4(1 << 21, 1 << 21, 1 << 21, 0);
     lstart[0] = 0;
     lstart[1] = 1;
     for (int i = 0; i < 4; ++i) flags[i] = 0;
@@ -191,7 +192,7 @@ __global__ void k_level_count(int l, const unsigned long long* codes, const int4
     }
 }
 
-__global__ void k_level_write(int l, const unsigned long long* codes, int4* info, Dbl4* geom, int* lstart,
+__global__ void k_level_write(int l, const unsigned long long* codes, int4* info, Dbl4* geom, int4* lat, int* lstart,
                               const double* box, const int* bounds, const int* cnt, const int* off,
                               const int* lvl_total, int cap, int* flags) {
     const int lo = lstart[l], hi = lstart[l + 1];
@@ -220,7 +221,10 @@ __global__ void k_level_write(int l, const unsigned long long* codes, int4* info
             const int s = bd[o], e = bd[o + 1];
             if (e <= s) continue;
             const unsigned long long pre = codes[s] >> cshift;
-            const double ix = (double)compact21(pre), iy = (double)compact21(pre >> 1), iz = (double)compact21(pre >> 2);
+            const unsigned long long jx = compact21(pre), jy = compact21(pre >> 1), jz = compact21(pre >> 2);
+            const double ix = (double)jx, iy = (double)jy, iz = (double)jz;
+            const int sh = kMaxLevel - cl;
+            lat[cf + j] = make_int4((int)((2 * jx + 1) << sh), (int)((2 * jy + 1) << sh), (int)((2 * jz + 1) << sh), cl);
             geom[cf + j] = make_dbl4(__dadd_rn(box[0], __dmul_rn(__dadd_rn(ix, 0.5), cell)),
                                         __dadd_rn(box[1], __dmul_rn(__dadd_rn(iy, 0.5), cell)),
                                         __dadd_rn(box[2], __dmul_rn(__dadd_rn(iz, 0.5), cell)), half);
@@ -267,7 +271,7 @@ int radix_tiles(long long n) { return (int)((n + kRsTile - 1) / kRsTile); }
 cudaError_t launch_tree(TreeBufs& b, cudaStream_t s) {
     const long long n = b.n;
     k_bbox_partial<<<kBoxParts, 256, 0, s>>>(b.pos, n, b.bbox_part);
-    k_bbox_final<<<1, 32, 0, s>>>(b.bbox_part, kBoxParts, n, b.box, b.geom, b.info, b.lstart, b.flags);
+    k_bbox_final<<<1, 32, 0, s>>>(b.bbox_part, kBoxParts, n, b.box, b.geom, b.info, b.lat, b.lstart, b.flags);
     k_codes<<<grid_for(n, 256, 4096), 256, 0, s>>>(b.pos, n, b.box, b.keys[0], b.vals[0]);
     const int ntiles = radix_tiles(n);
     int cur = 0;
@@ -287,7 +291,7 @@ cudaError_t launch_tree(TreeBufs& b, cudaStream_t s) {
         k_level_count<<<g, 256, 0, s>>>(l, codes, b.info, b.lstart, b.leaf, b.bounds, b.cnt, b.lvl_n);
         cudaError_t e = scan::exclusive(b.cnt, b.off, b.lvl_n + l, b.cap_cells, b.tile_sums, b.lvl_total + l, s);
         if (e != cudaSuccess) return e;
-        k_level_write<<<g, 256, 0, s>>>(l, codes, b.info, b.geom, b.lstart, b.box, b.bounds, b.cnt, b.off,
+        k_level_write<<<g, 256, 0, s>>>(l, codes, b.info, b.geom, b.lat, b.lstart, b.box, b.bounds, b.cnt, b.off,
                                         b.lvl_total, b.cap_cells, b.flags);
     }
     k_gather<<<grid_for(n, 256, 4096), 256, 0, s>>>(b.pos, b.q, b.order, n, b.pts);

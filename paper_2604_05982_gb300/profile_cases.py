@@ -17,6 +17,8 @@ def main(argv=None):
     ap.add_argument("--queues", type=int, default=1)
     ap.add_argument("--route", type=int, default=0)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--dist", default="uniform", help="fmm point set: uniform or plummer")
+    ap.add_argument("--mixed", type=int, default=1, help="fmm: 1 mixed precision, 0 FP64")
     args = ap.parse_args(argv)
 
     from . import gtap as G
@@ -50,6 +52,21 @@ def main(argv=None):
             print("mergesort", n, r.stats["kernel_ms"])
         out = dst.cpu().numpy().view(np.uint32)
         assert np.all(out[1:] >= out[:-1])
+    elif args.case == "kclique":
+        from . import inputs
+        n, e = inputs.rmat_graph(args.n or 16, 16, seed=7)
+        g = runner.DeviceGraph(n, e)
+        for _ in range(args.reps):
+            r = runner.kclique(g, 4, n_queues=args.queues, route=args.route)
+            print("kclique", r.values, r.stats["kernel_ms"])
+    elif args.case == "fmm":
+        from . import inputs
+        n = 1 << (args.n or 18)
+        pos, q = inputs.fmm_points(n, args.dist, seed=3)
+        with runner.Fmm(order=6, leaf_size=64, theta=0.5, mixed=bool(args.mixed)) as f:
+            for _ in range(args.reps):
+                f.run(pos, q)
+                print("fmm", n, args.dist, f.info())
     else:
         print(f"case {args.case} is not available in this build", file=sys.stderr)
         return 2
