@@ -112,6 +112,14 @@ GTAP_FMM_FP64 = 0
 GTAP_FMM_MIXED = 1
 
 
+class gtap_tune_trial(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int), ("deque_capacity", ctypes.c_int), ("n_queues", ctypes.c_int),
+                ("steal_policy", ctypes.c_int), ("kernel_ms", ctypes.c_float), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class gtap_completion(ctypes.Structure):
     _fields_ = [("req", ctypes.c_uint64), ("result", ctypes.c_uint64 * 2), ("status", ctypes.c_int32),
                 ("pad", ctypes.c_int32)]
@@ -151,6 +159,9 @@ _SIGS = {
     "gtap_fmm_copy_tree": (ctypes.c_int, [_P, _P, _P, _P]),
     "gtap_fmm_copy_lists": (ctypes.c_int, [_P, _P, _P]),
     "gtap_fmm_destroy": (ctypes.c_int, [_P]),
+    "gtap_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_size_t,
+                                     ctypes.POINTER(gtap_config), ctypes.c_int, _P, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(gtap_tune_trial)]),
 }
 
 _lib = None
@@ -354,3 +365,21 @@ def gtap_fmm_copy_lists(f: int, m2l, p2p) -> None:
 
 def gtap_fmm_destroy(f: int) -> None:
     _check(load_library().gtap_fmm_destroy(f), "gtap_fmm_destroy")
+
+
+def gtap_autotune(mode: int, program: str, root_args, frame_pool_bytes: int, base: gtap_config | None = None,
+                  reps: int = 3, max_trials: int = 64):
+    """Tune one program over a batch of roots (a list of args structs); returns (best, trials)."""
+    root_args = list(root_args)
+    n = len(root_args)
+    size = ctypes.sizeof(root_args[0])
+    buf = (ctypes.c_char * (size * n))()
+    for i, a in enumerate(root_args):
+        ctypes.memmove(ctypes.addressof(buf) + i * size, ctypes.addressof(a), size)
+    trials = (gtap_tune_trial * max_trials)()
+    nt = ctypes.c_int(0)
+    best = gtap_tune_trial()
+    _check(load_library().gtap_autotune(mode, program.encode(), buf, size, n, frame_pool_bytes,
+                                        ctypes.byref(base) if base else None, reps, trials, max_trials,
+                                        ctypes.byref(nt), ctypes.byref(best)), "gtap_autotune")
+    return best.as_dict(), [trials[i].as_dict() for i in range(min(nt.value, max_trials))]
