@@ -514,7 +514,7 @@ def run_kclique(args):
     work = torch.empty(4 * n + 16, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
     kargs = G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), 0, m, KC_K, 64, 1, 0)
-    pool, scratch = 1 << 30, 1 << 30
+    pool, scratch = 1 << 30, 4 << 30
 
     def step():
         G.gtap_kclique_orient(edges.data_ptr(), m, n, off.data_ptr(), adj.data_ptr(), src.data_ptr(),

@@ -89,6 +89,26 @@ __device__ __forceinline__ T ld_obj(const void* src) {
     }
     return out;
 }
+// The same through the read-only (non-coherent) path: for data that no thread
+// writes while the kernel runs (root environments of a batch run).
+template <class T>
+__device__ __forceinline__ T ld_obj_ro(const void* src) {
+    static_assert(sizeof(T) % 8 == 0, "read-only objects are copied in 8-byte pieces");
+    T out;
+    if constexpr (sizeof(T) % 16 == 0) {
+        uint4 tmp[sizeof(T) / 16];
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 16); ++i) tmp[i] = __ldg(reinterpret_cast<const uint4*>(src) + i);
+        memcpy(&out, tmp, sizeof(T));
+    } else {
+        uint2 tmp[sizeof(T) / 8];
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 8); ++i) tmp[i] = __ldg(reinterpret_cast<const uint2*>(src) + i);
+        memcpy(&out, tmp, sizeof(T));
+    }
+    return out;
+}
+
 template <class T>
 __device__ __forceinline__ void st_obj(void* dst, const T& v) {
     static_assert(sizeof(T) % 4 == 0, "record fields must be 4-byte multiples");

@@ -38,8 +38,17 @@ struct ThreadDispatch {
     }
 };
 
+// Resident 256-thread blocks per SM each program set is compiled for (the
+// register budget follows): k-clique tasks wait on L2 round trips, so it keeps
+// 4 blocks (64 registers); N-Queens and the full set measured faster with 80
+// registers at 3 blocks than capped at 64.
 template <unsigned PSET>
-__global__ void __launch_bounds__(256) thread_kernel(KParams P) {
+constexpr int thread_min_blocks() {
+    return (PSET == PS_NQUEENS || PSET == PS_THREAD_ALL) ? 3 : 4;
+}
+
+template <unsigned PSET>
+__global__ void __launch_bounds__(256, thread_min_blocks<PSET>()) thread_kernel(KParams P) {
     extern __shared__ __align__(16) char smem[];
     const int wib = threadIdx.x >> 5;
     thread_mode_loop<ThreadDispatch<PSET>>(P, smem + (size_t)wib * thread_warp_smem((int)P.maxspawn));

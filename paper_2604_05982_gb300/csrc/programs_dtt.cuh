@@ -67,7 +67,7 @@ __device__ void dtt_step(BTaskCtx& c) {
         c.ret_void();
         return;
     }
-    const fmm::DttEnv env = ld_obj<fmm::DttEnv>(c.P.root_desc[arg.root].env);
+    const fmm::DttEnv env = ld_obj_ro<fmm::DttEnv>(c.P.root_desc[arg.root].env);   // immutable during the run
     const uint32_t ncell = (uint32_t)env.n_cells;
     int F = (int)arg.n;
     if (t < F) S.fr[t] = arg.pr[t];

@@ -199,10 +199,12 @@ constexpr uint32_t kKcSetSlotAcc = 6, kKcSetLocal = 56;
 constexpr int kKcFan = 8;          // children per split
 constexpr int kKcMaxThr = 64;      // in-lane sets use 64-bit bitsets
 
-// The root environment is read through L2: in a served session the poller
-// writes it while the kernel runs.
+// The root environment is immutable during a batch run (read-only path, L1);
+// in a served session the poller writes root slots while the kernel runs, so
+// it is read through L2 there.
 __device__ __forceinline__ gtap_kclique_args kc_env(const KParams& P, uint32_t root) {
-    return ld_obj<gtap_kclique_args>(P.root_desc[root].env);
+    return P.serving ? ld_obj<gtap_kclique_args>(P.root_desc[root].env)
+                     : ld_obj_ro<gtap_kclique_args>(P.root_desc[root].env);
 }
 
 // Read-only adjacency (never written during a run): non-coherent cached loads.
