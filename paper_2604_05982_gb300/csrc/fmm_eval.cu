@@ -648,12 +648,27 @@ __global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
             }
             __syncthreads();
             if (active) {
-                for (int j = part; j < total; j += parts) {
-                    if (sid[j] == ki) continue;
-                    const R4 s = sp[j];
-                    const R dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
-                    const R r2 = dx * dx + dy * dy + dz * dz;
-                    acc.add(s.w * Ops<R>::rsq(r2));
+                if constexpr (sizeof(R) == 4) {
+                    // FP32: the target's own copy has exactly the same local coordinates
+                    // (r^2 == 0) and is the only source that can; each batch is summed
+                    // plainly and added to the compensated total
+                    float bsum = 0.f;
+#pragma unroll 4
+                    for (int j = part; j < total; j += parts) {
+                        const float4 s = sp[j];
+                        const float dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        bsum += (r2 > 0.f) ? s.w * rsqrtf(r2) : 0.f;
+                    }
+                    acc.add(bsum);
+                } else {
+                    for (int j = part; j < total; j += parts) {
+                        if (sid[j] == ki) continue;
+                        const R4 s = sp[j];
+                        const R dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
+                        const R r2 = dx * dx + dy * dy + dz * dz;
+                        acc.add(s.w * Ops<R>::rsq(r2));
+                    }
                 }
             }
             cur += nfit;
