@@ -605,6 +605,11 @@ static __device__ void serve_poller(const KParams& P, const WarpSh& ws, int* fto
 // ---------------------------------------------------------------------------
 // Thread-mode scheduler loop (Algorithm 1), one instance per warp.
 // Dispatch is a functor: Dispatch::run(TaskCtx&) executes one step.
+// Longest sleep of an idle warp between steal rounds.  Longer sleeps relieve L2
+// of idle probing (the hashed tree gained 8 % at 4 us) but slow the spread of
+// work at start-up (fib and N-Queens lost 15-25 % at 4 us).
+constexpr int kIdleBackoffMaxNs = 512;
+
 template <class Dispatch>
 __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
     const int lane = threadIdx.x & 31;
@@ -646,6 +651,10 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
     int ftop = 0;
     const int fhigh = 32 * (int)P.maxspawn + 2 * kChunk;
     constexpr int kProbes = 8;   // victims probed in parallel per steal attempt (one lane each)
+    // Fill steals (the warp holds tasks but fewer than 32) back off after failures:
+    // after k failed attempts in a row the next 2^k - 1 steps skip them (k <= 6).
+    // A warp with no task at all always tries.  Warp-uniform.
+    int fill_fail = 0, fill_wait = 0;
     // per-phase clock accounting (tracing counters): pop, steal, execute, retain/push, idle
     unsigned long long cy_pop = 0, cy_steal = 0, cy_exec = 0, cy_push = 0, cy_idle = 0;
     long long tc0 = clock64();
@@ -711,8 +720,14 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
         { const long long t = clock64(); cy_pop += (unsigned long long)(t - tc0); tc0 = t; }
         // ---- StealBatch.  SelectVictimQueue probes kProbes random victims at once (one
         // lane each) and picks the fullest, so an idle warp finds work in one round trip.
-        const bool want_steal = (P.steal_policy & GTAP_STEAL_EMPTY) ? (cnt == 0) : (cnt < 32);
+        bool want_steal = (P.steal_policy & GTAP_STEAL_EMPTY) ? (cnt == 0) : (cnt < 32);
+        const bool fill = cnt > 0;
+        if (want_steal && fill && fill_wait > 0) {
+            --fill_wait;
+            want_steal = false;
+        }
         if (want_steal && P.n_workers > 1) {
+            const int cnt_before = cnt;
             ++st_sa;
             int c = -1, victim = 0, vqi = cls;
             if (lane < kProbes) {
@@ -790,6 +805,14 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                     st_stolen += claim;
                 }
             }
+            if (fill) {
+                if (cnt > cnt_before) {
+                    fill_fail = 0;
+                } else {
+                    fill_fail = min(fill_fail + 1, 6);
+                    fill_wait = (1 << fill_fail) - 1;
+                }
+            }
         }
         { const long long t = clock64(); cy_steal += (unsigned long long)(t - tc0); tc0 = t; }
         // ---- Nothing to run: termination test (all roots complete), deadline, backoff.
@@ -808,7 +831,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             }
             if (__shfl_sync(0xffffffffu, stop, 0)) break;
             __nanosleep(backoff);
-            backoff = min(backoff * 2, 512);
+            backoff = min(backoff * 2, kIdleBackoffMaxNs);
             { const long long t = clock64(); cy_idle += (unsigned long long)(t - tc0); tc0 = t; }
             continue;
         }

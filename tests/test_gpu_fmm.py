@@ -155,3 +155,42 @@ def test_fmm_full_size_sampled(dist):
                 assert np.array_equal(_pairs(g_m2l), _pairs(m2l))
                 assert np.array_equal(_pairs(g_p2p), _pairs(p2p))
         assert _rel_l2(phi[tg], ref) <= (MIXED_TOL if mixed else FP64_TOL)
+
+
+def test_fmm_plan_reuse_across_sizes_and_sets():
+    """One plan and one context, rebuilt for growing and shrinking inputs (buffer growth paths)."""
+    with runner.Fmm(order=4, leaf_size=32, theta=0.5, mixed=True) as f:
+        for n, dist in ((1000, "uniform"), (60000, "plummer"), (300, "plummer"), (20000, "uniform")):
+            pos, q = inputs.fmm_points(n, dist, seed=n)
+            phi = f.run(pos, q).cpu().numpy()
+            ref = oracle.fmm(pos, q, p=4, theta=0.5, leaf_size=32)
+            assert _rel_l2(phi, ref) <= MIXED_TOL, (n, dist)
+            _check_tree(f, pos, 32)
+
+
+@pytest.mark.parametrize("theta", [0.2, 0.9])
+def test_fmm_opening_angle_extremes(theta):
+    pos, q = inputs.fmm_points(5000, "uniform", seed=9)
+    ref, m2l, p2p, _ = oracle.fmm(pos, q, p=3, theta=theta, leaf_size=16, lists=True)
+    with runner.Fmm(order=3, leaf_size=16, theta=theta) as f:
+        phi = f.run(pos, q).cpu().numpy()
+        g_m2l, g_p2p = f.lists()
+    assert np.array_equal(_pairs(g_m2l), _pairs(m2l)) and np.array_equal(_pairs(g_p2p), _pairs(p2p))
+    assert _rel_l2(phi, ref) <= FP64_TOL
+
+
+def test_fmm_call_order_is_checked():
+    from paper_2604_05982_gb300 import gtap as G
+    with runner.Fmm(order=2) as f:
+        phi = torch.empty(10, dtype=torch.float64, device="cuda")
+        with pytest.raises(G.GtapError):
+            G.gtap_fmm_traverse(f.plan, f.ctx.ctx)          # not built
+        with pytest.raises(G.GtapError):
+            G.gtap_fmm_evaluate(f.plan, phi.data_ptr())     # not traversed
+        pos, q = inputs.fmm_points(10, "uniform")
+        f.build(pos, q)
+        with pytest.raises(G.GtapError):
+            G.gtap_fmm_evaluate(f.plan, phi.data_ptr())     # built, not traversed
+        f.traverse()
+        G.gtap_fmm_evaluate(f.plan, phi.data_ptr())
+        assert _rel_l2(phi.cpu().numpy(), oracle.fmm(pos, q, p=2)) <= FP64_TOL
