@@ -47,6 +47,38 @@ constexpr int kMsPadded = kMsTile + kMsTile / 32;
 
 // Merge path inside shared memory (padded layout): how many of A's elements
 // precede output position d; equal keys come from A first.
+// The same split found by G lanes together (G divides 32, the group is G
+// consecutive lanes of one warp, all active): every round the lanes test G
+// evenly spaced candidates at once and the group keeps the gap between the
+// last candidate where A still precedes and the first where it does not, so a
+// range of n candidates takes about log_{G+1}(n) dependent loads instead of
+// log_2(n).  Every lane of the group returns the split.
+template <int G, class Load>
+__device__ __forceinline__ unsigned long long merge_path_group(unsigned long long na, unsigned long long nb,
+                                                               unsigned long long d, Load ld) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane % G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - g));
+    unsigned long long lo = d > nb ? d - nb : 0, hi = d < na ? d : na;   // answer in [lo, hi]
+    while (hi - lo > (unsigned long long)G) {
+        const unsigned long long span = hi - lo;
+        const unsigned long long pos = lo + span * (unsigned long long)(g + 1) / (unsigned long long)(G + 1);
+        const bool before = ld(true, pos) <= ld(false, d - 1 - pos);     // answer > pos
+        const unsigned m = __ballot_sync(gmask, before) >> (lane - g);
+        const int t = __popc(m & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)));
+        // candidates 0..t-1 precede: the answer lies after candidate t-1 and at or before candidate t
+        const unsigned long long nlo = (t > 0) ? lo + span * (unsigned long long)t / (unsigned long long)(G + 1) + 1 : lo;
+        const unsigned long long nhi = (t < G) ? lo + span * (unsigned long long)(t + 1) / (unsigned long long)(G + 1) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    // at most G candidates left: test lo + g for g < hi - lo
+    const unsigned long long pos = lo + (unsigned long long)g;
+    const bool before = pos < hi && ld(true, pos) <= ld(false, d - 1 - pos);
+    const unsigned m = __ballot_sync(gmask, before) >> (lane - g);
+    return lo + (unsigned long long)__popc(m & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)));
+}
+
 __device__ __forceinline__ int smem_merge_path(const uint32_t* sa, int na, const uint32_t* sb, int nb, int d,
                                                int a0, int b0) {
     int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
@@ -197,9 +229,14 @@ __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uin
     const uint32_t* A = X + a_lo;
     const uint32_t* B = X + b_lo;
     if (tiles > 1) {
-        for (int p = threadIdx.x; p <= tiles; p += BS) {
-            const unsigned long long d = min(total, (unsigned long long)p * kMsTile);
-            split[p] = merge_path(na, nb, d, [&](bool inA, unsigned long long k) { return __ldcg((inA ? A : B) + k); });
+        // tile boundaries: 8 lanes per boundary, BS/8 boundaries per round
+        constexpr int kG = 8;
+        for (int p0 = 0; p0 <= tiles; p0 += BS / kG) {
+            const int p = p0 + (int)threadIdx.x / kG;
+            const unsigned long long d = min(total, (unsigned long long)min(p, tiles) * kMsTile);
+            const unsigned long long sp =
+                merge_path_group<kG>(na, nb, d, [&](bool inA, unsigned long long k) { return __ldcg((inA ? A : B) + k); });
+            if (p <= tiles && (threadIdx.x % kG) == 0) split[p] = sp;
         }
     } else if (threadIdx.x == 0) {
         split[0] = 0;
