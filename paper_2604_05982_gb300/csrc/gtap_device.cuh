@@ -392,14 +392,49 @@ struct TaskCtx {
     bool staged_self = false;
     uint32_t iter = 0;
 
+    uint4 pre[2];   // record bytes 16..47 (payload start), loaded together with the header
+
+    // The header and the first 32 payload bytes are read in one burst of three
+    // independent 16-byte loads, so the step waits for one L2 round trip, not two.
     __device__ TaskCtx(const KParams& p, const WarpSh& w, uint32_t id, int wk)
         : P(p), ws(w), self(id), frame(frame_ptr(p, id)), worker(wk), nspawned(0), freed_self(false) {
-        h = ld_obj<FrameHdr>(frame);
+        const uint4* f4 = reinterpret_cast<const uint4*>(frame);
+        const uint4 r0 = __ldcg(f4);
+        pre[0] = __ldcg(f4 + 1);
+        pre[1] = __ldcg(f4 + 2);
+        memcpy(&h, &r0, sizeof(h));
     }
     __device__ int type() const { return (int)(h.w0 & 0xFF); }
     __device__ int pc() const { return (int)((h.w0 >> 8) & 0xFF); }
     template <class T> __device__ T* payload() const { return reinterpret_cast<T*>(frame + kHdrBytes); }
-    template <class T> __device__ T load() const { return ld_obj<T>(frame + kHdrBytes); }
+    // The payload as of the start of the step (children's results included).
+    template <class T> __device__ T load() const {
+        static_assert(sizeof(T) % 8 == 0, "payloads are 8-byte multiples");
+        constexpr int kPre = (int)sizeof(pre);
+        unsigned char buf[sizeof(T)];
+        memcpy(buf, pre, sizeof(T) < (size_t)kPre ? sizeof(T) : (size_t)kPre);
+        if constexpr (sizeof(T) > (size_t)kPre) {
+#pragma unroll
+            for (int o = kPre; o < (int)sizeof(T); o += 8) {
+                const unsigned long long v = ld_cg64(frame + kHdrBytes + o);
+                memcpy(buf + o, &v, 8);
+            }
+        }
+        T out;
+        memcpy(&out, buf, sizeof(T));
+        return out;
+    }
+    // 8-byte word K of the record (a result slot) as of the start of the step.
+    template <int K> __device__ unsigned long long word() const {
+        static_assert(K >= 2, "words 0 and 1 are the header");
+        if constexpr (K < 6) {
+            unsigned long long v;
+            memcpy(&v, reinterpret_cast<const unsigned char*>(pre) + 8 * (K - 2), 8);
+            return v;
+        } else {
+            return ld_cg64(frame + 8 * K);
+        }
+    }
 
     __device__ void fail(int code, unsigned long long detail) { raise_error(P, code, type(), worker, detail); }
 

@@ -24,8 +24,8 @@ __device__ __forceinline__ void fib_step(TaskCtx& c) {
         c.spawn(T_FIB, kFibSlotR, (a.n - 2 >= 2) ? qrec : qleaf, FibSpawn{a.n - 2, a.route});
         c.join(1, qcont);
     } else {
-        const long long l = (long long)ld_cg64(c.frame + 8 * kFibSlotL);
-        const long long r = (long long)ld_cg64(c.frame + 8 * kFibSlotR);
+        const long long l = (long long)c.word<kFibSlotL>();
+        const long long r = (long long)c.word<kFibSlotR>();
         c.ret((unsigned long long)(l + r));
     }
 }
@@ -38,7 +38,7 @@ constexpr uint32_t kNqSlotAcc = 4;
 
 __device__ __forceinline__ void nqueens_step(TaskCtx& c) {
     if (c.pc() == 0) {
-        const uint4 a = ld_obj<uint4>(c.frame + kHdrBytes);
+        const uint4 a = c.load<uint4>();
         const int row = (int)(a.w & 0xFF), n = (int)((a.w >> 8) & 0xFF), route = (int)(a.w >> 16);
         if (row == n) { c.ret(1ull); return; }
         const uint32_t full = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
@@ -54,7 +54,7 @@ __device__ __forceinline__ void nqueens_step(TaskCtx& c) {
         }
         c.join(1, route ? row : 0);
     } else {
-        c.ret(ld_cg64(c.frame + 8 * kNqSlotAcc));
+        c.ret(c.word<kNqSlotAcc>());
     }
 }
 
@@ -157,7 +157,7 @@ constexpr uint32_t kIntSlotL = 5, kIntSlotR = 6;
 
 __device__ __forceinline__ void integrate_step(TaskCtx& c) {
     if (c.pc() == 0) {
-        const IntegSpawn s = ld_obj<IntegSpawn>(c.frame + kHdrBytes);
+        const IntegSpawn s = c.load<IntegSpawn>();
         const double m = __dmul_rn(0.5, __dadd_rn(s.a, s.b));
         const double coarse = trap_rn(s.a, s.b);
         const double fine = __dadd_rn(trap_rn(s.a, m), trap_rn(m, s.b));
@@ -170,8 +170,8 @@ __device__ __forceinline__ void integrate_step(TaskCtx& c) {
         c.spawn(T_INTEGRATE, kIntSlotR, 0, IntegSpawn{m, s.b, s.eps, 0.0});
         c.join(1, 0);
     } else {
-        const double l = __longlong_as_double((long long)ld_cg64(c.frame + 8 * kIntSlotL));
-        const double r = __longlong_as_double((long long)ld_cg64(c.frame + 8 * kIntSlotR));
+        const double l = __longlong_as_double((long long)c.word<kIntSlotL>());
+        const double r = __longlong_as_double((long long)c.word<kIntSlotR>());
         c.ret((unsigned long long)__double_as_longlong(__dadd_rn(l, r)));
     }
 }
