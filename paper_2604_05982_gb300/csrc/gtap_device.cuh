@@ -1022,7 +1022,8 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
 struct BlockSh {
     int* ctrl;          // [0] ftop [2] nstaged [3] state (0 idle, 1 task, 2 exit) [4] join pc+1 [5] completed
     uint32_t* misc;     // [0] current task [1] retained task [2] own tail
-    FrameHdr* hdr;      // header of the current task
+    FrameHdr* hdr;      // header of the current task (the first 16 bytes of rec)
+    uint4* rec;         // [8]: the current task's record bytes 0..127, read once by warp 0
     uint32_t* fstack;   // [fcap]
     uint32_t* staged_id;// [scap]
     char* prog;         // program shared area
@@ -1035,8 +1036,9 @@ __device__ __forceinline__ BlockSh carve_block(char* base, int step_max) {
     b.scap = block_scap(step_max);
     b.ctrl = reinterpret_cast<int*>(base);
     b.misc = reinterpret_cast<uint32_t*>(base + 32);
+    b.rec = reinterpret_cast<uint4*>(base + 64);
     b.hdr = reinterpret_cast<FrameHdr*>(base + 64);
-    b.fstack = reinterpret_cast<uint32_t*>(base + 128);
+    b.fstack = reinterpret_cast<uint32_t*>(base + 192);
     b.staged_id = b.fstack + b.fcap;
     b.prog = reinterpret_cast<char*>(b.staged_id + b.scap);
     return b;
@@ -1055,7 +1057,13 @@ struct BTaskCtx {
         : P(p), bs(b), self(b.misc[0]), h(*b.hdr), frame(frame_ptr(p, b.misc[0])), worker(wk) {}
     __device__ int type() const { return (int)(h.w0 & 0xFF); }
     __device__ int pc() const { return (int)((h.w0 >> 8) & 0xFF); }
-    template <class T> __device__ T load() const { return ld_obj<T>(frame + kHdrBytes); }
+    // The payload, from the shared-memory copy of the record taken at acquire.
+    template <class T> __device__ T load() const {
+        static_assert(kHdrBytes + sizeof(T) <= 128, "block-mode payloads fit the first 128 record bytes");
+        T out;
+        memcpy(&out, reinterpret_cast<const unsigned char*>(bs.rec) + kHdrBytes, sizeof(T));
+        return out;
+    }
     template <class T> __device__ T* prog_smem() const { return reinterpret_cast<T*>(bs.prog); }
     __device__ void fail(int code, unsigned long long detail) { raise_error(P, code, type(), worker, detail); }
 
@@ -1262,6 +1270,9 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
             }
             if (state == 1) {
                 ftop = pool_refill(P, bs.fstack, ftop, (int)P.maxspawn);
+                // the task's header and payload in one burst: lane i copies record bytes 16i..16i+15
+                const int nrec = min(8, (int)(P.frame_bytes / 16));
+                if (lane < nrec) bs.rec[lane] = __ldcg(reinterpret_cast<const uint4*>(frame_ptr(P, task)) + lane);
                 if (lane == 0) {
                     if (P.fstate != nullptr) {
                         unsigned st = (task < P.n_frames) ? atomicCAS(&P.fstate[task], 3u, 1u) : 99u;  // roots start queued
@@ -1269,7 +1280,6 @@ __device__ void block_mode_loop(const KParams& P, char* smem, int bsz) {
                             raise_error(P, GTAP_ERR_TASK_FAILED, (int)st, bid, (DBG_EXEC_NOT_ALLOCATED << 32) | task);
                     }
                     bs.misc[0] = task;
-                    *bs.hdr = ld_obj<FrameHdr>(frame_ptr(P, task));
                     bs.ctrl[0] = ftop;
                     bs.ctrl[2] = 0;
                     bs.ctrl[4] = 0;

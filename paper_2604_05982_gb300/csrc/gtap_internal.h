@@ -211,6 +211,6 @@ GTAP_HD constexpr int thread_warp_smem(int maxspawn) {
 // Block mode: step_max = most children one block step can spawn (all threads together).
 GTAP_HD constexpr int block_fcap(int step_max) { return step_max + 3 * kChunk + 32; }
 GTAP_HD constexpr int block_scap(int step_max) { return ((step_max + 2 + 3) / 4) * 4; }
-GTAP_HD constexpr int block_rt_smem(int step_max) { return 128 + 4 * block_fcap(step_max) + 4 * block_scap(step_max); }
+GTAP_HD constexpr int block_rt_smem(int step_max) { return 192 + 4 * block_fcap(step_max) + 4 * block_scap(step_max); }
 
 }  // namespace gtap
