@@ -153,7 +153,7 @@ struct gtap_fmm {
     int cell_cap = 0;
     const uint32_t* order = nullptr;
     // expansions and lists
-    DBuf M, L, m2l, p2p, counters, gcnt, gcur, m2l_off, m2l_src, p2p_off, p2p_src, ms;
+    DBuf M, L, m2l, p2p, counters, gcnt, gcur, m2l_off, m2l_src, p2p_off, p2p_src, ms, aux;
     long long m2l_cap = 0, p2p_cap = 0;
 
     long long n = 0;
@@ -167,7 +167,7 @@ struct gtap_fmm {
     ~gtap_fmm() {
         DBuf* all[] = {&tab_dev, &keys0, &keys1, &vals0, &vals1, &pts, &ploc, &hist, &hist_scan, &tile_sums, &box,
                        &bbox_part, &geom, &info, &lat, &lstart, &lvl_n, &lvl_total, &cnt, &off, &bounds, &flags, &M, &L,
-                       &m2l, &p2p, &counters, &gcnt, &gcur, &m2l_off, &m2l_src, &p2p_off, &p2p_src, &ms};
+                       &m2l, &p2p, &counters, &gcnt, &gcur, &m2l_off, &m2l_src, &p2p_off, &p2p_src, &ms, &aux};
         for (DBuf* b : all) b->release();
         for (cudaEvent_t& e : ev)
             if (e) cudaEventDestroy(e);
@@ -230,12 +230,11 @@ gtap_status dtt_env(const gtap_fmm* f, int target, int source, DttEnv* out) {
     if (target < 0 || source < 0 || target >= f->n_cells || source >= f->n_cells) return GTAP_ERR_INVALID_ARG;
     out->geom = f->geom.as<Dbl4>();
     out->info = f->info.as<int4>();
+    out->lat = f->lat.as<int4>();
     out->m2l = f->m2l.as<unsigned long long>();
     out->p2p = f->p2p.as<unsigned long long>();
     out->counters = f->counters.as<unsigned long long>();
-    out->m2l_cap = (int)f->m2l_cap;
-    out->p2p_cap = (int)f->p2p_cap;
-    out->theta = f->cfg.theta;
+    out->aux = f->aux.as<DttAux>();
     out->n_cells = f->n_cells;
     out->pad = 0;
     return GTAP_OK;
@@ -298,7 +297,8 @@ gtap_status gtap_fmm_create(const gtap_fmm_config* cfg, gtap_fmm** out) {
             delete f;
             return GTAP_ERR_CUDA;
         }
-    if (!f->counters.ensure(4 * sizeof(unsigned long long)) || !f->box.ensure(8 * sizeof(double)) ||
+    if (!f->counters.ensure(4 * sizeof(unsigned long long)) || !f->aux.ensure(sizeof(DttAux)) ||
+        !f->box.ensure(8 * sizeof(double)) ||
         !f->bbox_part.ensure(6 * kBoxParts * sizeof(double)) || !f->lstart.ensure((kMaxLevel + 3) * sizeof(int)) ||
         !f->lvl_n.ensure((kMaxLevel + 1) * sizeof(int)) || !f->lvl_total.ensure((kMaxLevel + 1) * sizeof(int)) ||
         !f->flags.ensure(4 * sizeof(int))) {
@@ -434,7 +434,22 @@ gtap_status gtap_fmm_traverse(gtap_fmm* f, gtap_ctx* ctx) {
     gtap_status st = gtap_register_task(ctx, "fmm_dtt", &type);
     if (st != GTAP_OK) return st;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        if (cudaMemsetAsync(f->counters.p, 0, 4 * sizeof(unsigned long long), f->s) != cudaSuccess ||
+        // traversal constants: theta, capacities, and whether the FP32 screen of the MAC is safe.
+        // Centres carry FP64 rounding of about 2^-52 |c|; a nonzero centre difference is at least
+        // side / 2^21, so the relative gap to the exact lattice values is at most ~2^-50 (|c|max /
+        // side) 2^21, which must stay far below the 1e-5 screening margin.
+        DttAux ax{};
+        ax.theta = f->cfg.theta;
+        ax.theta2 = (float)(f->cfg.theta * f->cfg.theta);
+        ax.margin = 1e-5f;
+        ax.m2l_cap = f->m2l_cap;
+        ax.p2p_cap = f->p2p_cap;
+        double cmax = 0.0;
+        for (int d = 0; d < 3; ++d) cmax = std::max(cmax, std::max(std::fabs(f->box_h[d]), std::fabs(f->box_h[d] + f->box_h[3])));
+        const double gap = std::ldexp(1.0, -50) * (cmax / f->box_h[3]) * std::ldexp(1.0, 21);
+        ax.screen = gap < 1e-6 ? 1 : 0;
+        if (cudaMemcpyAsync(f->aux.p, &ax, sizeof(ax), cudaMemcpyHostToDevice, f->s) != cudaSuccess ||
+            cudaMemsetAsync(f->counters.p, 0, 4 * sizeof(unsigned long long), f->s) != cudaSuccess ||
             cudaStreamSynchronize(f->s) != cudaSuccess)
             return GTAP_ERR_CUDA;
         if ((st = gtap_clear_roots(ctx)) != GTAP_OK) return st;

@@ -36,15 +36,29 @@ constexpr double kSqrt3 = 1.7320508075688772;
 
 __host__ __device__ constexpr int n_coef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
+// Traversal constants kept in device memory (the plan's, refreshed before every traversal).
+//  screen: the MAC may first be decided in FP32 from the exact lattice centres
+//  (3 (h_A + h_B)^2 against theta^2 |d|^2 in lattice units); only a pair within
+//  the relative margin of the boundary takes the FP64 test that reproduces the
+//  oracle's rounding.  The margin (1e-5) exceeds the FP32 error (< 4e-7) plus
+//  the gap between exact and FP64-rounded centres, which the host bounds from
+//  the coordinates' magnitude and disables screening when it is not small.
+struct DttAux {
+    double theta;
+    float theta2, margin;
+    long long m2l_cap, p2p_cap;      // list capacities (entries)
+    int screen, pad;
+};
+
 // Read-only environment of one traversal (lives in the root's 64-byte env).
 struct DttEnv {
     const Dbl4* geom;
     const int4* info;
+    const int4* lat;                 // lattice centres: (2i+1) << (21 - level) per axis, level
     unsigned long long* m2l;         // (target << 32 | source) entries
     unsigned long long* p2p;
     unsigned long long* counters;    // [0] M2L appends, [1] P2P appends (may exceed the capacities)
-    double theta;
-    int m2l_cap, p2p_cap;            // list capacities (< 2^31 entries)
+    const DttAux* aux;
     int n_cells, pad;
 };
 static_assert(sizeof(DttEnv) == 64, "DttEnv must fill the root environment");

@@ -68,6 +68,7 @@ __device__ void dtt_step(BTaskCtx& c) {
         return;
     }
     const fmm::DttEnv env = ld_obj_ro<fmm::DttEnv>(c.P.root_desc[arg.root].env);   // immutable during the run
+    const fmm::DttAux ax = ld_obj_ro<fmm::DttAux>(env.aux);
     const uint32_t ncell = (uint32_t)env.n_cells;
     int F = (int)arg.n;
     if (t < F) S.fr[t] = arg.pr[t];
@@ -120,7 +121,21 @@ __device__ void dtt_step(BTaskCtx& c) {
                     ca = cb = 0;
                 }
                 iv[r] = ((unsigned long long)(uint32_t)ca << 32) | (uint32_t)cb;
-                if (ca != cb && dtt_mac(ldg_geom(env.geom + ca), ldg_geom(env.geom + cb), env.theta)) {
+                bool accept = false;
+                if (ca != cb) {
+                    int decided = 0;   // 1 accept, -1 reject, 0 undecided
+                    if (ax.screen) {
+                        const int4 la = __ldg(env.lat + ca), lb = __ldg(env.lat + cb);
+                        const float dx = (float)(la.x - lb.x), dy = (float)(la.y - lb.y), dz = (float)(la.z - lb.z);
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        const float sh = (float)((1 << (fmm::kMaxLevel - la.w)) + (1 << (fmm::kMaxLevel - lb.w)));
+                        const float g = 3.f * sh * sh, f = ax.theta2 * d2;
+                        decided = (g < f * (1.f - ax.margin)) ? 1 : (g > f * (1.f + ax.margin)) ? -1 : 0;
+                    }
+                    accept = decided != 0 ? decided > 0
+                                          : dtt_mac(ldg_geom(env.geom + ca), ldg_geom(env.geom + cb), ax.theta);
+                }
+                if (accept) {
                     cls[r] = 0;
                 } else {
                     const int4 ia = __ldg(&env.info[ca]), ib = __ldg(&env.info[cb]);
@@ -159,10 +174,10 @@ __device__ void dtt_step(BTaskCtx& c) {
 #pragma unroll
             for (int r = 0; r < kPer; ++r) {
                 if (cls[r] == 0) {
-                    if (p0 < (unsigned long long)env.m2l_cap) env.m2l[p0] = iv[r];
+                    if (p0 < (unsigned long long)ax.m2l_cap) env.m2l[p0] = iv[r];
                     ++p0;
                 } else if (cls[r] == 1) {
-                    if (p1 < (unsigned long long)env.p2p_cap) env.p2p[p1] = iv[r];
+                    if (p1 < (unsigned long long)ax.p2p_cap) env.p2p[p1] = iv[r];
                     ++p1;
                 } else if (cls[r] == 2) {
                     if (p2 < kDttFront) S.fr[p2] = iv[r];
