@@ -102,6 +102,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device: str = "cuda") -> float:
+    """Barrier, then the maximum of `value` over all ranks (one rank: the value itself)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank_step: float, steps: int, world: int, elapsed_ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank_step * steps * world / (elapsed_ms / 1e3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -173,14 +190,9 @@ def run_gpu(args):
             per_kernel["mergesort"].append(c)
         e1.record()
         torch.cuda.synchronize()
-    elapsed_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        elapsed_ms = float(tt.item())
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1))
     ms_per_step = elapsed_ms / args.steps
-    value = STEP_TASKS * args.steps * world / (elapsed_ms / 1e3)
+    value = aggregate_rate(STEP_TASKS, args.steps, world, elapsed_ms)
 
     # end to end through the C ABI with host buffers: H2D of the keys from pinned memory,
     # the three runs, and D2H of the sorted keys and of the counts (gtap_wait reads them back)
@@ -346,6 +358,8 @@ def run_fmm(args):
     from paper_2604_05982_gb300 import inputs, runner
     world, rank, local = _dist()
     torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
     mixed = args.fmm_precision == "mixed"
     sets = {}
     for dist in FMM_SETS:
@@ -389,8 +403,8 @@ def run_fmm(args):
                 phases[dist].append(d["f"].info())
         e1.record()
         torch.cuda.synchronize()
-    elapsed_ms = e0.elapsed_time(e1)
-    ms_per_instance = elapsed_ms / (args.steps * len(sets))
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1))
+    ms_per_instance = elapsed_ms / (args.steps * len(sets) * world)
 
     # end to end through the public calls with host buffers: pinned H2D of positions and
     # charges, the three calls, D2H of the potentials
@@ -471,6 +485,8 @@ def run_fmm(args):
         d["f"].close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def _fmm_cpu_sample():
@@ -505,6 +521,8 @@ def run_kclique(args):
     from paper_2604_05982_gb300 import inputs, runner
     world, rank, local = _dist()
     torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
     n, e = inputs.rmat_graph(KC_SCALE, 16, seed=7)
     edges = torch.from_numpy(np.ascontiguousarray(e)).cuda()
     m = int(edges.shape[0])
@@ -546,8 +564,8 @@ def run_kclique(args):
             assert c_ == count
             kms.append(k_)
         torch.cuda.synchronize()
-        elapsed = time.perf_counter() - t0
-    ms = elapsed * 1e3 / args.steps
+        elapsed = max_over_ranks(time.perf_counter() - t0)
+    ms = elapsed * 1e3 / (args.steps * world)
     kms.sort()
     line = {
         "metric": "k-clique time", "value": ms, "unit": "ms/instance", "n_gpus": world, "steps": args.steps,
@@ -566,6 +584,8 @@ def run_kclique(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 SERVE_REQUESTS = 20000
