@@ -450,6 +450,14 @@ def run_fmm(args):
         peak = FP64_NOMINAL_TFLOPS
         peak_kind = "nominal GB300 FP64"
     launches = sum(_fmm_kernels_per_instance(info[dd]["n_levels"], mixed) for dd in sets) * args.steps
+    m2l_traffic = None
+    if mixed:
+        try:
+            with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+                tj = json.load(fh)
+            m2l_traffic = tj["fmm_m2l_mixed_uniform_bytes"] + tj["fmm_m2l_mixed_plummer_bytes"]
+        except (OSError, KeyError, ValueError):
+            pass
     line = {
         "metric": "FMM time", "value": ms_per_instance, "unit": "ms/instance", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
@@ -467,7 +475,9 @@ def run_fmm(args):
                        "levels": info[dd]["n_levels"]} for dd in sets},
         "rel_l2_vs_oracle_fmm_64_targets": errs,
         "roofline": {"bound": "alu", "kernel": "k_m2l_reg (M2L)", "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": m2l_traffic, "traffic_note": "DRAM bytes of the two M2L launches of a step "
+                     "(uniform + Plummer), one-pass ncu capture at full size",
                      "algorithmic_flops_per_pair": fl},
         "e2e": {"value": e2e_ms, "unit": "ms/instance", "h2d_bytes_per_step": len(sets) * FMM_N * 32,
                 "d2h_bytes_per_step": len(sets) * FMM_N * 8},
