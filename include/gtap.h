@@ -299,16 +299,24 @@ gtap_status gtap_microbench(int kind, void* region, uint64_t region_bytes, int b
  *                queues {1,2,3,4}, capacity {1024, 4096, 16384};
  *   block mode:  blocks/SM {1,2,3,4,6}, steal {half of the victim, ONE},
  *                queues {1}, capacity {1024, 4096, 16384},
- * starting from 4 blocks/SM, capacity 4096, 1 queue, default stealing.  Each
- * trial creates a context (gtap_init with `base` and the trial's fields,
- * frame_pool_bytes), queues n_roots roots whose argument structs lie
- * back to back in root_args (host, args_bytes each, queue 0), runs once to
- * warm up and `reps` more times, and is scored by the median kernel_ms.  Every
- * trial must reproduce the first trial's 16-byte root results exactly, else
- * GTAP_ERR_TASK_FAILED.  trials (host, may be NULL) receives up to max_trials
- * records; *n_trials the number of trials run; *best the chosen configuration.
- * Device buffers named in the arguments are used by every trial (a program
- * that writes them, e.g. mergesort, must be idempotent: src is read only). */
+ * starting from 4 blocks/SM, capacity 4096, n_queues queues and default
+ * stealing; tune_mask selects the dimensions that may change
+ * (GTAP_TUNE_BLOCKS | GTAP_TUNE_STEAL | GTAP_TUNE_QUEUES | GTAP_TUNE_CAPACITY,
+ * 0 = all).  Each trial creates a context (gtap_init with `base` and the
+ * trial's fields, frame_pool_bytes), queues n_roots roots whose argument
+ * structs lie back to back in root_args (host, args_bytes each, queue 0), runs
+ * once to warm up and `reps` more times, and is scored by the median
+ * kernel_ms.  Every trial must reproduce the first trial's 16-byte root
+ * results exactly, else GTAP_ERR_TASK_FAILED.  trials (host, may be NULL)
+ * receives up to max_trials records; *n_trials the number of trials run;
+ * *best the chosen configuration.  Device buffers named in the arguments are
+ * used by every trial (a program that writes them, e.g. mergesort, must be
+ * idempotent: src is read only). */
+#define GTAP_TUNE_BLOCKS 1
+#define GTAP_TUNE_STEAL 2
+#define GTAP_TUNE_QUEUES 4
+#define GTAP_TUNE_CAPACITY 8
+
 typedef struct {
     int blocks_per_sm, deque_capacity, n_queues, steal_policy;
     float kernel_ms;   /* median persistent-kernel time of the trial */
@@ -316,8 +324,8 @@ typedef struct {
 } gtap_tune_trial;
 
 gtap_status gtap_autotune(int mode, const char* program, const void* root_args, size_t args_bytes, int n_roots,
-                          size_t frame_pool_bytes, const gtap_config* base, int reps, gtap_tune_trial* trials,
-                          int max_trials, int* n_trials, gtap_tune_trial* best);
+                          int n_queues, size_t frame_pool_bytes, const gtap_config* base, int reps, int tune_mask,
+                          gtap_tune_trial* trials, int max_trials, int* n_trials, gtap_tune_trial* best);
 
 /* ------------------------------------------------------------------------
  * Laplace FMM pipeline (Sec. 6.4.1): adaptive octree construction, upward

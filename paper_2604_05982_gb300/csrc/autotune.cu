@@ -84,11 +84,14 @@ struct Tuner {
 }  // namespace
 
 extern "C" gtap_status gtap_autotune(int mode, const char* program, const void* root_args, size_t args_bytes,
-                                     int n_roots, size_t frame_pool_bytes, const gtap_config* base, int reps,
-                                     gtap_tune_trial* trials, int max_trials, int* n_trials, gtap_tune_trial* best) {
+                                     int n_roots, int n_queues, size_t frame_pool_bytes, const gtap_config* base,
+                                     int reps, int tune_mask, gtap_tune_trial* trials, int max_trials, int* n_trials,
+                                     gtap_tune_trial* best) {
     if ((mode != GTAP_MODE_THREAD && mode != GTAP_MODE_BLOCK) || !program || !root_args || args_bytes == 0 ||
-        n_roots < 1 || reps < 1 || !best || max_trials < 0)
+        n_roots < 1 || reps < 1 || !best || max_trials < 0 || n_queues < 1 || n_queues > 8 ||
+        (mode == GTAP_MODE_BLOCK && n_queues != 1) || (tune_mask & ~15) != 0)
         return GTAP_ERR_INVALID_ARG;
+    if (tune_mask == 0) tune_mask = GTAP_TUNE_BLOCKS | GTAP_TUNE_STEAL | GTAP_TUNE_QUEUES | GTAP_TUNE_CAPACITY;
     Tuner t;
     t.mode = mode;
     t.program = program;
@@ -110,7 +113,7 @@ extern "C" gtap_status gtap_autotune(int mode, const char* program, const void* 
     const std::vector<int> queues = thread ? std::vector<int>{1, 2, 3, 4} : std::vector<int>{1};
     const std::vector<int> caps = {1024, 4096, 16384};
 
-    Trial cur{thread ? 4 : 4, thread ? 4096 : 4096, 1, thread ? GTAP_STEAL_FILL : 0};
+    Trial cur{4, 4096, n_queues, thread ? GTAP_STEAL_FILL : 0};
     float cur_ms = 0.f;
     gtap_status st = t.run(cur, &cur_ms);
     if (st != GTAP_OK) {
@@ -119,6 +122,7 @@ extern "C" gtap_status gtap_autotune(int mode, const char* program, const void* 
     }
     // coordinate descent, one sweep per parameter in this order
     for (int dim = 0; dim < 4; ++dim) {
+        if ((tune_mask & (1 << dim)) == 0) continue;
         const std::vector<int>& vals = dim == 0 ? bps : dim == 1 ? steal : dim == 2 ? queues : caps;
         const int start = dim == 0 ? cur.bps : dim == 1 ? cur.steal : dim == 2 ? cur.queues : cur.cap;
         for (int v : vals) {

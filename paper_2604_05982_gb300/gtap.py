@@ -159,9 +159,9 @@ _SIGS = {
     "gtap_fmm_copy_tree": (ctypes.c_int, [_P, _P, _P, _P]),
     "gtap_fmm_copy_lists": (ctypes.c_int, [_P, _P, _P]),
     "gtap_fmm_destroy": (ctypes.c_int, [_P]),
-    "gtap_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_size_t,
-                                     ctypes.POINTER(gtap_config), ctypes.c_int, _P, ctypes.c_int,
-                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(gtap_tune_trial)]),
+    "gtap_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_size_t, ctypes.POINTER(gtap_config), ctypes.c_int, ctypes.c_int, _P,
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(gtap_tune_trial)]),
 }
 
 _lib = None
@@ -367,8 +367,11 @@ def gtap_fmm_destroy(f: int) -> None:
     _check(load_library().gtap_fmm_destroy(f), "gtap_fmm_destroy")
 
 
+GTAP_TUNE_BLOCKS, GTAP_TUNE_STEAL, GTAP_TUNE_QUEUES, GTAP_TUNE_CAPACITY = 1, 2, 4, 8
+
+
 def gtap_autotune(mode: int, program: str, root_args, frame_pool_bytes: int, base: gtap_config | None = None,
-                  reps: int = 3, max_trials: int = 64):
+                  reps: int = 3, max_trials: int = 64, n_queues: int = 1, tune_mask: int = 0):
     """Tune one program over a batch of roots (a list of args structs); returns (best, trials)."""
     root_args = list(root_args)
     n = len(root_args)
@@ -379,7 +382,7 @@ def gtap_autotune(mode: int, program: str, root_args, frame_pool_bytes: int, bas
     trials = (gtap_tune_trial * max_trials)()
     nt = ctypes.c_int(0)
     best = gtap_tune_trial()
-    _check(load_library().gtap_autotune(mode, program.encode(), buf, size, n, frame_pool_bytes,
-                                        ctypes.byref(base) if base else None, reps, trials, max_trials,
+    _check(load_library().gtap_autotune(mode, program.encode(), buf, size, n, n_queues, frame_pool_bytes,
+                                        ctypes.byref(base) if base else None, reps, tune_mask, trials, max_trials,
                                         ctypes.byref(nt), ctypes.byref(best)), "gtap_autotune")
     return best.as_dict(), [trials[i].as_dict() for i in range(min(nt.value, max_trials))]

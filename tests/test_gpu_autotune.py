@@ -46,6 +46,17 @@ def test_autotune_block_mode_mergesort():
     assert np.array_equal(dst.cpu().numpy().view(np.uint32), oracle.sort_u32(keys))
 
 
+def test_autotune_with_fixed_queues_keeps_them():
+    args = [G.gtap_nqueens_args(10, 1)]
+    best, trials = G.gtap_autotune(G.GTAP_MODE_THREAD, "nqueens", args, 256 << 20, runner.make_config(), reps=1,
+                                   n_queues=4, tune_mask=G.GTAP_TUNE_BLOCKS | G.GTAP_TUNE_STEAL)
+    _check(best, trials)
+    assert len(trials) == 1 + 4 + 3
+    assert all(t["n_queues"] == 4 and t["deque_capacity"] == 4096 for t in trials)
+
+
 def test_autotune_rejects_bad_arguments():
     with pytest.raises(G.GtapError):
         G.gtap_autotune(G.GTAP_MODE_THREAD, "no_such_program", [G.gtap_fib_args(10, 0)], 1 << 24)
+    with pytest.raises(G.GtapError):
+        G.gtap_autotune(G.GTAP_MODE_BLOCK, "mergesort", [G.gtap_fib_args(10, 0)], 1 << 24, n_queues=2)
