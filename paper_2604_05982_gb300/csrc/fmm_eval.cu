@@ -554,7 +554,7 @@ __global__ void k_l2l(EvalBufs e, int lo, int hi) {
 // source points staged in shared memory in batches of up to kSrcBatch from
 // consecutive source leaves; then the parts are combined and L2P added.
 constexpr int kLeafBlock = 128;
-constexpr int kSrcBatch = 256;
+constexpr int kSrcBatch = 1024;
 
 template <class R>
 __global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
