@@ -577,11 +577,12 @@ __global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
         const int4 in = e.info[c];
         if (in.z >= 0) continue;
         const Dbl4 g = e.geom[c];
+        // one slot per target point, kLeafBlock / count source parts per slot
         const int count = in.y;
-        const int tp = count <= 32 ? 32 : 64;
+        const int tp = max(count, 1);
         const int parts = kLeafBlock / tp;
-        const int slot = t % tp, part = t / tp;
-        const bool active = slot < count;
+        const int part = t / tp, slot = t - part * tp;
+        const bool active = part < parts;
         const int ki = in.x + (active ? slot : 0);
         R xi, yi, zi;
         if constexpr (sizeof(R) == 4) {
@@ -594,6 +595,24 @@ __global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
         __syncthreads();
         for (int i = t; i < nt; i += kLeafBlock) lsm[i] = (R)e.L[(size_t)c * nt + i];
         Acc<R> acc;
+        if constexpr (sizeof(R) == 4) {
+            // the leaf's own points first: the target's own copy has exactly the same
+            // local coordinates (r^2 == 0) and is the only source that can, so only this
+            // pass tests for it; the batches below skip the leaf itself
+            __syncthreads();
+            for (int i = t; i < count; i += kLeafBlock) sp[i] = e.ploc[in.x + i];
+            __syncthreads();
+            if (active) {
+                float bsum = 0.f;
+                for (int j = part; j < count; j += parts) {
+                    const float4 sj = sp[j];
+                    const float dx = xi - sj.x, dy = yi - sj.y, dz = zi - sj.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    bsum += (r2 > 0.f) ? sj.w * rsqrtf(r2) : 0.f;
+                }
+                acc.add(bsum);
+            }
+        }
         const int s0 = e.p2p_off[c], s1 = e.p2p_off[c + 1];
         int cur = s0;
         while (cur < s1) {
@@ -605,7 +624,7 @@ __global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
                 if (j < s1) {
                     const int sc = e.p2p_src[j];
                     const int4 si = e.info[sc];
-                    cnt = si.y;
+                    cnt = (sizeof(R) == 4 && sc == c) ? 0 : si.y;   // FP32: the own leaf had its pass
                     first = si.x;
                     gs = e.geom[sc];
                 }
@@ -649,16 +668,15 @@ __global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
             __syncthreads();
             if (active) {
                 if constexpr (sizeof(R) == 4) {
-                    // FP32: the target's own copy has exactly the same local coordinates
-                    // (r^2 == 0) and is the only source that can; each batch is summed
-                    // plainly and added to the compensated total
+                    // other leaves only: no self term; each batch is summed plainly and
+                    // added to the compensated total
                     float bsum = 0.f;
 #pragma unroll 4
                     for (int j = part; j < total; j += parts) {
                         const float4 s = sp[j];
                         const float dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
                         const float r2 = dx * dx + dy * dy + dz * dz;
-                        bsum += (r2 > 0.f) ? s.w * rsqrtf(r2) : 0.f;
+                        bsum = fmaf(s.w, rsqrtf(r2), bsum);
                     }
                     acc.add(bsum);
                 } else {
