@@ -355,8 +355,9 @@ typedef struct {
     int precision;         /* GTAP_FMM_FP64 (default) or GTAP_FMM_MIXED */
     int fp64_levels;       /* mixed form: translations whose parent is on a level below this
                               number run in FP64 (default 3) */
-    int64_t m2l_capacity;  /* list capacities in entries; 0 = from the tree: ceil(64/theta^3)
-                              per cell and ceil(32/theta^3) per leaf, grown once on overflow */
+    int64_t m2l_capacity;  /* list capacities in entries; 0 = from the tree: ceil(128/theta^3)
+                              per cell and ceil(32/theta^3) per leaf; an overflow grows the
+                              lists (kept for later builds) and repeats the traversal once */
     int64_t p2p_capacity;
     void* stream;          /* cudaStream_t of the data-parallel kernels; use the same stream as
                               the traversal context (default: the legacy default stream) */

@@ -181,6 +181,9 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? ms : 0.f;
 }
 
+// Make the lists hold at least the given entries.  A capacity never drops below
+// what is already allocated, so a size learned from an overflow is kept for
+// later builds of the plan.
 gtap_status grow_lists(gtap_fmm* f, long long m2l_cap, long long p2p_cap) {
     const long long lim = (1ll << 31) - 1;
     m2l_cap = std::min(std::max(m2l_cap, 1ll), lim);
@@ -188,8 +191,8 @@ gtap_status grow_lists(gtap_fmm* f, long long m2l_cap, long long p2p_cap) {
     if (!f->m2l.ensure(sizeof(unsigned long long) * (size_t)m2l_cap) ||
         !f->p2p.ensure(sizeof(unsigned long long) * (size_t)p2p_cap))
         return GTAP_ERR_NO_MEMORY;
-    f->m2l_cap = m2l_cap;
-    f->p2p_cap = p2p_cap;
+    f->m2l_cap = std::min(lim, (long long)(f->m2l.bytes / sizeof(unsigned long long)));
+    f->p2p_cap = std::min(lim, (long long)(f->p2p.bytes / sizeof(unsigned long long)));
     return GTAP_OK;
 }
 
@@ -416,7 +419,7 @@ gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int6
     cudaEventRecord(f->ev[2], f->s);
     // list capacities
     const double th3 = f->cfg.theta * f->cfg.theta * f->cfg.theta;
-    long long mc = f->cfg.m2l_capacity ? f->cfg.m2l_capacity : (long long)f->n_cells * (long long)std::ceil(64.0 / th3);
+    long long mc = f->cfg.m2l_capacity ? f->cfg.m2l_capacity : (long long)f->n_cells * (long long)std::ceil(128.0 / th3);
     long long pc = f->cfg.p2p_capacity ? f->cfg.p2p_capacity : (long long)f->n_leaves * (long long)std::ceil(32.0 / th3);
     gtap_status st = grow_lists(f, mc, pc);
     if (st != GTAP_OK) return st;
