@@ -53,6 +53,7 @@ struct HostTables {
     std::vector<int> item_off;
     std::vector<TermEntry> m2l, m2m, l2l;
     std::vector<int> m2m_off, l2l_off;
+    std::vector<double> mscale, lscale;   // (-1)^|a| / a!  and  1 / b!  per coefficient
 
     int at(int a, int b, int c) const {
         if (a < 0 || b < 0 || c < 0 || a + b + c > p) return -1;
@@ -83,6 +84,12 @@ struct HostTables {
             d.k = (short)(a + b + c);
             d.pad = 0;
             deriv.push_back(d);
+            double fa = 1.0;
+            for (int t = 2; t <= a; ++t) fa *= t;
+            for (int t = 2; t <= b; ++t) fa *= t;
+            for (int t = 2; t <= c; ++t) fa *= t;
+            lscale.push_back(1.0 / fa);
+            mscale.push_back(((a + b + c) & 1) ? -1.0 / fa : 1.0 / fa);
         }
         // M2L: for each beta, the alphas with |alpha| + |beta| <= p, in chunks
         for (int bi = 0; bi < nt; ++bi) {
@@ -273,7 +280,8 @@ gtap_status gtap_fmm_create(const gtap_fmm_config* cfg, gtap_fmm** out) {
     std::vector<unsigned char> blob;
     const size_t o_mi = put(blob, h.mi), o_der = put(blob, h.deriv), o_items = put(blob, h.items),
                  o_ioff = put(blob, h.item_off), o_m2l = put(blob, h.m2l), o_m2mo = put(blob, h.m2m_off),
-                 o_m2m = put(blob, h.m2m), o_l2lo = put(blob, h.l2l_off), o_l2l = put(blob, h.l2l);
+                 o_m2m = put(blob, h.m2m), o_l2lo = put(blob, h.l2l_off), o_l2l = put(blob, h.l2l),
+                 o_ms = put(blob, h.mscale), o_ls = put(blob, h.lscale);
     if (!f->tab_dev.ensure(blob.size()) ||
         cudaMemcpy(f->tab_dev.p, blob.data(), blob.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         delete f;
@@ -295,6 +303,8 @@ gtap_status gtap_fmm_create(const gtap_fmm_config* cfg, gtap_fmm** out) {
     t.m2m_terms = reinterpret_cast<TermEntry*>(base + o_m2m);
     t.l2l_off = reinterpret_cast<int*>(base + o_l2lo);
     t.l2l_terms = reinterpret_cast<TermEntry*>(base + o_l2l);
+    t.mscale = reinterpret_cast<double*>(base + o_ms);
+    t.lscale = reinterpret_cast<double*>(base + o_ls);
     for (cudaEvent_t& e : f->ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             delete f;

@@ -286,7 +286,6 @@ __global__ void k_m2l(EvalBufs e) {
 __host__ __device__ constexpr int cidx(int a, int b, int c) {
     return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
 }
-__host__ __device__ constexpr float cfact(int n) { return n <= 1 ? 1.f : (float)n * cfact(n - 1); }
 __host__ __device__ constexpr int row_stride(int p) { return (n_coef(p) + 3) / 4 * 4; }
 
 template <int P>
@@ -316,24 +315,17 @@ __device__ __forceinline__ void taylor_scaled(float x, float y, float z, float* 
     }
 }
 
-// Ms[cell][row_stride(P)] = (-1)^|a| M_a / a! in FP32.
+// Ms[cell][row_stride(P)] = (-1)^|a| M_a / a! in FP32; the factors come from a
+// per-coefficient table (an FP64 divide is a long sequence on the FP64 pipe,
+// the narrowest pipe of this GPU).
 template <int P>
-__global__ void k_scale_m(const double* M, int n_cells, float* Ms) {
+__global__ void k_scale_m(const double* __restrict__ M, int n_cells, const double* __restrict__ mscale,
+                          float* __restrict__ Ms) {
     constexpr int N = n_coef(P), S = row_stride(P);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n_cells * S;
          i += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(i / S), j = (int)(i - (long long)c * S);
-        float v = 0.f;
-#pragma unroll
-        for (int k = 0; k <= P; ++k)
-#pragma unroll
-            for (int a = k; a >= 0; --a)
-#pragma unroll
-                for (int b = k - a; b >= 0; --b)
-                    if (j == cidx(a, b, k - a - b))
-                        v = (float)(M[(size_t)c * N + j] / (double)(cfact(a) * cfact(b) * cfact(k - a - b))) *
-                            ((k & 1) ? -1.f : 1.f);
-        Ms[i] = v;
+        Ms[i] = (j < N) ? (float)(M[(size_t)c * N + j] * __ldg(mscale + j)) : 0.f;
     }
 }
 
@@ -385,7 +377,8 @@ __global__ void __launch_bounds__(128, 3) k_m2l_reg(EvalBufs e, const float* __r
                             }
                 }
     }
-    // sum the lanes' partial expansions, then lane (b mod 32) writes L_b = Lt_b / b!
+    // sum the lanes' partial expansions, then lane l writes L_b = Lt_b / b! for
+    // b = l, l + 32, l + 64 (selected by register moves; one FP64 multiply each)
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         float v = L[i];
@@ -393,16 +386,16 @@ __global__ void __launch_bounds__(128, 3) k_m2l_reg(EvalBufs e, const float* __r
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         L[i] = v;
     }
+    constexpr int R = (N + 31) / 32;
+    float w[R];
 #pragma unroll
-    for (int k = 0; k <= P; ++k)
+    for (int r = 0; r < R; ++r) w[r] = 0.f;
 #pragma unroll
-        for (int a = k; a >= 0; --a)
+    for (int i = 0; i < N; ++i)
+        if ((i & 31) == lane) w[i >> 5] = L[i];
 #pragma unroll
-            for (int b = k - a; b >= 0; --b) {
-                const int i = cidx(a, b, k - a - b);
-                if ((i & 31) == lane)
-                    e.L[(size_t)tgt * N + i] = (double)L[i] / (double)(cfact(a) * cfact(b) * cfact(k - a - b));
-            }
+    for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < N) e.L[(size_t)tgt * N + lane + 32 * r] = (double)w[r] * __ldg(e.tab.lscale + lane + 32 * r);
 }
 
 // FP64 M2L in the same scaled form: the local expansion stays in registers,
@@ -410,22 +403,13 @@ __global__ void __launch_bounds__(128, 3) k_m2l_reg(EvalBufs e, const float* __r
 // shared-memory table (FP64 registers cannot hold both).  The FP64 pipe, not
 // the shared-memory bandwidth, bounds this kernel.
 template <int P>
-__global__ void k_scale_m64(const double* M, int n_cells, double* Ms) {
+__global__ void k_scale_m64(const double* __restrict__ M, int n_cells, const double* __restrict__ mscale,
+                            double* __restrict__ Ms) {
     constexpr int N = n_coef(P), S = row_stride(P);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n_cells * S;
          i += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(i / S), j = (int)(i - (long long)c * S);
-        double v = 0.0;
-#pragma unroll
-        for (int k = 0; k <= P; ++k)
-#pragma unroll
-            for (int a = k; a >= 0; --a)
-#pragma unroll
-                for (int b = k - a; b >= 0; --b)
-                    if (j == cidx(a, b, k - a - b))
-                        v = M[(size_t)c * N + j] / ((double)cfact(a) * (double)cfact(b) * (double)cfact(k - a - b)) *
-                            ((k & 1) ? -1.0 : 1.0);
-        Ms[i] = v;
+        Ms[i] = (j < N) ? M[(size_t)c * N + j] * __ldg(mscale + j) : 0.0;
     }
 }
 
@@ -503,16 +487,16 @@ __global__ void __launch_bounds__(32 * kM2l64Warps) k_m2l_reg64(EvalBufs e, cons
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         L[i] = v;
     }
+    constexpr int R = (N + 31) / 32;
+    double w[R];
 #pragma unroll
-    for (int k = 0; k <= P; ++k)
+    for (int r = 0; r < R; ++r) w[r] = 0.0;
 #pragma unroll
-        for (int a = k; a >= 0; --a)
+    for (int i = 0; i < N; ++i)
+        if ((i & 31) == lane) w[i >> 5] = L[i];
 #pragma unroll
-            for (int b = k - a; b >= 0; --b) {
-                const int i = cidx(a, b, k - a - b);
-                if ((i & 31) == lane)
-                    e.L[(size_t)tgt * N + i] = L[i] / ((double)cfact(a) * (double)cfact(b) * (double)cfact(k - a - b));
-            }
+    for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < N) e.L[(size_t)tgt * N + lane + 32 * r] = w[r] * __ldg(e.tab.lscale + lane + 32 * r);
 }
 
 // L2L from the parents of one level into their children: one block per parent.
@@ -814,14 +798,14 @@ cudaError_t launch_upward(const EvalBufs& e, bool mixed, int fp64_levels, cudaSt
 
 template <int P>
 cudaError_t launch_m2l_reg(const EvalBufs& e, float* ms, cudaStream_t s) {
-    k_scale_m<P><<<grid_for((long long)e.n_cells * row_stride(P), 256, 4096), 256, 0, s>>>(e.M, e.n_cells, ms);
+    k_scale_m<P><<<grid_for((long long)e.n_cells * row_stride(P), 256, 4096), 256, 0, s>>>(e.M, e.n_cells, e.tab.mscale, ms);
     k_m2l_reg<P><<<grid_for((long long)e.n_cells * 32, 128, 1 << 30), 128, 0, s>>>(e, ms);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t launch_m2l_reg64(const EvalBufs& e, double* ms, cudaStream_t s) {
-    k_scale_m64<P><<<grid_for((long long)e.n_cells * row_stride(P), 256, 4096), 256, 0, s>>>(e.M, e.n_cells, ms);
+    k_scale_m64<P><<<grid_for((long long)e.n_cells * row_stride(P), 256, 4096), 256, 0, s>>>(e.M, e.n_cells, e.tab.mscale, ms);
     const size_t sm = sizeof(double) * n_coef(P) * 32 * kM2l64Warps;
     cudaError_t err = set_smem(k_m2l_reg64<P>, sm);
     if (err != cudaSuccess) return err;

@@ -107,6 +107,8 @@ struct Tables {
     TermEntry* m2m_terms;       // a = beta (index into child M), b = alpha - beta (monomial index)
     int* l2l_off;               // [nt + 1] by gamma
     TermEntry* l2l_terms;       // a = beta (index into parent L), b = beta - gamma (monomial index)
+    double* mscale;             // [nt] (-1)^|alpha| / alpha!  (scaled multipoles of the M2L)
+    double* lscale;             // [nt] 1 / beta!  (local coefficients from the scaled M2L sums)
 };
 
 }  // namespace fmm
