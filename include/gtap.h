@@ -266,7 +266,9 @@ typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; 
  * (k-2)-cliques of C = N+(u) n N+(v); a set larger than split_threshold
  * (<= 64, default 64) is materialised in the context's scratch arena
  * (gtap_config.scratch_bytes) and forked into child tasks over its branch
- * range, smaller ones are counted in the lane with 64-bit bitsets.
+ * range; smaller ones are counted in the lane with 64-bit bitsets.  A
+ * first-level set is written by its own task when that task starts (waiting
+ * first-level tasks hold no scratch); deeper sets by the task that spawns them.
  * route 1: queue = recursion depth mod n_queues.  k in [3, 16].  Result: uint64 count. */
 typedef struct { const int64_t* off; const int32_t* adj; const int32_t* src;
                  int64_t edge_begin, edge_end;   /* the root counts DAG edges [edge_begin, edge_end) */

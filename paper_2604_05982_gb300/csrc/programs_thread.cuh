@@ -183,19 +183,32 @@ namespace gtap {
 // ---------------------------------------------------------------------------
 // k-clique counting by orientation (Sec. 6.4.2).  For a DAG edge (u, v),
 // C = N+(u) n N+(v); count(S, 1) = |S|, count(S, j) = sum over w in S of
-// count(S n N+(w), j - 1).  A set of at most `thr` (<= 32) vertices is counted
-// inside the lane with 32-bit adjacency bitsets; a larger one is written to
-// the scratch arena and forked over its branch range (the paper's split on the
-// spawn-time estimate |C|).
+// count(S n N+(w), j - 1).  A set of at most `thr` (<= 64) vertices is counted
+// inside the lane with 64-bit adjacency bitsets; a larger one is forked over
+// its branch range (the paper's split on the spawn-time estimate |C|).
+//
+// Sets of the first level, C = N+(u) n N+(v), are spawned unmaterialised:
+// the record names P = N+(u), the vertex w = v and |C|, and the child writes C
+// to the scratch arena when it first runs.  The edge-range tasks then only
+// count, and the expensive intersections are spread over the set tasks that
+// idle lanes steal (k = 4, scale 20: 874 -> 769 ms), while waiting first-level
+// tasks hold no scratch.  Deeper sets are materialised by the spawning lane:
+// that keeps the lanes expanding the frontier busy, and with DAQ choosing the
+// fullest queue, cheap unmaterialised spawns at every level let the waiting
+// frontier outgrow the frame pool (k = 5, scale 18, 1 GiB pool).
 //
 // Records (64 bytes):
 //   KC range [16] root, lo, hi, pad   [32] acc  [40] local
 //   KC set   [16] root, j  [24] set pointer  [32] len, lo  [40] hi, own  [48] acc  [56] local
-//   (own = 1: this task frees the set's scratch block when its subtree is done with it)
+//   own = kKcLazy: not materialised yet; set/len are P = N+(u), lo is w = v, hi is |C|
+//   own = 1: materialised set in a recycled scratch block, freed by this task when its subtree is done
+//   own = 0: a branch range of a set owned by an ancestor (or a set in never-recycled scratch)
 struct KcRangeSpawn { uint32_t root, lo, hi, pad; unsigned long long acc, local; };
 struct KcSetSpawn { uint32_t root, j; unsigned long long set; uint32_t len, lo, hi, own; unsigned long long acc, local; };
 constexpr uint32_t kKcRangeSlotAcc = 4, kKcRangeLocal = 40;
 constexpr uint32_t kKcSetSlotAcc = 6, kKcSetLocal = 56;
+constexpr uint32_t kKcSetPtr = 24, kKcSetLenLo = 32, kKcSetHiOwn = 40;
+constexpr uint32_t kKcLazy = 2;
 constexpr int kKcFan = 8;          // children per split
 constexpr int kKcMaxThr = 64;      // in-lane sets use 64-bit bitsets
 
@@ -352,14 +365,11 @@ static __device__ void kclique_range_step(TaskCtx& c) {
         if (need == 1) { local += (unsigned)cn; continue; }
         if (cn < need) continue;
         if (cn <= thr) { local += kc_count_small(C, cn, need, e.off, e.adj); continue; }
-        bool pooled;
-        int* S = kc_scratch_alloc(c, cn, &pooled);
-        if (!S) return;
-        kc_intersect(e.adj + ou, nu, AdjLoad{}, e.adj + ov, nv, AdjLoad{}, S, cn);
-        // the child adds its count into this range task's accumulator and owns the set
+        // the child materialises N+(u) n N+(v) when it runs and adds its count
+        // into this range task's accumulator
         c.spawn(T_KCLIQUE_SET, kKcRangeSlotAcc, kc_queue(e, 1),
-                KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)cn, 0u, (uint32_t)cn, pooled ? 1u : 0u,
-                           0ull, 0ull},
+                KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)(e.adj + ou), (uint32_t)nu, (uint32_t)v, (uint32_t)cn,
+                           kKcLazy, 0ull, 0ull},
                 kFlagAccumulate);
     }
     if (c.nspawned == 0) { c.ret(local); return; }
@@ -370,20 +380,40 @@ static __device__ void kclique_range_step(TaskCtx& c) {
 static __device__ void kclique_set_step(TaskCtx& c) {
     const KcSetSpawn a = c.load<KcSetSpawn>();
     const gtap_kclique_args& e = kc_env(c.P, a.root);
-    const int* set = reinterpret_cast<const int*>(a.set);
-    const uint32_t n = a.hi - a.lo;
     if (c.pc() != 0) {
-        // a split owner frees its set once all range children are done with it
-        if (a.own && n > (uint32_t)kKcFan) scratch_free(c.P, set, c.type(), c.worker);
+        // an owner frees its set once every task that reads it is done
+        if (a.own == 1u) scratch_free(c.P, reinterpret_cast<const int*>(a.set), c.type(), c.worker);
         c.ret(a.acc + a.local);
         return;
     }
+    const int* set = reinterpret_cast<const int*>(a.set);
+    uint32_t len = a.len, lo = a.lo, hi = a.hi, own = a.own;
+    if (own == kKcLazy) {
+        // materialise S = P n N+(w) (|S| = hi > thr, known from the spawn)
+        const int w = (int)a.lo;
+        const long long ow = kc_off(e, w);
+        const int nw = (int)(kc_off(e, w + 1) - ow);
+        bool pooled;
+        int* S = kc_scratch_alloc(c, (int)a.hi, &pooled);
+        if (!S) return;
+        kc_intersect(set, (int)a.len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, S, (int)a.hi);
+        set = S;
+        len = a.hi;
+        lo = 0;
+        own = pooled ? 1u : 0u;
+        // what the resume needs: the set to free
+        st_cg64(c.frame + kKcSetPtr, (unsigned long long)S);
+        st_cg64(c.frame + kKcSetLenLo, (unsigned long long)len);
+        st_cg64(c.frame + kKcSetHiOwn, (unsigned long long)hi | ((unsigned long long)own << 32));
+    }
     const int depth = e.k - 2 - (int)a.j + 1;
+    const uint32_t n = hi - lo;
     if (n > (uint32_t)kKcFan) {
         const uint32_t per = (n + kKcFan - 1) / kKcFan;
-        for (uint32_t s = a.lo; s < a.hi; s += per)
+        for (uint32_t s = lo; s < hi; s += per)
             c.spawn(T_KCLIQUE_SET, kKcSetSlotAcc, kc_queue(e, depth),
-                    KcSetSpawn{a.root, a.j, a.set, a.len, s, min(a.hi, s + per), 0u, 0ull, 0ull}, kFlagAccumulate);
+                    KcSetSpawn{a.root, a.j, (unsigned long long)set, len, s, min(hi, s + per), 0u, 0ull, 0ull},
+                    kFlagAccumulate);
         c.join(1, kc_queue(e, depth));
         return;
     }
@@ -391,26 +421,29 @@ static __device__ void kclique_set_step(TaskCtx& c) {
     const int need = (int)a.j - 1;
     unsigned long long local = 0;
     int C[kKcMaxThr];
-    for (uint32_t i = a.lo; i < a.hi; ++i) {
+    for (uint32_t i = lo; i < hi; ++i) {
         const int w = __ldcg(set + i);
         const long long ow = kc_off(e, w);
         const int nw = (int)(kc_off(e, w + 1) - ow);
-        const int cn = kc_intersect(set, (int)a.len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, C, thr);
+        const int cn = kc_intersect(set, (int)len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, C, thr);
         if (need == 1) { local += (unsigned)cn; continue; }
         if (cn < need) continue;
         if (cn <= thr) { local += kc_count_small(C, cn, need, e.off, e.adj); continue; }
+        // deeper sets are materialised here, by the spawning lane (see the header)
         bool pooled;
         int* S = kc_scratch_alloc(c, cn, &pooled);
         if (!S) return;
-        kc_intersect(set, (int)a.len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, S, cn);
+        kc_intersect(set, (int)len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, S, cn);
         c.spawn(T_KCLIQUE_SET, kKcSetSlotAcc, kc_queue(e, depth + 1),
                 KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)cn, 0u, (uint32_t)cn, pooled ? 1u : 0u,
                            0ull, 0ull},
                 kFlagAccumulate);
     }
-    // a leaf owner is done with its set here (its children work on their own sets)
-    if (a.own) scratch_free(c.P, set, c.type(), c.worker);
-    if (c.nspawned == 0) { c.ret(local); return; }
+    if (c.nspawned == 0) {
+        if (own == 1u) scratch_free(c.P, set, c.type(), c.worker);
+        c.ret(local);
+        return;
+    }
     st_cg64(c.frame + kKcSetLocal, local);
     c.join(1, kc_queue(e, depth));
 }
