@@ -534,6 +534,35 @@ __global__ void k_l2l(EvalBufs e, int lo, int hi) {
     }
 }
 
+// Packed FP32 pairs (two lanes of a 64-bit register) for the P2P inner loop:
+// one f32x2 instruction does the work of two FP32 ones.
+__device__ __forceinline__ unsigned long long pack_f32x2(float lo, float hi) {
+    return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float lo_f32(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float hi_f32(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ unsigned long long sub_f32x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul_f32x2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// 1/sqrt(x), the hardware approximation (inputs here are normal: distinct points)
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---------------------------------------------------------------------------
 // Leaf kernel: one block per leaf.  Threads are (target slot, source part):
 // each thread sums over every parts-th source point of the near-field list,
@@ -636,35 +665,62 @@ __global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
             __syncthreads();
             const int nfit = bnum[0];
             const int total = bpre[nfit];
-            for (int i = t; i < total; i += kLeafBlock) {
-                int a = 0, b = nfit - 1;   // last source with bpre[s] <= i
-                while (a < b) {
-                    const int mid = (a + b + 1) >> 1;
-                    if (bpre[mid] <= i) a = mid; else b = mid - 1;
+            if constexpr (sizeof(R) == 4) {
+                // pair records {x0 x1 | y0 y1 | z0 z1 | q0 q1} of source points 2m, 2m+1
+                // (an odd tail is padded with a far, chargeless point)
+                float4* pr = reinterpret_cast<float4*>(sp);
+                for (int m = t; 2 * m < total; m += kLeafBlock) {
+                    const int i0 = 2 * m;
+                    int a = 0, b = nfit - 1;   // last source leaf with bpre[s] <= i0
+                    while (a < b) {
+                        const int mid = (a + b + 1) >> 1;
+                        if (bpre[mid] <= i0) a = mid; else b = mid - 1;
+                    }
+                    const float4 l0 = e.ploc[bfirst[a] + (i0 - bpre[a])];
+                    const float4 p0 = make_float4(l0.x + boff[a * 3], l0.y + boff[a * 3 + 1], l0.z + boff[a * 3 + 2], l0.w);
+                    float4 p1 = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+                    if (i0 + 1 < total) {
+                        int a1 = a;   // skips empty entries (the target's own leaf counts 0 here)
+                        while (a1 + 1 < nfit && bpre[a1 + 1] <= i0 + 1) ++a1;
+                        const float4 l1 = e.ploc[bfirst[a1] + (i0 + 1 - bpre[a1])];
+                        p1 = make_float4(l1.x + boff[a1 * 3], l1.y + boff[a1 * 3 + 1], l1.z + boff[a1 * 3 + 2], l1.w);
+                    }
+                    pr[2 * m] = make_float4(p0.x, p1.x, p0.y, p1.y);
+                    pr[2 * m + 1] = make_float4(p0.z, p1.z, p0.w, p1.w);
                 }
-                const int k = bfirst[a] + (i - bpre[a]);
-                sid[i] = k;
-                if constexpr (sizeof(R) == 4) {
-                    const float4 pl = e.ploc[k];
-                    sp[i] = make_float4(pl.x + boff[a * 3], pl.y + boff[a * 3 + 1], pl.z + boff[a * 3 + 2], pl.w);
-                } else {
+            } else {
+                for (int i = t; i < total; i += kLeafBlock) {
+                    int a = 0, b = nfit - 1;   // last source leaf with bpre[s] <= i
+                    while (a < b) {
+                        const int mid = (a + b + 1) >> 1;
+                        if (bpre[mid] <= i) a = mid; else b = mid - 1;
+                    }
+                    const int k = bfirst[a] + (i - bpre[a]);
+                    sid[i] = k;
                     sp[i] = e.pts[k];
                 }
             }
             __syncthreads();
             if (active) {
                 if constexpr (sizeof(R) == 4) {
-                    // other leaves only: no self term; each batch is summed plainly and
-                    // added to the compensated total
-                    float bsum = 0.f;
-#pragma unroll 4
-                    for (int j = part; j < total; j += parts) {
-                        const float4 s = sp[j];
-                        const float dx = xi - s.x, dy = yi - s.y, dz = zi - s.z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        bsum = fmaf(s.w, rsqrtf(r2), bsum);
+                    // other leaves only: no self term.  Two source points per step in
+                    // packed FP32 pairs; each batch is summed plainly and added to the
+                    // compensated total
+                    const unsigned long long X2 = pack_f32x2(xi, xi), Y2 = pack_f32x2(yi, yi), Z2 = pack_f32x2(zi, zi);
+                    const ulonglong2* pr = reinterpret_cast<const ulonglong2*>(sp);
+                    const int npairs = (total + 1) >> 1;
+                    unsigned long long acc2 = 0ull;
+#pragma unroll 2
+                    for (int m = part; m < npairs; m += parts) {
+                        const ulonglong2 xy = pr[2 * m], zq = pr[2 * m + 1];
+                        const unsigned long long dx = sub_f32x2(X2, xy.x), dy = sub_f32x2(Y2, xy.y), dz = sub_f32x2(Z2, zq.x);
+                        unsigned long long r2 = mul_f32x2(dx, dx);
+                        r2 = fma_f32x2(dy, dy, r2);
+                        r2 = fma_f32x2(dz, dz, r2);
+                        const unsigned long long ir = pack_f32x2(rsqrt_ftz(lo_f32(r2)), rsqrt_ftz(hi_f32(r2)));
+                        acc2 = fma_f32x2(zq.y, ir, acc2);
                     }
-                    acc.add(bsum);
+                    acc.add(lo_f32(acc2) + hi_f32(acc2));
                 } else {
                     for (int j = part; j < total; j += parts) {
                         if (sid[j] == ki) continue;
