@@ -173,18 +173,21 @@ class Fmm:
     """A Laplace FMM plan plus the block-mode context its traversal runs on (marshalling only).
 
     ``run(pos, q)`` takes host or CUDA arrays (n x 3 and n, FP64) and returns the
-    potentials as a CUDA float64 tensor in input order."""
+    potentials as a CUDA float64 tensor in input order.  The traversal context
+    defaults to 6 resident blocks of 128 threads per SM, what its kernel's
+    registers allow (N = 2^20: 1.48 -> 1.20 ms uniform, 4.09 -> 3.27 ms Plummer
+    against 4 blocks)."""
 
     def __init__(self, order: int = 6, leaf_size: int = 64, theta: float = 0.5, mixed: bool = False,
                  fp64_levels: int = 3, threads_per_block: int = 128, pool_bytes: int = 1 << 30,
-                 deque_capacity: int = 4096, **cfg):
+                 deque_capacity: int = 4096, blocks_per_sm: int = 6, **cfg):
         fc = G.gtap_fmm_config()
         fc.order, fc.leaf_size, fc.theta = order, leaf_size, theta
         fc.precision = G.GTAP_FMM_MIXED if mixed else G.GTAP_FMM_FP64
         fc.fp64_levels = fp64_levels
         self.plan = G.gtap_fmm_create(fc)
         self.ctx = Context(G.GTAP_MODE_BLOCK, 1, pool_bytes=pool_bytes, threads_per_block=threads_per_block,
-                           deque_capacity=deque_capacity, **cfg)
+                           deque_capacity=deque_capacity, blocks_per_sm=blocks_per_sm, **cfg)
 
     def build(self, pos, q):
         import torch
