@@ -371,7 +371,24 @@ gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int6
         b.flags = f->flags.as<int>();
         b.pts = f->pts.as<Dbl4>();
         b.ploc = f->ploc.as<float4>();
-        if (launch_tree(b, f->s) != cudaSuccess) return GTAP_ERR_CUDA;
+        if (launch_tree_sort(b, f->s) != cudaSuccess) return GTAP_ERR_CUDA;
+        // Refine level by level.  A level without cells ends the tree, so between
+        // chunks of levels the host looks at the next level's size and stops at the
+        // first empty one (a uniform 2^20 set has 6 levels, a Plummer set 10, of 21).
+        int done = 0;
+        for (int chunk : {8, 4, 4, 5}) {
+            const int l1 = std::min(done + chunk, kMaxLevel);
+            if (launch_tree_levels(b, done, l1, f->s) != cudaSuccess) return GTAP_ERR_CUDA;
+            done = l1;
+            if (done >= kMaxLevel) break;
+            int ls[2] = {0, 0};   // the cells of level `done`: [ls[0], ls[1])
+            if (cudaMemcpyAsync(ls, f->lstart.as<int>() + done, sizeof(ls), cudaMemcpyDeviceToHost, f->s) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(f->s) != cudaSuccess)
+                return GTAP_ERR_CUDA;
+            if (ls[1] == ls[0]) break;
+        }
+        if (launch_tree_finish(b, done, f->s) != cudaSuccess) return GTAP_ERR_CUDA;
         int flags[4] = {0, 0, 0, 0};
         if (cudaMemcpyAsync(flags, f->flags.p, sizeof(flags), cudaMemcpyDeviceToHost, f->s) != cudaSuccess ||
             cudaMemcpyAsync(f->lstart_h, f->lstart.p, sizeof(f->lstart_h), cudaMemcpyDeviceToHost, f->s) != cudaSuccess ||
@@ -380,7 +397,13 @@ gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int6
             return GTAP_ERR_CUDA;
         f->order = b.order;
         if (!flags[0]) {
+            // the records were checked on the device before any later kernel follows their links
+            if (flags[1]) return GTAP_ERR_TASK_FAILED;
+            // only a cell of the deepest level can exceed leaf_size: more than
+            // kMaxLeaf points sharing one 21-bit Morton code are not supported
+            if (flags[3] > kMaxLeaf) return GTAP_ERR_INVALID_ARG;
             f->n_cells = f->lstart_h[kMaxLevel + 1];
+            f->n_leaves = flags[2];
             if (f->mixed && launch_leaf_local(b, f->n_cells, f->s) != cudaSuccess) return GTAP_ERR_CUDA;
             break;
         }
@@ -390,37 +413,6 @@ gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int6
     f->n_levels = 0;
     for (int l = 0; l <= kMaxLevel; ++l)
         if (f->lstart_h[l + 1] > f->lstart_h[l]) f->n_levels = l + 1;
-    // leaves: count from the cell records
-    {
-        std::vector<int4> info((size_t)f->n_cells);
-        if (cudaMemcpyAsync(info.data(), f->info.p, sizeof(int4) * info.size(), cudaMemcpyDeviceToHost, f->s) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(f->s) != cudaSuccess)
-            return GTAP_ERR_CUDA;
-        f->n_leaves = 0;
-        int max_leaf = 0;
-        for (int i = 0; i < f->n_cells; ++i) {
-            const int4 c = info[i];
-            const int level = c.w >> 8, nch = c.w & 0xFF;
-            // structural check of the records before any kernel follows their links
-            bool ok = c.x >= 0 && c.y >= 1 && (long long)c.x + c.y <= n && level >= 0 && level <= kMaxLevel;
-            if (c.z >= 0) {
-                ok = ok && c.z > i && nch >= 1 && nch <= 8 && c.z + nch <= f->n_cells;
-                if (ok)
-                    for (int j = 0; j < nch; ++j) ok = ok && (info[c.z + j].w >> 8) == level + 1;
-            } else {
-                ok = ok && c.z == -1 && nch == 0;
-            }
-            if (!ok) return GTAP_ERR_TASK_FAILED;
-            if (c.z < 0) {
-                ++f->n_leaves;
-                max_leaf = std::max(max_leaf, c.y);
-            }
-        }
-        // only a cell of the deepest level can exceed leaf_size: more than
-        // kMaxLeaf points sharing one 21-bit Morton code are not supported
-        if (max_leaf > kMaxLeaf) return GTAP_ERR_INVALID_ARG;
-    }
     cudaEventRecord(f->ev[1], f->s);
     const size_t ncoef = (size_t)f->n_cells * f->nt;
     if (!f->M.ensure(sizeof(double) * ncoef) || !f->L.ensure(sizeof(double) * ncoef)) return GTAP_ERR_NO_MEMORY;

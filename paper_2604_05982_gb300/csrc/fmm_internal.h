@@ -140,16 +140,22 @@ struct TreeBufs {
     int* cnt;                     // [cap_cells] per-level child counts
     int* off;                     // [cap_cells] their exclusive scan
     int* bounds;                  // [9 * cap_cells] octant boundaries
-    int* flags;                   // [4]: [0] cell capacity exceeded
+    int* flags;                   // [4]: [0] cell capacity exceeded, [1] malformed record, [2] leaves, [3] largest leaf
     Dbl4* pts;                 // sorted points {x, y, z, q}
     float4* ploc;                 // sorted points relative to their leaf centre {x, y, z, q} (FP32)
     const uint32_t* order;        // sorted position -> input index (one of vals[])
+    const unsigned long long* codes;   // sorted Morton codes (one of keys[])
 };
 constexpr int kBoxParts = 304;
 
 int radix_tiles(long long n);
-// Enqueue the whole build: bounding cube, Morton codes, sort, levels, gather.
-cudaError_t launch_tree(TreeBufs& b, cudaStream_t s);
+// Tree build in three stream-ordered parts: bounding box, Morton codes and
+// radix sort; refinement of levels [l0, l1); then the start entries of levels
+// left unrefined (all empty), the gather of points into tree order, and the
+// structural check of the cell records (flags[1..3]).
+cudaError_t launch_tree_sort(TreeBufs& b, cudaStream_t s);
+cudaError_t launch_tree_levels(const TreeBufs& b, int l0, int l1, cudaStream_t s);
+cudaError_t launch_tree_finish(const TreeBufs& b, int levels_done, cudaStream_t s);
 // Leaf-local FP32 coordinates (needs the cell count, known after the build).
 cudaError_t launch_leaf_local(const TreeBufs& b, int n_cells, cudaStream_t s);
 

@@ -268,7 +268,47 @@ int grid_for(long long n, int block, int cap) {
 
 int radix_tiles(long long n) { return (int)((n + kRsTile - 1) / kRsTile); }
 
-cudaError_t launch_tree(TreeBufs& b, cudaStream_t s) {
+// Levels from `from` down are empty (the refinement stopped early): their
+// start entries all equal lstart[from], as the full level loop would leave them.
+__global__ void k_lstart_tail(int* lstart, int from) {
+    const int v = lstart[from];
+    for (int k = from + 1 + (int)threadIdx.x; k <= kMaxLevel + 1; k += blockDim.x) lstart[k] = v;
+}
+
+// Structural check of the cell records before any kernel follows their links:
+// flags[1] = 1 on a malformed record; flags[2] = leaves; flags[3] = largest leaf.
+// The cell count is read from lstart[kMaxLevel + 1], never above `cap`.
+__global__ void k_check_tree(const int4* info, const int* lstart, int cap, long long n, int* flags) {
+    const int n_cells = min(lstart[kMaxLevel + 1], cap);
+    int bad = 0, leaves = 0, big = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cells; i += gridDim.x * blockDim.x) {
+        const int4 c = info[i];
+        const int level = c.w >> 8, nch = c.w & 0xFF;
+        bool ok = c.x >= 0 && c.y >= 1 && (long long)c.x + c.y <= n && level >= 0 && level <= kMaxLevel;
+        if (c.z >= 0) {
+            ok = ok && c.z > i && nch >= 1 && nch <= 8 && (long long)c.z + nch <= n_cells;
+            if (ok)
+                for (int j = 0; j < nch; ++j) ok = ok && (info[c.z + j].w >> 8) == level + 1;
+        } else {
+            ok = ok && c.z == -1 && nch == 0;
+            if (ok) {
+                ++leaves;
+                big = max(big, c.y);
+            }
+        }
+        if (!ok) bad = 1;
+    }
+    bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);
+    leaves = (int)__reduce_add_sync(0xffffffffu, (unsigned)leaves);
+    big = (int)__reduce_max_sync(0xffffffffu, (unsigned)big);
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(&flags[1], 1);
+        if (leaves) atomicAdd(&flags[2], leaves);
+        if (big) atomicMax(&flags[3], big);
+    }
+}
+
+cudaError_t launch_tree_sort(TreeBufs& b, cudaStream_t s) {
     const long long n = b.n;
     k_bbox_partial<<<kBoxParts, 256, 0, s>>>(b.pos, n, b.bbox_part);
     k_bbox_final<<<1, 32, 0, s>>>(b.bbox_part, kBoxParts, n, b.box, b.geom, b.info, b.lat, b.lstart, b.flags);
@@ -284,17 +324,27 @@ cudaError_t launch_tree(TreeBufs& b, cudaStream_t s) {
                                                  b.hist_scan, ntiles);
         cur ^= 1;
     }
-    const unsigned long long* codes = b.keys[cur];
+    b.codes = b.keys[cur];
     b.order = b.vals[cur];
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_levels(const TreeBufs& b, int l0, int l1, cudaStream_t s) {
     const int g = grid_for(b.cap_cells, 256, 1216);
-    for (int l = 0; l < kMaxLevel; ++l) {
-        k_level_count<<<g, 256, 0, s>>>(l, codes, b.info, b.lstart, b.leaf, b.bounds, b.cnt, b.lvl_n);
+    for (int l = l0; l < l1 && l < kMaxLevel; ++l) {
+        k_level_count<<<g, 256, 0, s>>>(l, b.codes, b.info, b.lstart, b.leaf, b.bounds, b.cnt, b.lvl_n);
         cudaError_t e = scan::exclusive(b.cnt, b.off, b.lvl_n + l, b.cap_cells, b.tile_sums, b.lvl_total + l, s);
         if (e != cudaSuccess) return e;
-        k_level_write<<<g, 256, 0, s>>>(l, codes, b.info, b.geom, b.lat, b.lstart, b.box, b.bounds, b.cnt, b.off,
+        k_level_write<<<g, 256, 0, s>>>(l, b.codes, b.info, b.geom, b.lat, b.lstart, b.box, b.bounds, b.cnt, b.off,
                                         b.lvl_total, b.cap_cells, b.flags);
     }
-    k_gather<<<grid_for(n, 256, 4096), 256, 0, s>>>(b.pos, b.q, b.order, n, b.pts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_finish(const TreeBufs& b, int levels_done, cudaStream_t s) {
+    if (levels_done < kMaxLevel) k_lstart_tail<<<1, 32, 0, s>>>(b.lstart, levels_done + 1);
+    k_gather<<<grid_for(b.n, 256, 4096), 256, 0, s>>>(b.pos, b.q, b.order, b.n, b.pts);
+    k_check_tree<<<grid_for(b.cap_cells, 256, 1216), 256, 0, s>>>(b.info, b.lstart, b.cap_cells, b.n, b.flags);
     return cudaGetLastError();
 }
 
