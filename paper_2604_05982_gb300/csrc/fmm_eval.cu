@@ -766,16 +766,34 @@ __global__ void __launch_bounds__(kLeafBlock) k_leaf(EvalBufs e) {
 }
 
 // ---------------------------------------------------------------------------
+// Counting sort of a list by target.  The traversal appends the child pairs of
+// one split pair together, so a warp's 32 entries often share a target: the
+// lanes of one target (found with __match_any_sync) make one atomic between
+// them.  The warp-uniform loop keeps all 32 lanes in every collective.
 __global__ void k_group_count(const unsigned long long* list, long long count, int* cnt) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[(int)(list[i] >> 32)], 1);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w < count; w += stride) {
+        const long long i = w + lane;
+        const int tg = (i < count) ? (int)(list[i] >> 32) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, tg);
+        if (tg >= 0 && lane == __ffs(grp) - 1) atomicAdd(&cnt[tg], __popc(grp));
+    }
 }
 
 __global__ void k_group_fill(const unsigned long long* list, long long count, const int* off, int* cursor, int* src) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long v = list[i];
-        const int tg = (int)(v >> 32);
-        src[off[tg] + atomicAdd(&cursor[tg], 1)] = (int)(v & 0xFFFFFFFFull);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w < count; w += stride) {
+        const long long i = w + lane;
+        const unsigned long long v = (i < count) ? list[i] : 0ull;
+        const int tg = (i < count) ? (int)(v >> 32) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, tg);
+        const int leader = __ffs(grp) - 1;
+        int base = 0;
+        if (tg >= 0 && lane == leader) base = atomicAdd(&cursor[tg], __popc(grp));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (tg >= 0) src[off[tg] + base + __popc(grp & ((1u << lane) - 1u))] = (int)(v & 0xFFFFFFFFull);
     }
 }
 
