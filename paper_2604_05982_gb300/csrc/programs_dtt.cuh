@@ -101,13 +101,16 @@ __device__ void dtt_step(BTaskCtx& c) {
         }
         __syncthreads();
         const int I = S.misc[0];
-        // classify the child pairs: 0 = M2L, 1 = P2P, 2 = unresolved, 3 = none
+        // classify the child pairs: 0 = M2L, 1 = P2P, 2 = unresolved, 3 = none.
+        // Items are strided over the threads (a round of ~100 items is one item
+        // per thread, not 8 dependent items on each of 13 threads while the block
+        // waits at the next barrier); lists and frontier take any order.
         unsigned long long iv[kPer];
         int cls[kPer];
         unsigned long long packed = 0;   // three 16-bit counts: M2L, P2P, unresolved
 #pragma unroll
         for (int r = 0; r < kPer; ++r) {
-            const int i = t * kPer + r;
+            const int i = r * BS + t;
             cls[r] = 3;
             iv[r] = 0;
             if (i < I) {
