@@ -55,6 +55,8 @@ def test_fmm_matches_oracle(dist, mixed):
         assert np.array_equal(_pairs(g_p2p), _pairs(p2p))
         info = f.info()
         assert info["n_cells"] == nc and info["n_m2l"] == len(m2l) and info["n_p2p"] == len(p2p)
+        cells, _ = oracle.fmm_tree(pos, leaf_size=leaf)
+        assert info["n_leaves"] == int((cells[:, 3] < 0).sum())   # counted by the device-side record check
     err = _rel_l2(phi, ref)
     assert err <= (MIXED_TOL if mixed else FP64_TOL), err
 
