@@ -319,6 +319,12 @@ def run_reference(args):
     if args.workload == "fmm":
         run_reference_fmm(args)
         return
+    if args.workload == "kclique":
+        run_reference_kclique(args)
+        return
+    if args.workload == "serve":
+        run_reference_serve(args)
+        return
     import oracle
     oracle.build()
     try:
@@ -540,6 +546,61 @@ def _fmm_cpu_sample():
 KC_SCALE = 20
 KC_K = 4
 KC_QUEUES = 4
+KC_CPU_RANGES = 2048     # oracle sample: evenly spaced DAG-edge ranges ...
+KC_CPU_RANGE = 64        # ... of this many edges each (~0.8 % of the scale-20 graph's edges)
+
+
+def _pin_one_core():
+    try:
+        os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    except (AttributeError, OSError):
+        pass
+
+
+def _kclique_cpu_sample(n, e):
+    """One oracle k-clique instance estimated on one core: the orientation in full,
+    the counting on KC_CPU_RANGES evenly spaced ranges of KC_CPU_RANGE DAG edges,
+    scaled to all edges.  Returns (ms per instance, seconds spent)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    m = len(e)
+    t0 = time.perf_counter()
+    off, adj = oracle.orient(n, e)
+    t1 = time.perf_counter()
+    starts = np.arange(KC_CPU_RANGES, dtype=np.int64) * (m // KC_CPU_RANGES)
+    ranges = np.stack([starts, np.minimum(starts + KC_CPU_RANGE, m)], axis=1)
+    oracle.kclique_dag_ranges(off, adj, KC_K, ranges)
+    t2 = time.perf_counter()
+    sampled = int((ranges[:, 1] - ranges[:, 0]).sum())
+    return ((t1 - t0) + (t2 - t1) * m / sampled) * 1e3, t2 - t0
+
+
+def _kclique_cpu_note(m):
+    return (f"oracle on one core: orientation of the whole graph, then the {KC_K}-clique count on "
+            f"{KC_CPU_RANGES} evenly spaced ranges of {KC_CPU_RANGE} DAG edges, scaled to all {m} edges")
+
+
+def run_reference_kclique(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2604_05982_gb300 import inputs
+    _pin_one_core()
+    n, e = inputs.rmat_graph(KC_SCALE, 16, seed=7)
+    for _ in range(min(args.warmup, 1)):
+        _kclique_cpu_sample(n, e)
+    vals = [_kclique_cpu_sample(n, e)[0] for _ in range(args.steps)]
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": "k-clique time", "value": value, "unit": "ms/instance", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{KC_K}-clique count, R-MAT scale {KC_SCALE} edge factor 16, seed 7 (oracle)"},
+            "cpu_baseline": {"value": value, "unit": "ms/instance", "cores": 1, "kind": "oracle",
+                             "sample": _kclique_cpu_note(len(e))},
+            "e2e": {"value": value, "unit": "ms/instance", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 def run_kclique(args):
@@ -615,6 +676,11 @@ def run_kclique(args):
         "gpu_launches": (9 + 2) * args.steps,
         "clocks": clk.summary(),
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _pin_one_core()
+        value, _ = _kclique_cpu_sample(n, e)
+        line["cpu_baseline"] = {"value": value, "unit": "ms/instance", "cores": 1, "kind": "oracle",
+                                "sample": _kclique_cpu_note(m)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -623,11 +689,64 @@ def run_kclique(args):
 
 SERVE_REQUESTS = 20000
 SERVE_RATE = 5000.0
+SERVE_CPU_SAMPLE = 200   # oracle sample: the first requests of the trace
+
+
+def _serve_cpu_sample(reqs, n_sample):
+    """The oracle answering the first n_sample requests of the trace one after
+    another on one core (arrival times ignored, i.e. a saturated server).
+    Returns (requests/s, seconds spent)."""
+    import oracle
+    from paper_2604_05982_gb300 import inputs
+    oracle.build()
+    graphs = {s: inputs.rmat_graph(s, 16, seed=7) for s in range(10, 15)}
+    sample = reqs[:n_sample]
+    t0 = time.perf_counter()
+    for i, (kind, x) in enumerate(sample):
+        if kind == "fib":
+            oracle.fib(x)
+        elif kind == "nqueens":
+            oracle.nqueens(x)
+        elif kind == "kclique":
+            oracle.kclique(*graphs[x], 4)
+        else:
+            oracle.uts(seed=1000 + i, root_children=x, m=5)
+    secs = time.perf_counter() - t0
+    return len(sample) / secs, secs
+
+
+def _serve_cpu_note(n_sample):
+    return (f"oracle on one core answering the first {n_sample} requests of the same trace one after another "
+            "(arrivals ignored: a saturated server)")
+
+
+def run_reference_serve(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    _pin_one_core()
+    _, reqs = _serve_trace(args.requests, SERVE_RATE)
+    n_sample = min(SERVE_CPU_SAMPLE, len(reqs))
+    for _ in range(min(args.warmup, 1)):
+        _serve_cpu_sample(reqs, n_sample)
+    vals = [_serve_cpu_sample(reqs, n_sample)[0] for _ in range(args.steps)]
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": "served requests/s", "value": value, "unit": "req/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_sample / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "served mix: fib n in [20,32], N-Queens n in [8,12], 4-clique on R-MAT scale "
+                                   "[10,14], hashed tree root [100,2000] (oracle)"},
+            "cpu_baseline": {"value": value, "unit": "req/s", "cores": 1, "kind": "oracle",
+                             "sample": _serve_cpu_note(n_sample)},
+            "e2e": {"value": value, "unit": "req/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 def _serve_trace(n_req, rate, seed=11):
     """Poisson arrivals and the served mix: fib n in [20,32], N-Queens n in [8,12],
     4-clique on an R-MAT graph of scale in [10,14], hashed tree with root branching in [100,2000]."""
+    import numpy as np
+
     from paper_2604_05982_gb300 import inputs
     arrivals, u = inputs.poisson_trace(n_req, rate, seed)
     v = inputs.u01(seed ^ 0x7E57, 0, n_req)
@@ -742,6 +861,12 @@ def run_serve(args):
             "per_request_launch": {"value": n_req / span_base, "unit": "req/s", "p50_ms": pct(lat_base, 50),
                                    "p99_ms": pct(lat_base, 99)},
             "results_identical_alone_and_in_mix": bool(identical)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _pin_one_core()
+        n_sample = min(SERVE_CPU_SAMPLE, n_req)
+        rps, _ = _serve_cpu_sample(reqs, n_sample)
+        line["cpu_baseline"] = {"value": rps, "unit": "req/s", "cores": 1, "kind": "oracle",
+                                "sample": _serve_cpu_note(n_sample)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

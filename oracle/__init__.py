@@ -62,6 +62,7 @@ def _load():
                 "orc_orient": (None, [i64, P, i64, i32, P, P]),
                 "orc_kclique_brute": (u64, [i32, P, i64, i32]),
                 "orc_kclique_edge_range": (u64, [i64, P, i64, i32, i32, i64, i64]),
+                "orc_kclique_dag_ranges": (u64, [i64, P, P, i32, P, i64]),
                 "orc_fmm": (i32, [i64, P, P, i32, f64, i32, P, i64, P, P, P, P, P, i64, P, i64]),
                 "orc_fmm_tree": (i64, [i64, P, i32, P, i64, P]),
                 "orc_direct": (None, [i64, P, P, P, i64, P]),
@@ -164,6 +165,15 @@ def kclique_edge_range(n: int, edges: np.ndarray, k: int, lo: int, hi: int, orde
     """Sum of per-DAG-edge k-clique counts over DAG edges [lo, hi)."""
     edges = np.ascontiguousarray(edges, dtype=np.int32)
     return int(_load().orc_kclique_edge_range(n, _ptr(edges), edges.shape[0], k, {"degree": 0, "id": 1}[order], lo, hi))
+
+
+def kclique_dag_ranges(off: np.ndarray, adj: np.ndarray, k: int, ranges) -> int:
+    """Sum of per-DAG-edge k-clique counts over several edge ranges [lo, hi) of a
+    graph already oriented by `orient` (for timing a sample of a large graph)."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    rg = np.ascontiguousarray(np.asarray(ranges, dtype=np.int64).reshape(-1, 2))
+    return int(_load().orc_kclique_dag_ranges(off.shape[0] - 1, _ptr(off), _ptr(adj), k, _ptr(rg), rg.shape[0]))
 
 
 def fmm(pos: np.ndarray, q: np.ndarray, p: int = 6, theta: float = 0.5, leaf_size: int = 64,

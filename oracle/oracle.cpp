@@ -341,6 +341,32 @@ uint64_t orc_kclique_edge_range(int64_t n, const int32_t* edges, int64_t m, int 
     return total;
 }
 
+// Sum of the per-edge counts over several DAG-edge ranges [ranges[2i],
+// ranges[2i+1]) of a graph already oriented (off/adj as orc_orient returns
+// them): the recursion of orc_kclique without the orientation step, so that a
+// sample of a large graph can be timed on its own.
+uint64_t orc_kclique_dag_ranges(int64_t n, const int64_t* off, const int32_t* adj, int k, const int64_t* ranges,
+                                int64_t n_ranges) {
+    Dag g;
+    g.off.assign(off, off + n + 1);
+    g.adj.assign(adj, adj + off[n]);
+    const int64_t m = off[n];
+    uint64_t total = 0;
+    for (int64_t r = 0; r < n_ranges; ++r) {
+        const int64_t lo = ranges[2 * r], hi = ranges[2 * r + 1];
+        int64_t u = 0;
+        for (int64_t p = lo; p < hi && p < m; ++p) {
+            while (g.off[u + 1] <= p) ++u;
+            int32_t v = g.adj[p];
+            std::vector<int32_t> C = intersect(g.adj.data() + g.off[u], g.off[u + 1] - g.off[u],
+                                               g.adj.data() + g.off[v], g.off[v + 1] - g.off[v]);
+            if (k == 3) total += C.size();
+            else if ((int)C.size() >= k - 2) total += count_in(g, C, k - 2);
+        }
+    }
+    return total;
+}
+
 // The oriented DAG itself (CSR), for checking the GPU orientation step.
 // off has n+1 entries, adj has m entries.
 void orc_orient(int64_t n, const int32_t* edges, int64_t m, int order_mode, int64_t* off, int32_t* adj) {

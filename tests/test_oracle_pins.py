@@ -259,6 +259,18 @@ def test_kclique_edge_range_sums_per_edge_counts():
         assert oracle.kclique_edge_range(n, edges, 4, lo, hi) == int(pe[lo:hi].sum())
 
 
+def test_kclique_dag_ranges_on_a_preoriented_graph():
+    # several ranges of an already oriented DAG sum the per-edge counts of those ranges
+    n, edges = inputs.rmat_graph(9, 16, seed=5)
+    off, adj = oracle.orient(n, edges)
+    m = len(edges)
+    for k in (3, 4, 5):
+        total, pe = oracle.kclique(n, edges, k, per_edge=True)
+        assert oracle.kclique_dag_ranges(off, adj, k, [(0, m)]) == total
+        ranges = [(0, 10), (37, 400), (m - 5, m), (500, 500)]
+        assert oracle.kclique_dag_ranges(off, adj, k, ranges) == sum(int(pe[lo:hi].sum()) for lo, hi in ranges)
+
+
 # ---------------------------------------------------------------------------
 # Laplace FMM (Sec. 6.4.1).  The plain definition is the direct sum
 # phi_i = sum_{j != i} q_j / |x_i - x_j|; the pins below tie the stepwise
