@@ -390,11 +390,14 @@ gtap_status gtap_fmm_create(const gtap_fmm_config* cfg, gtap_fmm** out);
  * caller owned and read during the call only.  1 <= n < 2^31; more than 64
  * points sharing one cell of the deepest level (21) is GTAP_ERR_INVALID_ARG.  Grows the
  * plan's device buffers when needed (cudaMalloc); returns after completion.
- * Errors: GTAP_ERR_INVALID_ARG, GTAP_ERR_NO_MEMORY, GTAP_ERR_CUDA. */
+ * The cell records are checked on the device (bounds, then child links) before
+ * any later kernel follows them; a failed check is GTAP_ERR_TASK_FAILED.
+ * Errors: GTAP_ERR_INVALID_ARG, GTAP_ERR_NO_MEMORY, GTAP_ERR_CUDA, GTAP_ERR_TASK_FAILED. */
 gtap_status gtap_fmm_build(gtap_fmm* f, const double* pos, const double* q, int64_t n);
 /* Build the M2L and P2P lists by running "fmm_dtt" from the root pair on ctx,
- * a block-mode context (gtap_init(GTAP_MODE_BLOCK, 1, ...)); the context's
- * pending roots are replaced.  On overflow the lists are grown to the sizes
+ * a block-mode context (gtap_init(GTAP_MODE_BLOCK, 1, ...); 128 threads per
+ * block and blocks_per_sm = 6, what the traversal kernel's registers allow, is
+ * the fastest GB300 setting measured); the context's pending roots are replaced.  On overflow the lists are grown to the sizes
  * the run counted and the traversal is repeated once.  Errors: those of
  * gtap_run/gtap_wait, GTAP_ERR_LIST_OVERFLOW, GTAP_ERR_INVALID_ARG (plan not
  * built, or ctx not in block mode). */
