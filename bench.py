@@ -371,8 +371,20 @@ def m2l_flops_per_pair(p: int) -> int:
     return fl + 2 * terms
 
 
+FMM_LEVEL_CHUNKS = (8, 12, 16, 21)   # the tree build checks for an empty level after these levels
+
+
+def _fmm_levels_refined(n_levels: int) -> int:
+    """Levels the tree build refines: up to the first chunk boundary at or past the
+    first empty level (levels 0 .. n_levels-1 hold cells)."""
+    return next((b for b in FMM_LEVEL_CHUNKS if b >= n_levels), FMM_LEVEL_CHUNKS[-1])
+
+
 def _fmm_kernels_per_instance(n_levels: int, mixed: bool) -> int:
-    tree = 2 + 1 + 8 * 5 + 21 * 5 + 1 + (1 if mixed else 0)
+    done = _fmm_levels_refined(n_levels)
+    # bbox (2), codes, 8 radix passes (histogram, 3-kernel scan, scatter), 5 kernels per refined level,
+    # level-start tail when stopped early, gather, record check, leaf-local coordinates (mixed)
+    tree = 2 + 1 + 8 * 5 + done * 5 + (1 if done < 21 else 0) + 1 + 1 + (1 if mixed else 0)
     upward = 1 + max(n_levels - 1, 0)
     traverse = 2
     evaluate = 2 * 5 + 2 + max(n_levels - 1, 0) + 1
