@@ -50,6 +50,15 @@ def test_mergesort_2pow26_full_size():
     assert np.array_equal(out, oracle.sort_u32(keys))
 
 
+@pytest.mark.parametrize("bps", [3, 6])
+def test_mergesort_2pow26_bench_launch_configuration(bps):
+    # the configuration the bench times: 4096-key leaves, 65536-key merge pieces,
+    # the block counts per SM the autotuner picks, rings of 16384
+    keys = inputs.keys_u32(1 << 26, seed=1)
+    out, _ = _sort_on_gpu(keys, leaf=4096, merge_cutoff=65536, blocks_per_sm=bps, deque_capacity=16384)
+    assert np.array_equal(out, oracle.sort_u32(keys))
+
+
 @pytest.mark.parametrize("grid", [1, 2])
 def test_mergesort_small_grid(grid):
     keys = inputs.keys_u32(50000, seed=2)
