@@ -103,3 +103,57 @@ def test_scratch_blocks_are_recycled():
         r = runner.kclique(g, 5, split_threshold=8, scratch_bytes=256 << 20)
         assert r.values == [math.comb(n, 5)]
     assert r.stats["scratch_used"] <= (256 << 20)
+
+
+def _golden(name):
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_kclique_goldens", os.path.join(here, "make_kclique_goldens.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    path = os.path.join(here, name)
+    if not os.path.exists(path):
+        pytest.skip(f"golden file {name} not written")
+    return mod.load(path), mod
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    n, e = inputs.rmat_graph(20, 16, seed=7)
+    return n, e, _graph(n, e)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_scale20_full_count_and_64_ranges_match_oracle_golden(rmat20, k):
+    # the whole graph in the bench's launch configuration (DAQ: 4 queues by recursion
+    # depth, split threshold 64, 1 GiB record pool, 4 GiB scratch), then the 64
+    # golden ranges that partition the DAG edges as 64 roots of one launch
+    gold, _ = _golden(f"kclique_rmat20_k{k}.txt")
+    n, e, g = rmat20
+    assert (gold["n"], gold["m"]) == (n, g.m)
+    cfg = dict(n_queues=4, route=1, scratch_bytes=4 << 30, deque_capacity=16384)
+    assert runner.kclique(g, k, split_threshold=64, **cfg).values == [gold["total"]]
+    ranges = [(lo, hi) for lo, hi, _ in gold["ranges"]]
+    r = runner.kclique([g] * len(ranges), k, split_threshold=64, ranges=ranges, **cfg)
+    assert r.values == [c for _, _, c in gold["ranges"]]
+
+
+def test_batch64_one_launch_matches_oracle_golden():
+    # 64 R-MAT graphs of scales 12..18 (graph i: scale 12 + floor(7i/64), seed 7 + i)
+    # in one persistent launch, each count against the oracle's
+    gold, mod = _golden("kclique_batch64_k4.txt")
+    graphs = []
+    for i, scale, seed, m, _ in gold["graphs"]:
+        assert mod.batch64_graph(i) == (scale, seed)
+        n, e = inputs.rmat_graph(scale, 16, seed=seed)
+        assert len(e) == m
+        graphs.append(_graph(n, e))
+    want = [c for *_, c in gold["graphs"]]
+    # DAQ 4 by depth: the frontier of 64 instances needs rings of 16384 (4096 overflows)
+    cfg = dict(n_queues=4, route=1, scratch_bytes=4 << 30, deque_capacity=16384)
+    r = runner.kclique(graphs, 4, **cfg)
+    assert r.values == want
+    # the same instances one launch each give the same counts
+    for i in (0, 31, 63):
+        assert runner.kclique(graphs[i], 4, **cfg).values == [want[i]]
