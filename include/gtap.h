@@ -66,7 +66,8 @@ typedef enum { GTAP_MODE_THREAD = 0, GTAP_MODE_BLOCK = 1 } gtap_mode;
  * all defaults. */
 typedef struct {
     int blocks_per_sm;      /* persistent grid = blocks_per_sm x SM count (default: 4 thread mode, 2 block mode) */
-    int threads_per_block;  /* thread mode: 64..1024, multiple of 32 (default 256); block mode: 128 or 256 (default 256) */
+    int threads_per_block;  /* thread mode: 32..256, multiple of 32 (default 256); block mode: 128 or 256
+                               (default 256), or 32 for "bintree_block" */
     int deque_capacity;     /* ring slots per queue, power of two (default 4096 thread mode, 1024 block mode) */
     int steal_policy;       /* GTAP_STEAL_* bits (default GTAP_STEAL_FILL) */
     int max_roots;          /* capacity of the root table (default 4096) */
@@ -81,7 +82,24 @@ typedef struct {
     int grid_blocks;        /* explicit persistent grid size (overrides blocks_per_sm x SM count), e.g. 1 */
     int debug_checks;       /* 1: track every record's state (free / allocated / running) and report
                                double allocation, double free or double execution as GTAP_ERR_TASK_FAILED */
+    int scheduler;          /* thread-mode queue management (GTAP_SCHED_*, default GTAP_SCHED_BATCHED);
+                               the alternatives exist for the scheduler comparison of Sec. 6.5 */
+    int pad_;
 } gtap_config;
+
+/* Thread-mode scheduler designs compared in Sec. 6.5 ("GPU-Side Scheduler
+ * Comparison").  All share the runtime (records, joins, termination) and
+ * differ only in queue management.
+ *   GTAP_SCHED_BATCHED: per-warp deques with warp-cooperative batched pop and
+ *     steal (Alg. 1 and 2), the default.
+ *   GTAP_SCHED_GLOBAL: one centralised queue shared by every warp: a warp
+ *     claims up to 32 - cnt tasks per claim from its head and publishes new
+ *     tasks at its tail (ticketed slots, one claim and one publish per batch).
+ *   GTAP_SCHED_SINGLE: per-warp deques, non-batched: the warp's lanes issue
+ *     up to 32 single-task pops, then single-task steals, one CAS per task. */
+#define GTAP_SCHED_BATCHED 0
+#define GTAP_SCHED_GLOBAL 1
+#define GTAP_SCHED_SINGLE 2
 
 /* Per-run statistics, summed over workers (gtap_get_stats). */
 typedef struct {
@@ -115,16 +133,28 @@ typedef struct {
 
 typedef struct gtap_ctx gtap_ctx;
 
-/* Create a context: mode, number of DAQ queues per warp (1..8; block mode
- * requires 1, as the queue clause is not supported there, Sec. 4.3), and the
- * size of the task-record pool in bytes.  All storage is allocated here.
+/* Create a context (Sec. 4, gtap_initialize(config): all runtime storage
+ * is reserved before any task runs): mode, number of DAQ queues per warp
+ * (1..8; block mode requires 1, as the queue clause is not supported there,
+ * Sec. 4.3), and the size of the task-record pool in bytes.  All storage is
+ * allocated here, or carved from cfg->device_arena when the caller gives one
+ * (see gtap_arena_bytes for the size it needs).
  * Errors: GTAP_ERR_INVALID_ARG, GTAP_ERR_NO_MEMORY, GTAP_ERR_CUDA. */
 gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, const gtap_config* cfg,
                       gtap_ctx** out);
 
+/* Bytes of device memory gtap_init needs for these arguments: the size a
+ * caller-owned cfg->device_arena must have (256-byte aligned).  Reads the
+ * SM count of the current device; allocates nothing.
+ * Errors: those of gtap_init's argument checks, GTAP_ERR_CUDA. */
+gtap_status gtap_arena_bytes(gtap_mode mode, int n_queues, size_t frame_pool_bytes, const gtap_config* cfg,
+                             size_t* out);
+
 /* Select a built-in task program by name and get its type ID for
- * gtap_spawn_root.  Thread mode: "fib", "nqueens", "uts", "kclique",
- * "integrate".  Block mode: "mergesort", "integrate_block", "fmm_dtt".
+ * gtap_spawn_root (the programs of Sec. 6, written as the continuation state
+ * machines Sec. 5.2 lowers tasks into).  Thread mode: "fib", "nqueens", "uts",
+ * "kclique", "integrate", "bintree".  Block mode: "mergesort",
+ * "integrate_block", "fmm_dtt", "bintree_block".
  * Errors: GTAP_ERR_INVALID_ARG for an unknown name or the wrong mode. */
 gtap_status gtap_register_task(gtap_ctx* ctx, const char* program, int* out_type);
 
@@ -137,7 +167,8 @@ gtap_status gtap_register_task(gtap_ctx* ctx, const char* program, int* out_type
 gtap_status gtap_spawn_root(gtap_ctx* ctx, int type, const void* args, size_t args_bytes, int queue,
                             uint64_t* out_handle);
 
-/* Start one persistent-kernel run over the queued roots, asynchronously on
+/* Start one persistent-kernel run over the queued roots (Sec. 4,
+ * gtap_launch; the kernel is the scheduler loop of Alg. 1), asynchronously on
  * the configured stream: a reset kernel re-zeroes deques, pool and control
  * words and writes the root records, then the scheduler kernel runs until
  * every root has completed (or an error/abort).  The queued roots stay
@@ -145,24 +176,35 @@ gtap_status gtap_spawn_root(gtap_ctx* ctx, int type, const void* args, size_t ar
  * Errors: GTAP_ERR_INVALID_ARG (no roots), GTAP_ERR_BUSY, GTAP_ERR_CUDA. */
 gtap_status gtap_run(gtap_ctx* ctx);
 
-/* Wait for the run started by gtap_run, at most timeout_ms milliseconds
- * (0 = the config's device deadline plus a margin).  Never hangs: on
+/* Wait for the run started by gtap_run (Sec. 4: the host regains control
+ * when every task has completed, Alg. 1's termination test), at most
+ * timeout_ms milliseconds (0 = the config's device deadline plus a margin).  Never hangs: on
  * timeout it raises the device abort flag, waits for the kernel to drain and
  * returns GTAP_ERR_TIMEOUT.  Returns the device-side error code if the run
  * failed.  Results and statistics are read back here. */
 gtap_status gtap_wait(gtap_ctx* ctx, uint64_t timeout_ms);
 
-/* Copy the result of a completed root (bytes <= 16) into out (host).
+/* Copy the result of a completed root (bytes <= 16) into out (host): the
+ * value the root task returned (Sec. 4.1, values returned from tasks; Sec.
+ * 5.1.2, the result a completing task writes for its parent).
  * Errors: GTAP_ERR_INVALID_ARG (bad handle), GTAP_ERR_NOT_READY. */
 gtap_status gtap_read_result(gtap_ctx* ctx, uint64_t handle, void* out, size_t bytes);
 
-/* Statistics of the last completed run. */
+/* Statistics of the last completed run: task, pop, steal and push counts
+ * of the scheduler loop (Alg. 1, Alg. 2) and its per-phase cycle counters. */
 gtap_status gtap_get_stats(gtap_ctx* ctx, gtap_stats* out);
 
 /* Structured report of the last device-side error (code 0 if none). */
 gtap_status gtap_last_error(gtap_ctx* ctx, gtap_error_info* out);
 
 /* Forget the queued roots (the next gtap_spawn_root starts a new batch). */
+
+/* Change the device-side run deadline (gtap_config.timeout_ns) of later runs;
+ * 0 restores the default of 60 s.  A run past its deadline drains and
+ * gtap_wait returns GTAP_ERR_TIMEOUT (Sec. 4: execution aborts with a
+ * structured report).  Drops a captured graph.  Errors: GTAP_ERR_BUSY while a
+ * run is in flight. */
+gtap_status gtap_set_timeout(gtap_ctx* ctx, uint64_t timeout_ns);
 gtap_status gtap_clear_roots(gtap_ctx* ctx);
 
 /* ------------------------------------------------------------------------
@@ -196,6 +238,13 @@ gtap_status gtap_submit(gtap_ctx* ctx, int type, const void* args, size_t args_b
  * drains; call gtap_serve_stop), else GTAP_OK. */
 gtap_status gtap_poll(gtap_ctx* ctx, gtap_completion* out, int max, int* n);
 
+/* Serving progress, read from host and mapped memory without touching the
+ * device: up to n of [0] requests submitted, [1] requests the device has
+ * admitted (taken from the inbox), [2] completions gtap_poll has returned.
+ * [0] - [1] is the inbox backlog (waiting for admission), [1] - [2] the
+ * requests on the device or completed and not yet polled. */
+gtap_status gtap_serve_progress(gtap_ctx* ctx, uint64_t* out, int n);
+
 /* Close the inbox: the kernel admits what was submitted, finishes it and
  * exits; waits at most timeout_ms (0: the device deadline), then raises the
  * abort word.  Returns the device status. */
@@ -222,7 +271,8 @@ gtap_status gtap_debug_snapshot(gtap_ctx* ctx, uint64_t* out, int n);
 /* Human-readable name of a status code (static storage). */
 const char* gtap_status_string(gtap_status s);
 
-/* Release every resource of the context (waits for an in-flight run first). */
+/* Release every resource of the context (Sec. 4, gtap_finalize; waits for
+ * an in-flight run first). */
 gtap_status gtap_finalize(gtap_ctx* ctx);
 
 /* ------------------------------------------------------------------------
@@ -250,6 +300,25 @@ typedef struct { uint64_t seed; uint64_t threshold; uint32_t root_children; uint
 /* Adaptive trapezoid integration of 1/(1+25x^2) over [a, b] (Program 1).
  * Thread mode ("integrate") and block mode ("integrate_block").  Result: double. */
 typedef struct { double a; double b; double eps; } gtap_integrate_args;
+
+/* Full binary task tree (Sec. 6.1 "Understanding the Execution Modes", Sec. 6.2
+ * "Effect of Divergence-Aware Queueing"), thread mode ("bintree") and block
+ * mode ("bintree_block").  Node ids: root 1, children of v are 2v and 2v+1;
+ * the leaves are the 2^depth nodes of level `depth`.  Each leaf runs a
+ * data-parallel loop of `iters` iterations of one of K (1..4) compute
+ * functions, k(v) = (splitmix64(v) >> 32) mod K (0 when K = 1), known at
+ * spawn:  value(v) = sum_{i < iters} g_k((v << 32) + i) mod 2^64 with
+ *   g_0(x): z = x * 0x9E3779B97F4A7C15; z ^= z >> 29; z *= 0xBF58476D1CE4E5B9; z ^ (z >> 32)
+ *   g_1(x): z = x ^ (x << 13); z ^= z >> 7; z ^= z << 17; z * 0x2545F4914F6CDD1D
+ *   g_2(x): z = (x + 0x632BE59BD9B4E019) * 0x94D049BB133111EB; rotl(z, 23) ^ (z >> 11)
+ *   g_3(x): z = x ^ (x >> 32); z *= 0xD6E8FEB86659FD93; z ^ (z >> 28)
+ * Result: uint64 sum of the leaf values mod 2^64.  Thread mode: one lane runs
+ * a leaf's loop; route 1 sends inner nodes to queue 0 and a leaf of function k
+ * to queue 1 + k (DAQ; use n_queues = K + 1).  Block mode: the block runs a
+ * leaf's loop with its iterations strided over the threads; cutoff c > 0 makes
+ * a node c levels above the leaves run its whole subtree as one task (thread
+ * mode requires cutoff 0).  depth <= 30. */
+typedef struct { int32_t depth; int32_t iters; int32_t K; int32_t route; int32_t cutoff; int32_t pad; } gtap_bintree_args;
 
 /* Block-mode mergesort (Cilksort with a forked parallel merge, Sec. 6.3) of
  * n uint32 keys from src (device, read only) into dst (device); tmp (device,
@@ -423,13 +492,15 @@ gtap_status gtap_fmm_destroy(gtap_fmm* f);
  *
  * gtap_mergesort_noalloc sorts n uint32 keys from src into dst (both device
  * pointers owned by the caller; src may equal dst) with the block-mode
- * mergesort above, for callers that cannot allocate device memory: code that
- * runs while someone else captures a CUDA graph, real-time paths whose memory
- * is fixed up front, plugins that are handed a stream but own no memory.  All
- * working memory (key scratch, task records, deques, control words) lives in
- * one fixed file-scope device array of about 10 MB, which every GPU that loads
- * the library holds until the process exits; the call makes no cudaMalloc or
- * cudaFree and uses no allocating library routine.
+ * mergesort above, for callers that cannot allocate device memory: plugins
+ * and libraries loaded into a host application that owns all device memory
+ * and hands them only a stream and buffers, real-time paths whose memory
+ * budget is fixed before they start, and code running under an allocator
+ * that must not be re-entered.  All working memory (key scratch, task
+ * records, deques, control words) lives in one fixed file-scope device array
+ * of about 10 MB, which every GPU that loads the library holds until the
+ * process exits; the call makes no cudaMalloc or cudaFree and uses no
+ * allocating library routine.
  *   - n must be at most 2^20 (1,048,576); larger n returns GTAP_ERR_INVALID_ARG.
  *   - The first call on a device sets that device up (it looks up the array's
  *     device address); make that first call before any stream capture.

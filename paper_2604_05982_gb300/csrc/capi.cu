@@ -35,6 +35,8 @@ const ProgInfo kPrograms[] = {
     {"mergesort", GTAP_MODE_BLOCK, T_MSORT, PS_MSORT},
     {"integrate_block", GTAP_MODE_BLOCK, T_INTEGRATE_BLK, PS_INTEGRATE_BLK},
     {"fmm_dtt", GTAP_MODE_BLOCK, T_DTT, PS_DTT},
+    {"bintree", GTAP_MODE_THREAD, T_BINTREE, PS_BINTREE},
+    {"bintree_block", GTAP_MODE_BLOCK, T_BINTREE_BLK, PS_BINTREE_BLK},
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -79,6 +81,8 @@ struct gtap_ctx {
     unsigned long long* flog = nullptr;
     unsigned* flogn = nullptr;
     uint64_t max_frames = 0;
+    unsigned long long* gq = nullptr;   // central-queue scheduler slots
+    uint64_t gq_cap = 0;
 
     RootDesc* root_desc_pinned = nullptr;
     int* host_abort = nullptr;       // pinned, mapped
@@ -171,14 +175,99 @@ static gtap_status free_all(gtap_ctx* c) {
     return GTAP_OK;
 }
 
-gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, const gtap_config* cfg_in, gtap_ctx** out) {
-    if (!out) return GTAP_ERR_INVALID_ARG;
-    *out = nullptr;
+// Launch geometry and arena layout of a context (shared by gtap_init and gtap_arena_bytes).
+struct ArenaLayout {
+    int threads_per_block = 256, blocks_per_sm = 4, grid = 0;
+    uint32_t ring_cap = 0, n_workers_max = 0;
+    uint64_t ncq = 0, max_frames = 0;
+    size_t o_frames = 0, o_rings = 0, o_qs = 0, o_cqs = 0, o_cqi = 0, o_ctl = 0, o_roots = 0, o_desc = 0,
+           o_stats = 0, o_scratch = 0, o_fstate = 0, o_flog = 0, o_flogn = 0, o_gq = 0, total = 0;
+    uint64_t gq_cap = 0;
+};
+
+// Validates the arguments, fills the defaults of cfg in place and computes the layout.
+static gtap_status plan_arena(gtap_mode mode, int n_queues, size_t frame_pool_bytes, gtap_config& cfg, int sm_count,
+                              ArenaLayout* L) {
     if (mode != GTAP_MODE_THREAD && mode != GTAP_MODE_BLOCK) return GTAP_ERR_INVALID_ARG;
     if (n_queues < 1 || n_queues > kMaxQueues) return GTAP_ERR_INVALID_ARG;
     if (mode == GTAP_MODE_BLOCK && n_queues != 1) return GTAP_ERR_INVALID_ARG;
     if (frame_pool_bytes < 64 * 1024) return GTAP_ERR_INVALID_ARG;
+    if (mode == GTAP_MODE_THREAD) {
+        L->threads_per_block = cfg.threads_per_block ? cfg.threads_per_block : 256;
+        if (L->threads_per_block < 32 || L->threads_per_block > 256 || L->threads_per_block % 32) return GTAP_ERR_INVALID_ARG;
+        L->blocks_per_sm = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
+        L->ring_cap = cfg.deque_capacity ? (uint32_t)cfg.deque_capacity : 4096u;
+    } else {
+        L->threads_per_block = cfg.threads_per_block ? cfg.threads_per_block : 256;
+        // 32 (one warp per block) is instantiated for the binary-tree microbenchmark only
+        if (L->threads_per_block != 32 && L->threads_per_block != 128 && L->threads_per_block != 256)
+            return GTAP_ERR_INVALID_ARG;
+        L->blocks_per_sm = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
+        L->ring_cap = cfg.deque_capacity ? (uint32_t)cfg.deque_capacity : 1024u;
+    }
+    if (L->blocks_per_sm < 1 || L->blocks_per_sm > 32) return GTAP_ERR_INVALID_ARG;
+    if (L->ring_cap < 32 || next_pow2(L->ring_cap) != L->ring_cap || L->ring_cap > (1u << 24)) return GTAP_ERR_INVALID_ARG;
+    if (cfg.frame_bytes != 0 && cfg.frame_bytes != 64 && cfg.frame_bytes != 128) return GTAP_ERR_INVALID_ARG;
+    if (!cfg.max_roots) cfg.max_roots = 4096;
+    if (cfg.max_roots < 1 || cfg.max_roots > (1 << 24)) return GTAP_ERR_INVALID_ARG;
+    if (!cfg.timeout_ns) cfg.timeout_ns = 60ull * 1000000000ull;
+    if (!cfg.seed) cfg.seed = 0x5EEDull;
+    if (cfg.grid_blocks < 0) return GTAP_ERR_INVALID_ARG;
+    if (cfg.scheduler < 0 || cfg.scheduler > 2) return GTAP_ERR_INVALID_ARG;
+    // the scheduler comparison variants are thread-mode designs with one queue per warp
+    if (cfg.scheduler != 0 && (mode != GTAP_MODE_THREAD || n_queues != 1)) return GTAP_ERR_INVALID_ARG;
+    L->grid = L->blocks_per_sm * sm_count;
+    if (cfg.grid_blocks > 0) L->grid = std::min(cfg.grid_blocks, L->grid);
+    L->n_workers_max = (mode == GTAP_MODE_THREAD) ? (uint32_t)(L->grid * (L->threads_per_block / 32)) : (uint32_t)L->grid;
 
+    // storage layout (256-byte aligned pieces of one arena)
+    const uint64_t max_frames = frame_pool_bytes / 64;
+    L->max_frames = max_frames;
+    L->ncq = next_pow2((uint32_t)std::min<uint64_t>((max_frames + kChunk - 1) / kChunk + 1, 1ull << 31));
+    const size_t qn = (size_t)L->n_workers_max * n_queues;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L->o_frames = take(frame_pool_bytes);
+    L->o_rings = take(qn * L->ring_cap * sizeof(uint32_t));
+    L->o_qs = take(qn * sizeof(QState));
+    L->o_cqs = take(L->ncq * sizeof(unsigned long long));
+    L->o_cqi = take(L->ncq * kChunk * sizeof(uint32_t));
+    L->o_ctl = take(sizeof(DevControl));
+    L->o_roots = take((size_t)cfg.max_roots * sizeof(RootEntry));
+    L->o_desc = take((size_t)cfg.max_roots * sizeof(RootDesc));
+    L->o_stats = take((size_t)L->n_workers_max * sizeof(WorkerStats));
+    L->o_scratch = take(cfg.scratch_bytes);
+    L->o_fstate = take(cfg.debug_checks ? (size_t)max_frames * sizeof(unsigned) : 0);
+    L->o_flog = take(cfg.debug_checks > 1 ? (size_t)max_frames * 8 * sizeof(unsigned long long) : 0);
+    L->o_flogn = take(cfg.debug_checks > 1 ? (size_t)max_frames * sizeof(unsigned) : 0);
+    // central queue: one slot per record, so it never fills
+    L->gq_cap = cfg.scheduler == GTAP_SCHED_GLOBAL ? next_pow2((uint32_t)std::min<uint64_t>(max_frames, 1ull << 31)) : 0;
+    L->o_gq = take(L->gq_cap * sizeof(unsigned long long));
+    L->total = off;
+    return GTAP_OK;
+}
+
+gtap_status gtap_arena_bytes(gtap_mode mode, int n_queues, size_t frame_pool_bytes, const gtap_config* cfg_in,
+                             size_t* out) {
+    if (!out) return GTAP_ERR_INVALID_ARG;
+    *out = 0;
+    gtap_config cfg{};
+    if (cfg_in) cfg = *cfg_in;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GTAP_ERR_CUDA;
+    }
+    ArenaLayout L;
+    gtap_status st = plan_arena(mode, n_queues, frame_pool_bytes, cfg, sms, &L);
+    if (st != GTAP_OK) return st;
+    *out = L.total;
+    return GTAP_OK;
+}
+
+gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, const gtap_config* cfg_in, gtap_ctx** out) {
+    if (!out) return GTAP_ERR_INVALID_ARG;
+    *out = nullptr;
     gtap_ctx* c = new gtap_ctx();
     c->mode = mode;
     c->n_queues = n_queues;
@@ -187,53 +276,27 @@ gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, con
     gtap_config& cfg = c->cfg;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
         delete c;
         return GTAP_ERR_CUDA;
     }
-    if (mode == GTAP_MODE_THREAD) {
-        c->threads_per_block = cfg.threads_per_block ? cfg.threads_per_block : 256;
-        if (c->threads_per_block < 32 || c->threads_per_block > 256 || c->threads_per_block % 32) { delete c; return GTAP_ERR_INVALID_ARG; }
-        c->blocks_per_sm = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
-        c->ring_cap = cfg.deque_capacity ? (uint32_t)cfg.deque_capacity : 4096u;
-    } else {
-        c->threads_per_block = cfg.threads_per_block ? cfg.threads_per_block : 256;
-        if (c->threads_per_block != 128 && c->threads_per_block != 256) { delete c; return GTAP_ERR_INVALID_ARG; }
-        c->blocks_per_sm = cfg.blocks_per_sm ? cfg.blocks_per_sm : 4;
-        c->ring_cap = cfg.deque_capacity ? (uint32_t)cfg.deque_capacity : 1024u;
+    ArenaLayout L;
+    {
+        gtap_status st = plan_arena(mode, n_queues, frame_pool_bytes, cfg, c->sm_count, &L);
+        if (st != GTAP_OK) { delete c; return st; }
     }
-    if (c->blocks_per_sm < 1 || c->blocks_per_sm > 32) { delete c; return GTAP_ERR_INVALID_ARG; }
-    if (c->ring_cap < 32 || next_pow2(c->ring_cap) != c->ring_cap || c->ring_cap > (1u << 24)) { delete c; return GTAP_ERR_INVALID_ARG; }
-    if (cfg.frame_bytes != 0 && cfg.frame_bytes != 64 && cfg.frame_bytes != 128) { delete c; return GTAP_ERR_INVALID_ARG; }
-    if (!cfg.max_roots) cfg.max_roots = 4096;
-    if (cfg.max_roots < 1 || cfg.max_roots > (1 << 24)) { delete c; return GTAP_ERR_INVALID_ARG; }
-    if (!cfg.timeout_ns) cfg.timeout_ns = 60ull * 1000000000ull;
-    if (!cfg.seed) cfg.seed = 0x5EEDull;
+    c->threads_per_block = L.threads_per_block;
+    c->blocks_per_sm = L.blocks_per_sm;
+    c->ring_cap = L.ring_cap;
     c->stream = reinterpret_cast<cudaStream_t>(cfg.stream);
-    c->grid = c->blocks_per_sm * c->sm_count;
-    if (cfg.grid_blocks < 0) { delete c; return GTAP_ERR_INVALID_ARG; }
-    if (cfg.grid_blocks > 0) c->grid = std::min(cfg.grid_blocks, c->grid);
-    c->n_workers_max = (mode == GTAP_MODE_THREAD) ? (uint32_t)(c->grid * (c->threads_per_block / 32)) : (uint32_t)c->grid;
-
-    // storage layout (256-byte aligned pieces of one arena)
-    const uint64_t max_frames = frame_pool_bytes / 64;
-    c->ncq = next_pow2((uint32_t)std::min<uint64_t>((max_frames + kChunk - 1) / kChunk + 1, 1ull << 31));
-    const size_t qn = (size_t)c->n_workers_max * n_queues;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    const size_t o_frames = take(frame_pool_bytes);
-    const size_t o_rings = take(qn * c->ring_cap * sizeof(uint32_t));
-    const size_t o_qs = take(qn * sizeof(QState));
-    const size_t o_cqs = take(c->ncq * sizeof(unsigned long long));
-    const size_t o_cqi = take(c->ncq * kChunk * sizeof(uint32_t));
-    const size_t o_ctl = take(sizeof(DevControl));
-    const size_t o_roots = take((size_t)cfg.max_roots * sizeof(RootEntry));
-    const size_t o_desc = take((size_t)cfg.max_roots * sizeof(RootDesc));
-    const size_t o_stats = take((size_t)c->n_workers_max * sizeof(WorkerStats));
-    const size_t o_scratch = take(cfg.scratch_bytes);
-    const size_t o_fstate = take(cfg.debug_checks ? (size_t)max_frames * sizeof(unsigned) : 0);
-    const size_t o_flog = take(cfg.debug_checks > 1 ? (size_t)max_frames * 8 * sizeof(unsigned long long) : 0);
-    const size_t o_flogn = take(cfg.debug_checks > 1 ? (size_t)max_frames * sizeof(unsigned) : 0);
-    const size_t total = off;
+    c->grid = L.grid;
+    c->n_workers_max = L.n_workers_max;
+    c->ncq = L.ncq;
+    const uint64_t max_frames = L.max_frames;
+    const size_t o_frames = L.o_frames, o_rings = L.o_rings, o_qs = L.o_qs, o_cqs = L.o_cqs, o_cqi = L.o_cqi,
+                 o_ctl = L.o_ctl, o_roots = L.o_roots, o_desc = L.o_desc, o_stats = L.o_stats,
+                 o_scratch = L.o_scratch, o_fstate = L.o_fstate, o_flog = L.o_flog, o_flogn = L.o_flogn;
+    const size_t total = L.total;
 
     if (cfg.device_arena) {
         if (cfg.arena_bytes < total || (reinterpret_cast<uintptr_t>(cfg.device_arena) & 255u)) { delete c; return GTAP_ERR_NO_MEMORY; }
@@ -271,6 +334,8 @@ gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, con
     c->flog = cfg.debug_checks > 1 ? reinterpret_cast<unsigned long long*>(c->arena + o_flog) : nullptr;
     c->flogn = cfg.debug_checks > 1 ? reinterpret_cast<unsigned*>(c->arena + o_flogn) : nullptr;
     c->max_frames = max_frames;
+    c->gq_cap = L.gq_cap;
+    c->gq = L.gq_cap ? reinterpret_cast<unsigned long long*>(c->arena + L.o_gq) : nullptr;
 
     bool ok = cudaHostAlloc(reinterpret_cast<void**>(&c->root_desc_pinned), (size_t)cfg.max_roots * sizeof(RootDesc), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(reinterpret_cast<void**>(&c->host_abort), 128, cudaHostAllocMapped) == cudaSuccess &&
@@ -371,6 +436,20 @@ static gtap_status make_root(gtap_ctx* c, int type, const void* args, size_t nby
         std::memcpy(d->env, &a, sizeof(a));
         return GTAP_OK;
     }
+    case T_BINTREE:
+    case T_BINTREE_BLK: {
+        if (nbytes != sizeof(gtap_bintree_args)) return GTAP_ERR_INVALID_ARG;
+        gtap_bintree_args a;
+        std::memcpy(&a, args, sizeof(a));
+        if (a.depth < 0 || a.depth > 30 || a.iters < 0 || a.K < 1 || a.K > 4 || a.cutoff < 0 || a.cutoff > 20 ||
+            (type == T_BINTREE && a.cutoff != 0))
+            return GTAP_ERR_INVALID_ARG;
+        struct { unsigned long long id; uint32_t level, depth, iters, kr; unsigned long long acc; } p{
+            1ull, 0u, (uint32_t)a.depth, (uint32_t)a.iters,
+            (uint32_t)a.K | ((a.route ? 1u : 0u) << 8) | ((uint32_t)a.cutoff << 16), 0ull};
+        put(&p, sizeof(p));
+        return GTAP_OK;
+    }
     case T_INTEGRATE_BLK: {
         if (nbytes != sizeof(gtap_integrate_args)) return GTAP_ERR_INVALID_ARG;
         gtap_integrate_args a;
@@ -432,6 +511,14 @@ gtap_status gtap_clear_roots(gtap_ctx* c) {
     c->pending_roots.clear();
     c->have_results = false;
     drop_graph(c);
+    return GTAP_OK;
+}
+
+gtap_status gtap_set_timeout(gtap_ctx* c, uint64_t timeout_ns) {
+    if (!c) return GTAP_ERR_INVALID_ARG;
+    if (c->running) return GTAP_ERR_BUSY;
+    c->cfg.timeout_ns = timeout_ns ? timeout_ns : 60ull * 1000000000ull;
+    drop_graph(c);   // a captured run carries the old deadline
     return GTAP_OK;
 }
 
@@ -527,7 +614,11 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
         frame_bytes = c->cfg.frame_bytes ? (uint32_t)c->cfg.frame_bytes : thread_record_bytes(pset);
         smem = (size_t)(c->threads_per_block / 32) * thread_warp_smem(maxspawn);
         int occ = 0;
-        if (thread_kernel_occupancy(pset, c->threads_per_block, smem, &occ) != cudaSuccess) return GTAP_ERR_CUDA;
+        {
+            const cudaError_t oe = thread_kernel_occupancy(pset, c->cfg.scheduler, c->threads_per_block, smem, &occ);
+            if (oe == cudaErrorInvalidValue) { cudaGetLastError(); return GTAP_ERR_INVALID_ARG; }   // no such instantiation
+            if (oe != cudaSuccess) return GTAP_ERR_CUDA;
+        }
         if (occ < 1) return GTAP_ERR_INVALID_ARG;
         grid = std::min(c->grid, occ * c->sm_count);
         P.n_workers = (uint32_t)(grid * (c->threads_per_block / 32));
@@ -537,7 +628,11 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
         frame_bytes = block_record_bytes(pset, c->threads_per_block);
         smem = (size_t)block_rt_smem(maxspawn) + block_prog_smem(pset, c->threads_per_block);
         int occ = 0;
-        if (block_kernel_occupancy(pset, c->threads_per_block, smem, &occ) != cudaSuccess) return GTAP_ERR_CUDA;
+        {
+            const cudaError_t oe = block_kernel_occupancy(pset, c->threads_per_block, smem, &occ);
+            if (oe == cudaErrorInvalidValue) { cudaGetLastError(); return GTAP_ERR_INVALID_ARG; }   // no such instantiation
+            if (oe != cudaSuccess) return GTAP_ERR_CUDA;
+        }
         if (occ < 1) return GTAP_ERR_INVALID_ARG;
         grid = std::min(c->grid, occ * c->sm_count);
         P.n_workers = (uint32_t)grid;
@@ -575,6 +670,8 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
     P.fstate = c->fstate;
     P.flog = c->flog;
     P.flogn = c->flogn;
+    P.gq = c->gq;
+    P.gq_mask = c->gq_cap ? c->gq_cap - 1 : 0;
     if (c->flogn) cudaMemsetAsync(c->flogn, 0, c->max_frames * sizeof(unsigned), c->stream);
 
     *c->host_abort = 0;
@@ -599,7 +696,7 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
     }
     record(c->ev_k0);
     cudaError_t e = (c->mode == GTAP_MODE_THREAD)
-                        ? launch_thread_kernel(pset, P, grid, c->threads_per_block, smem, s)
+                        ? launch_thread_kernel(pset, c->cfg.scheduler, P, grid, c->threads_per_block, smem, s)
                         : launch_block_kernel(pset, c->threads_per_block, P, grid, smem, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -760,6 +857,14 @@ gtap_status gtap_poll(gtap_ctx* c, gtap_completion* out, int max, int* n) {
     hf->out_consumed = oc;
     *n = k;
     return (gtap_status)hf->dev_error;
+}
+
+gtap_status gtap_serve_progress(gtap_ctx* c, uint64_t* out, int n) {
+    if (!c || !out || n < 0 || !c->hflags) return GTAP_ERR_INVALID_ARG;
+    volatile HostFlags* hf = c->hflags;
+    const uint64_t v[3] = {c->submitted, hf->inbox_consumed, hf->out_consumed};
+    for (int i = 0; i < n && i < 3; ++i) out[i] = v[i];
+    return GTAP_OK;
 }
 
 gtap_status gtap_serve_stop(gtap_ctx* c, uint64_t timeout_ms) {

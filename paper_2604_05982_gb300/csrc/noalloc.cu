@@ -1,13 +1,15 @@
 // Allocation-free block-mode mergesort: gtap_mergesort_noalloc.
 //
-// Some callers cannot call cudaMalloc: code running while another framework
-// captures a CUDA graph (an allocation would break the capture), real-time
-// paths whose memory budget is fixed up front, or plugins handed a stream by a
-// host application that owns all device memory.  For them this entry point
-// keeps every byte of working memory the sort needs -- the ping-pong key
-// buffer, the task-record pool, the deques, the pool's chunk queue and the
-// control block -- in one file-scope __device__ array of fixed size, so the
-// call allocates nothing.  The caller passes only the input and output.
+// Some callers cannot call cudaMalloc: a plugin or library loaded into a host
+// application that owns every byte of device memory and hands the plugin only
+// a stream and the buffers to work on, a real-time path whose memory budget is
+// fixed before it starts, or code running under an allocator that must not be
+// re-entered.  For them this entry point keeps every byte of working memory
+// the sort needs -- the ping-pong key buffer, the task-record pool, the deques,
+// the pool's chunk queue and the control block -- in one file-scope __device__
+// array of fixed size, so the call allocates nothing.  The caller passes only
+// the input and output.  The call waits for its own stream before returning
+// (it reads the device-side status back).
 //
 // Limits and sharing: at most kNoallocMaxKeys keys per call.  Every GPU that
 // loads the library holds the array until the process exits.  All calls share

@@ -19,6 +19,9 @@ GTAP_STEAL_FILL = 0
 GTAP_STEAL_EMPTY = 1
 GTAP_STEAL_HALF = 2
 GTAP_STEAL_ONE = 4
+GTAP_SCHED_BATCHED = 0
+GTAP_SCHED_GLOBAL = 1
+GTAP_SCHED_SINGLE = 2
 
 STATUS = {
     0: "GTAP_OK", 1: "GTAP_ERR_INVALID_ARG", 2: "GTAP_ERR_NO_MEMORY", 3: "GTAP_ERR_POOL_EXHAUSTED",
@@ -39,7 +42,8 @@ class gtap_config(ctypes.Structure):
                 ("deque_capacity", ctypes.c_int), ("steal_policy", ctypes.c_int), ("max_roots", ctypes.c_int),
                 ("frame_bytes", ctypes.c_int), ("device_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
                 ("stream", ctypes.c_void_p), ("timeout_ns", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("scratch_bytes", ctypes.c_size_t), ("grid_blocks", ctypes.c_int), ("debug_checks", ctypes.c_int)]
+                ("scratch_bytes", ctypes.c_size_t), ("grid_blocks", ctypes.c_int), ("debug_checks", ctypes.c_int),
+                ("scheduler", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class gtap_stats(ctypes.Structure):
@@ -80,6 +84,11 @@ class gtap_kclique_args(ctypes.Structure):
     _fields_ = [("off", ctypes.c_void_p), ("adj", ctypes.c_void_p), ("src", ctypes.c_void_p),
                 ("edge_begin", ctypes.c_int64), ("edge_end", ctypes.c_int64), ("k", ctypes.c_int32),
                 ("split_threshold", ctypes.c_int32), ("route", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class gtap_bintree_args(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("iters", ctypes.c_int32), ("K", ctypes.c_int32), ("route", ctypes.c_int32),
+                ("cutoff", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class gtap_mergesort_args(ctypes.Structure):
@@ -138,6 +147,9 @@ _SIGS = {
     "gtap_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gtap_stats)]),
     "gtap_last_error": (ctypes.c_int, [_P, ctypes.POINTER(gtap_error_info)]),
     "gtap_clear_roots": (ctypes.c_int, [_P]),
+    "gtap_set_timeout": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "gtap_arena_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(gtap_config),
+                                        ctypes.POINTER(ctypes.c_size_t)]),
     "gtap_capture_graph": (ctypes.c_int, [_P]),
     "gtap_serve_start": (ctypes.c_int, [_P]),
     "gtap_microbench": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -145,6 +157,7 @@ _SIGS = {
     "gtap_submit": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "gtap_poll": (ctypes.c_int, [_P, ctypes.POINTER(gtap_completion), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gtap_serve_stop": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "gtap_serve_progress": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     "gtap_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gtap_finalize": (ctypes.c_int, [_P]),
     "gtap_debug_snapshot": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
@@ -249,6 +262,19 @@ def gtap_clear_roots(ctx: int) -> None:
     _check(load_library().gtap_clear_roots(ctx), "gtap_clear_roots")
 
 
+def gtap_set_timeout(ctx: int, timeout_ns: int) -> None:
+    """Device-side deadline of later runs (0: the default of 60 s)."""
+    _check(load_library().gtap_set_timeout(ctx, timeout_ns), "gtap_set_timeout")
+
+
+def gtap_arena_bytes(mode: int, n_queues: int, frame_pool_bytes: int, cfg: gtap_config | None = None) -> int:
+    """Device bytes gtap_init needs for these arguments (the size of a caller-owned arena)."""
+    out = ctypes.c_size_t(0)
+    _check(load_library().gtap_arena_bytes(mode, n_queues, frame_pool_bytes, ctypes.byref(cfg) if cfg else None,
+                                           ctypes.byref(out)), "gtap_arena_bytes")
+    return out.value
+
+
 def gtap_capture_graph(ctx: int) -> None:
     _check(load_library().gtap_capture_graph(ctx), "gtap_capture_graph")
 
@@ -301,6 +327,13 @@ def gtap_poll(ctx: int, max_n: int = 4096):
     max_n = min(max_n, len(_poll_buf))
     _check(load_library().gtap_poll(ctx, _poll_buf, max_n, ctypes.byref(n)), "gtap_poll")
     return [(c.req, c.result[0], c.result[1], c.status) for c in _poll_buf[: n.value]]
+
+
+def gtap_serve_progress(ctx: int):
+    """(submitted, admitted by the device, completions polled)."""
+    buf = (ctypes.c_uint64 * 3)()
+    _check(load_library().gtap_serve_progress(ctx, buf, 3), "gtap_serve_progress")
+    return tuple(int(x) for x in buf)
 
 
 def gtap_serve_stop(ctx: int, timeout_ms: int = 0) -> int:

@@ -43,9 +43,27 @@ def test_library_loads_and_binding_matches(lib_path):
     assert G.gtap_status_string(3) == "task-record pool exhausted"
 
 
-def test_struct_layouts_match_header(lib_path):
+def test_struct_layouts_match_header(lib_path, tmp_path):
     from paper_2604_05982_gb300 import gtap as G
-    assert ctypes.sizeof(G.gtap_config) == 6 * 4 + 8 * 6 + 8
+    # sizes and field offsets as the C compiler lays out include/gtap.h
+    structs = {"gtap_config": G.gtap_config, "gtap_stats": G.gtap_stats, "gtap_error_info": G.gtap_error_info,
+               "gtap_kclique_args": G.gtap_kclique_args, "gtap_uts_args": G.gtap_uts_args,
+               "gtap_mergesort_args": G.gtap_mergesort_args}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gtap.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
     assert ctypes.sizeof(G.gtap_fib_args) == 8
     assert ctypes.sizeof(G.gtap_uts_args) == 32
     assert ctypes.sizeof(G.gtap_mergesort_args) == 40
