@@ -67,6 +67,8 @@ def _load():
                 "orc_fmm_tree": (i64, [i64, P, i32, P, i64, P]),
                 "orc_direct": (None, [i64, P, P, P, i64, P]),
                 "orc_taylor": (i32, [i32, f64, f64, f64, P]),
+                "orc_bintree": (u64, [i32, i32, i32, i32, P]),
+                "orc_bintree_leaf": (u64, [u64, i32, i32]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -116,6 +118,18 @@ def uts(seed: int = 42, root_children: int = 2000, m: int = 5, threshold: int = 
     else:
         _load().orc_uts_bfs(seed, root_children, m, threshold, ctypes.byref(n), ctypes.byref(l))
     return int(n.value), int(l.value)
+
+
+def bintree(depth: int, iters: int, K: int = 1, cutoff: int = 0):
+    """(sum of leaf values mod 2^64, tasks) of the full binary task tree (Sec. 6.1, 6.2)."""
+    t = ctypes.c_uint64(0)
+    v = _load().orc_bintree(depth, iters, K, cutoff, ctypes.byref(t))
+    return int(v), int(t.value)
+
+
+def bintree_leaf(v: int, iters: int, K: int = 1) -> int:
+    """Value of leaf v of the binary task tree."""
+    return int(_load().orc_bintree_leaf(v, iters, K))
 
 
 def sort_u32(keys: np.ndarray) -> np.ndarray:

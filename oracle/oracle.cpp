@@ -18,7 +18,7 @@
 // multiply-add, so floating-point programs round at every operation).
 //
 // Parity status per routine (see tests/test_oracle_pins.py):
-//   fib, nqueens, uts, sort, integrate, kclique: pinned.
+//   fib, nqueens, uts, sort, integrate, kclique, bintree: pinned.
 //   fmm: pinned against the direct O(N^2) sum (exact regime and convergence).
 
 #include <algorithm>
@@ -401,5 +401,75 @@ uint64_t orc_kclique_brute(int n, const int32_t* edges, int64_t m, int k) {
     }
     return count;
 }
+
+// ---------------------------------------------------------------------------
+// Full binary task tree microbenchmark (Sec. 6.1, Sec. 6.2).  Node v has the
+// children 2v and 2v+1; the leaves are the nodes of level D.  A leaf's
+// function index is the high half of splitmix64(v) reduced mod K, and its value
+// is the sum, mod 2^64, of its function over the inputs (v << 32) + i for
+// i = 0 .. iters-1.  The four functions, as the program definition states them:
+//   f0: multiply by 0x9E3779B97F4A7C15, xor the value shifted right 29, multiply
+//       by 0xBF58476D1CE4E5B9, xor the value shifted right 32;
+//   f1: xor x shifted left 13, then xor shifted right 7, then xor shifted left 17,
+//       multiply by 0x2545F4914F6CDD1D;
+//   f2: add 0x632BE59BD9B4E019, multiply by 0x94D049BB133111EB, rotate left 23
+//       and xor with the value shifted right 11;
+//   f3: xor x with x shifted right 32, multiply by 0xD6E8FEB86659FD93, xor the
+//       value shifted right 28.
+// The serial elision sums the two subtrees; a block-mode cutoff c only changes
+// how many tasks are created (a node c levels above the leaves is one task).
+static uint64_t bt_fn(int k, uint64_t x) {
+    uint64_t z;
+    if (k == 0) {
+        z = x * 0x9E3779B97F4A7C15ULL;
+        z = z ^ (z >> 29);
+        z = z * 0xBF58476D1CE4E5B9ULL;
+        return z ^ (z >> 32);
+    }
+    if (k == 1) {
+        z = x ^ (x << 13);
+        z = z ^ (z >> 7);
+        z = z ^ (z << 17);
+        return z * 0x2545F4914F6CDD1DULL;
+    }
+    if (k == 2) {
+        z = (x + 0x632BE59BD9B4E019ULL) * 0x94D049BB133111EBULL;
+        uint64_t rotated = (z << 23) | (z >> 41);
+        return rotated ^ (z >> 11);
+    }
+    z = x ^ (x >> 32);
+    z = z * 0xD6E8FEB86659FD93ULL;
+    return z ^ (z >> 28);
+}
+
+static uint64_t bt_leaf(uint64_t v, int iters, int K) {
+    int k = 0;
+    if (K > 1) k = (int)((splitmix64(v) >> 32) % (uint64_t)K);
+    uint64_t sum = 0;
+    for (int i = 0; i < iters; ++i) sum += bt_fn(k, (v << 32) + (uint64_t)i);
+    return sum;
+}
+
+static uint64_t bt_rec(uint64_t v, int level, int D, int iters, int K, int cutoff, uint64_t* tasks) {
+    // a block-mode task that runs its whole subtree counts once
+    bool whole = level == D || (cutoff > 0 && D - level <= cutoff);
+    *tasks += 1;
+    if (whole) {
+        uint64_t s = 0;
+        uint64_t first = v << (D - level), n = 1ULL << (D - level);
+        for (uint64_t j = 0; j < n; ++j) s += bt_leaf(first + j, iters, K);
+        return s;
+    }
+    return bt_rec(2 * v, level + 1, D, iters, K, cutoff, tasks) + bt_rec(2 * v + 1, level + 1, D, iters, K, cutoff, tasks);
+}
+
+uint64_t orc_bintree(int depth, int iters, int K, int cutoff, uint64_t* tasks) {
+    uint64_t t = 0;
+    uint64_t r = bt_rec(1, 0, depth, iters, K, cutoff, &t);
+    if (tasks) *tasks = t;
+    return r;
+}
+
+uint64_t orc_bintree_leaf(uint64_t v, int iters, int K) { return bt_leaf(v, iters, K); }
 
 }  // extern "C"

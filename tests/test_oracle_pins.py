@@ -140,6 +140,40 @@ def test_uts_branching_frequency():
 
 
 # --------------------------------------------------------------------------- sort
+def test_bintree_task_counts_closed_form():
+    # thread mode: every node of the full tree is a task; block mode with cutoff c:
+    # the nodes of levels 0 .. D - c (a node c levels above the leaves is one task)
+    for d in range(0, 11):
+        assert oracle.bintree(d, 1)[1] == 2 ** (d + 1) - 1
+        for c in (1, 3, 5):
+            assert oracle.bintree(d, 1, cutoff=c)[1] == (2 ** (d - c + 1) - 1 if c < d else 1)
+
+
+def test_bintree_recursion_equals_flat_leaf_enumeration():
+    # the recursion's result is the sum over the leaf ids 2^D .. 2^(D+1)-1 of their
+    # values (mod 2^64), whatever the cutoff
+    for d, iters, k in [(0, 5, 1), (4, 3, 2), (7, 2, 4), (9, 1, 3)]:
+        flat = sum(oracle.bintree_leaf(v, iters, k) for v in range(2 ** d, 2 ** (d + 1))) % 2 ** 64
+        for c in (0, 2, 5):
+            assert oracle.bintree(d, iters, k, cutoff=c)[0] == flat
+
+
+def test_bintree_leaf_special_cases():
+    # no iterations: every leaf is 0; the loop value is additive in the iteration range
+    assert oracle.bintree(6, 0, 4)[0] == 0
+    # K = 1 runs function 0 everywhere; a K = 4 leaf whose selected function is 0 has
+    # the K = 1 value, and a leaf's value over n + 1 iterations adds one term to n
+    sel = {}
+    for v in range(64, 128):
+        k4 = (oracle.splitmix64(v) >> 32) % 4
+        sel[v] = k4
+        if k4 == 0:
+            assert oracle.bintree_leaf(v, 7, 4) == oracle.bintree_leaf(v, 7, 1)
+    assert set(sel.values()) == {0, 1, 2, 3}
+    # f0(0) = f1(0) = f3(0) = 0: leaf 0 with one iteration (input 0 << 32 = 0)
+    assert oracle.bintree_leaf(0, 1, 1) == 0
+
+
 def test_sort_is_sorted_permutation():
     keys = inputs.keys_u32(1 << 16, seed=1)
     out = oracle.sort_u32(keys)
