@@ -645,7 +645,7 @@ static __device__ void serve_poller(const KParams& P, const WarpSh& ws, int* fto
 // work at start-up (fib and N-Queens lost 15-25 % at 4 us).
 constexpr int kIdleBackoffMaxNs = 512;
 
-template <class Dispatch>
+template <class Dispatch, int SCHED = SCHED_BATCHED>
 __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
     const int lane = threadIdx.x & 31;
     const int wid = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
@@ -700,55 +700,133 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             if (lane == 0) ab = abort_requested(P, (iter & 1023u) == 0u) ? 1 : 0;
             if (__shfl_sync(0xffffffffu, ab, 0)) break;
         }
-        // ---- PopBatch (Algorithm 2) from the own queue: the retained class, else the fullest (DAQ).
-        // The owner keeps an upper bound of each count (thieves only lower it), so an empty
-        // queue costs no memory access and the CAS starts from a good guess.
-        if (cnt < 32) {
-            int q = cls;
-            if (cnt == 0 && Q > 1) {
-                int best = (lane < Q) ? ws.hint[lane] : -1, bq = lane;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    int oc = __shfl_down_sync(0xffffffffu, best, o);
-                    int oq = __shfl_down_sync(0xffffffffu, bq, o);
-                    if (oc > best || (oc == best && oq < bq)) { best = oc; bq = oq; }
+        if constexpr (SCHED == SCHED_GLOBAL) {
+            // ---- Central queue (Sec. 6.5 comparison): the warp claims up to 32 - cnt tasks
+            // from the one queue every warp shares (reserve from the published count, then
+            // take dequeue tickets; each lane waits for its slot's publication).
+            if (cnt < 32) {
+                const int want = 32 - cnt;
+                int got = 0;
+                unsigned long long d0 = 0;
+                if (lane == 0 && (long long)ld_cg64(&P.ctl->gq_avail.v) > 0) {
+                    const long long av = (long long)atomicAdd(&P.ctl->gq_avail.v, (unsigned long long)(-(long long)want));
+                    got = (int)max(0ll, min((long long)want, av));
+                    if (got < want) atomicAdd(&P.ctl->gq_avail.v, (unsigned long long)(want - got));
+                    if (got > 0) d0 = atomicAdd(&P.ctl->gq_deq.v, (unsigned long long)got);
                 }
-                q = __shfl_sync(0xffffffffu, bq, 0);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                d0 = __shfl_sync(0xffffffffu, d0, 0);
+                if (got > 0) {
+                    int bad = 0;
+                    if (lane >= cnt && lane < cnt + got) {
+                        const unsigned long long tk = d0 + (unsigned long long)(lane - cnt);
+                        unsigned long long* slot = &P.gq[tk & P.gq_mask];
+                        bad = 1;
+                        for (int it = 0; it < (1 << 20); ++it) {
+                            const unsigned long long w = ld_acquire_u64(slot);
+                            if ((uint32_t)(w >> 32) == (uint32_t)(tk + 1)) {
+                                tid = (uint32_t)w;
+                                st_release_u64(slot, (unsigned long long)(uint32_t)(tk + P.gq_mask + 1) << 32);
+                                bad = 0;
+                                break;
+                            }
+                            __nanosleep(32);
+                        }
+                        if (bad) raise_error(P, GTAP_ERR_TASK_FAILED, -1, wid, tk);
+                        src = 1;
+                    }
+                    if (__any_sync(0xffffffffu, bad)) break;
+                    cnt += got;
+                    cls = 0;
+                    ++st_pops;
+                    st_popped += got;
+                }
             }
-            if (ws.hint[q] > 0) {
+        } else if constexpr (SCHED == SCHED_SINGLE) {
+            // ---- Non-batched pop (Sec. 6.5 comparison): single-task claims, one CAS each,
+            // issued one after another by lane 0 until the batch is full or the queue is empty.
+            const int q = 0;
+            if (cnt < 32 && ws.hint[q] > 0) {
                 int claim = 0;
                 if (lane == 0) {
                     int old = ws.hint[q];
-                    for (int it = 0; it < 64 && old > 0; ++it) {
-                        const int want = min(32 - cnt, old);
-                        const int got = atom_cas_acq_i32(&myq[q].count, old, old - want);
-                        if (got == old) { claim = want; old -= want; break; }
-                        old = got;
+                    for (int k = 0; k < 32 - cnt && old > 0; ++k) {
+                        bool ok = false;
+                        for (int it = 0; it < 64 && old > 0; ++it) {
+                            const int got = atom_cas_acq_i32(&myq[q].count, old, old - 1);
+                            if (got == old) { ok = true; old -= 1; break; }
+                            old = got;
+                        }
+                        if (!ok) break;
+                        const uint32_t t = ws.tail[q] - 1u;
+                        ws.tail[q] = t;
+                        ws.retained[cnt + claim] = __ldcg(&myring[t & cap_mask]);
+                        ++claim;
                     }
                     ws.hint[q] = max(old, 0);
                 }
                 claim = __shfl_sync(0xffffffffu, claim, 0);
+                __syncwarp();
                 if (claim > 0) {
-                    uint32_t t = ws.tail[q] - (uint32_t)claim;
-                    if (lane >= cnt && lane < cnt + claim) {
-                        uint32_t* slot = &myring[(size_t)q * (cap_mask + 1) + ((t + (uint32_t)(lane - cnt)) & cap_mask)];
-                        tid = __ldcg(slot);
-                        src = 1;
-                        dbg_log(P, tid, 7, wid, iter, (t + (uint32_t)(lane - cnt)) & 0xFFFF);
-                        if (P.fstate != nullptr) {
-                            uint32_t was = atomicExch(slot, kNoTask);
-                            if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 1, wid, (DBG_BAD_ID << 32) | was);
-                        }
-                    }
-                    __syncwarp();
-                    if (lane == 0) ws.tail[q] = t;
-                    __syncwarp();
+                    if (lane >= cnt && lane < cnt + claim) { tid = ws.retained[lane]; src = 1; }
                     cnt += claim;
-                    cls = q;
-                    ++st_pops;
+                    cls = 0;
+                    st_pops += claim;
                     st_popped += claim;
-                } else {
-                    __syncwarp();
+                }
+                __syncwarp();
+            }
+        } else {
+            // ---- PopBatch (Algorithm 2) from the own queue: the retained class, else the fullest (DAQ).
+            // The owner keeps an upper bound of each count (thieves only lower it), so an empty
+            // queue costs no memory access and the CAS starts from a good guess.
+            if (cnt < 32) {
+                int q = cls;
+                if (cnt == 0 && Q > 1) {
+                    int best = (lane < Q) ? ws.hint[lane] : -1, bq = lane;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        int oc = __shfl_down_sync(0xffffffffu, best, o);
+                        int oq = __shfl_down_sync(0xffffffffu, bq, o);
+                        if (oc > best || (oc == best && oq < bq)) { best = oc; bq = oq; }
+                    }
+                    q = __shfl_sync(0xffffffffu, bq, 0);
+                }
+                if (ws.hint[q] > 0) {
+                    int claim = 0;
+                    if (lane == 0) {
+                        int old = ws.hint[q];
+                        for (int it = 0; it < 64 && old > 0; ++it) {
+                            const int want = min(32 - cnt, old);
+                            const int got = atom_cas_acq_i32(&myq[q].count, old, old - want);
+                            if (got == old) { claim = want; old -= want; break; }
+                            old = got;
+                        }
+                        ws.hint[q] = max(old, 0);
+                    }
+                    claim = __shfl_sync(0xffffffffu, claim, 0);
+                    if (claim > 0) {
+                        uint32_t t = ws.tail[q] - (uint32_t)claim;
+                        if (lane >= cnt && lane < cnt + claim) {
+                            uint32_t* slot = &myring[(size_t)q * (cap_mask + 1) + ((t + (uint32_t)(lane - cnt)) & cap_mask)];
+                            tid = __ldcg(slot);
+                            src = 1;
+                            dbg_log(P, tid, 7, wid, iter, (t + (uint32_t)(lane - cnt)) & 0xFFFF);
+                            if (P.fstate != nullptr) {
+                                uint32_t was = atomicExch(slot, kNoTask);
+                                if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 1, wid, (DBG_BAD_ID << 32) | was);
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) ws.tail[q] = t;
+                        __syncwarp();
+                        cnt += claim;
+                        cls = q;
+                        ++st_pops;
+                        st_popped += claim;
+                    } else {
+                        __syncwarp();
+                    }
                 }
             }
         }
@@ -756,6 +834,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
         // ---- StealBatch.  SelectVictimQueue probes kProbes random victims at once (one
         // lane each) and picks the fullest, so an idle warp finds work in one round trip.
         bool want_steal = (P.steal_policy & GTAP_STEAL_EMPTY) ? (cnt == 0) : (cnt < 32);
+        if constexpr (SCHED == SCHED_GLOBAL) want_steal = false;   // no per-warp deques to steal from
         const bool fill = cnt > 0;
         if (want_steal && fill && fill_wait > 0) {
             --fill_wait;
@@ -793,51 +872,93 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             victim = __shfl_sync(0xffffffffu, victim, bl);
             const int q = __shfl_sync(0xffffffffu, vqi, bl);
             if (best > 0) {
-                QState* vq = P.qs + (size_t)victim * Q + q;
-                int claim = 0;
-                uint32_t h = 0;
-                if (lane == 0) {
-                    if (atom_cas_acq_i32(&vq->lock, 0, 1) == 0) {  // try-lock: never wait on a thief
-                        int old = best;
-                        for (int it = 0; it < 64 && old > 0; ++it) {
-                            int want = min(32 - cnt, old);
-                            if (P.steal_policy & GTAP_STEAL_HALF) want = min(want, (old + 1) >> 1);
-                            const int got = atom_cas_acq_i32(&vq->count, old, old - want);
-                            if (got == old) { claim = want; break; }
-                            old = got;
-                        }
-                        if (claim > 0) h = __ldcg(&vq->head);
-                        else st_release_i32(&vq->lock, 0);
-                    }
-                }
-                claim = __shfl_sync(0xffffffffu, claim, 0);
-                if (claim > 0) {
-                    h = __shfl_sync(0xffffffffu, h, 0);
+                if constexpr (SCHED == SCHED_SINGLE) {
+                    // non-batched steal (Sec. 6.5 comparison): lane 0 repeats single-task steals
+                    // from the chosen victim, each one lock, one CAS, one head read and update
+                    QState* vq = P.qs + (size_t)victim * Q + q;
                     const uint32_t* vring = P.rings + ((size_t)victim * Q + q) * (cap_mask + 1);
-                    if (lane >= cnt && lane < cnt + claim) {
-                        uint32_t* slot = const_cast<uint32_t*>(&vring[(h + (uint32_t)(lane - cnt)) & cap_mask]);
-                        tid = __ldcg(slot);
-                        src = 2;
-                        dbg_log(P, tid, 8, wid, iter, (unsigned)victim & 0xFFFF);
-                        if (P.fstate != nullptr) {
-                            uint32_t was = atomicExch(slot, kNoTask);
-                            if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 2, wid, (DBG_BAD_ID << 32) | was);
+                    int claim = 0;
+                    if (lane == 0) {
+                        int old = best;
+                        for (int k = 0; k < 32 - cnt && old > 0; ++k) {
+                            if (atom_cas_acq_i32(&vq->lock, 0, 1) != 0) break;   // try-lock
+                            bool ok = false;
+                            for (int it = 0; it < 64 && old > 0; ++it) {
+                                const int got = atom_cas_acq_i32(&vq->count, old, old - 1);
+                                if (got == old) { ok = true; old -= 1; break; }
+                                old = got;
+                            }
+                            if (ok) {
+                                const uint32_t hd = __ldcg(&vq->head);
+                                const uint32_t id = __ldcg(&vring[hd & cap_mask]);
+                                uint32_t zero;
+                                asm volatile("and.b32 %0, %1, 0;" : "=r"(zero) : "r"(id));  // the head store waits for the load
+                                __threadfence();
+                                __stcg(&vq->head, hd + 1u + zero);
+                                ws.retained[cnt + claim] = id;
+                                ++claim;
+                            }
+                            st_release_i32(&vq->lock, 0);
+                            if (!ok) break;
                         }
                     }
-                    // every claimed ID is in a register before the head moves (wrap-around safety, Sec. 5.1.3)
-                    const uint32_t used = __reduce_or_sync(0xffffffffu, (lane >= cnt && lane < cnt + claim) ? tid : 0u);
-                    uint32_t zero;
-                    asm volatile("and.b32 %0, %1, 0;" : "=r"(zero) : "r"(used));  // the head store waits for the loads
-                    __threadfence();
+                    claim = __shfl_sync(0xffffffffu, claim, 0);
                     __syncwarp();
-                    if (lane == 0) {
-                        __stcg(&vq->head, h + (uint32_t)claim + zero);
-                        st_release_i32(&vq->lock, 0);
+                    if (claim > 0) {
+                        if (lane >= cnt && lane < cnt + claim) { tid = ws.retained[lane]; src = 2; }
+                        cnt += claim;
+                        cls = q;
+                        st_steals += claim;
+                        st_stolen += claim;
                     }
-                    cnt += claim;
-                    cls = q;
-                    ++st_steals;
-                    st_stolen += claim;
+                    __syncwarp();
+                } else {
+                    QState* vq = P.qs + (size_t)victim * Q + q;
+                    int claim = 0;
+                    uint32_t h = 0;
+                    if (lane == 0) {
+                        if (atom_cas_acq_i32(&vq->lock, 0, 1) == 0) {  // try-lock: never wait on a thief
+                            int old = best;
+                            for (int it = 0; it < 64 && old > 0; ++it) {
+                                int want = min(32 - cnt, old);
+                                if (P.steal_policy & GTAP_STEAL_HALF) want = min(want, (old + 1) >> 1);
+                                const int got = atom_cas_acq_i32(&vq->count, old, old - want);
+                                if (got == old) { claim = want; break; }
+                                old = got;
+                            }
+                            if (claim > 0) h = __ldcg(&vq->head);
+                            else st_release_i32(&vq->lock, 0);
+                        }
+                    }
+                    claim = __shfl_sync(0xffffffffu, claim, 0);
+                    if (claim > 0) {
+                        h = __shfl_sync(0xffffffffu, h, 0);
+                        const uint32_t* vring = P.rings + ((size_t)victim * Q + q) * (cap_mask + 1);
+                        if (lane >= cnt && lane < cnt + claim) {
+                            uint32_t* slot = const_cast<uint32_t*>(&vring[(h + (uint32_t)(lane - cnt)) & cap_mask]);
+                            tid = __ldcg(slot);
+                            src = 2;
+                            dbg_log(P, tid, 8, wid, iter, (unsigned)victim & 0xFFFF);
+                            if (P.fstate != nullptr) {
+                                uint32_t was = atomicExch(slot, kNoTask);
+                                if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 2, wid, (DBG_BAD_ID << 32) | was);
+                            }
+                        }
+                        // every claimed ID is in a register before the head moves (wrap-around safety, Sec. 5.1.3)
+                        const uint32_t used = __reduce_or_sync(0xffffffffu, (lane >= cnt && lane < cnt + claim) ? tid : 0u);
+                        uint32_t zero;
+                        asm volatile("and.b32 %0, %1, 0;" : "=r"(zero) : "r"(used));  // the head store waits for the loads
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) {
+                            __stcg(&vq->head, h + (uint32_t)claim + zero);
+                            st_release_i32(&vq->lock, 0);
+                        }
+                        cnt += claim;
+                        cls = q;
+                        ++st_steals;
+                        st_stolen += claim;
+                    }
                 }
             }
             if (fill) {
@@ -936,7 +1057,8 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             int overflow = 0;
             if (lane < Q) {
                 int npush = ((Q > 1) ? ws.cls_count[lane] : nst) - (lane == qstar ? nkeep : 0);
-                if (npush > 0 && ws.tail[lane] - ws.head_lb[lane] + (uint32_t)npush > cap_mask + 1) {
+                // (the central queue has a slot for every record, so it cannot overflow)
+                if (SCHED != SCHED_GLOBAL && npush > 0 && ws.tail[lane] - ws.head_lb[lane] + (uint32_t)npush > cap_mask + 1) {
                     const uint32_t hd = __ldcg(&myq[lane].head);   // refresh the lower bound only when needed
                     ws.head_lb[lane] = hd;
                     if (ws.tail[lane] - hd + (uint32_t)npush > cap_mask + 1) overflow = 1;
@@ -948,7 +1070,18 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                 break;
             }
             __syncwarp();
+            unsigned long long gt0 = 0;   // central queue: first enqueue ticket of this batch
+            if constexpr (SCHED == SCHED_GLOBAL) {
+                // the records must be visible before any slot publishes them
+                if (nkeep < nst) {
+                    __threadfence();
+                    if (lane == 0) gt0 = atomicAdd(&P.ctl->gq_enq.v, (unsigned long long)(nst - nkeep));
+                    gt0 = __shfl_sync(0xffffffffu, gt0, 0);
+                }
+                __syncwarp();
+            }
             int kept = 0;
+            int gbad = 0;
             for (int base = 0; base < nst; base += 32) {
                 const int i = base + lane;
                 const bool valid = i < nst;
@@ -968,9 +1101,22 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                 if (push) off = ws.push_off[q];
                 __syncwarp();
                 if (push) {
-                    uint32_t pos = ws.tail[q] + (uint32_t)(off + prk);
-                    __stcg(&myring[(size_t)q * (cap_mask + 1) + (pos & cap_mask)], id);
-                    dbg_log(P, id, 6, wid, iter, pos & 0xFFFF);
+                    if constexpr (SCHED == SCHED_GLOBAL) {
+                        // wait (bounded) for the slot's previous occupant to be taken, then publish
+                        const unsigned long long tk = gt0 + (unsigned long long)(off + prk);
+                        unsigned long long* slot = &P.gq[tk & P.gq_mask];
+                        int ok = 0;
+                        for (int it = 0; it < (1 << 20); ++it) {
+                            if ((uint32_t)(ld_acquire_u64(slot) >> 32) == (uint32_t)tk) { ok = 1; break; }
+                            __nanosleep(32);
+                        }
+                        if (ok) st_release_u64(slot, ((unsigned long long)(uint32_t)(tk + 1) << 32) | id);
+                        else { gbad = 1; raise_error(P, GTAP_ERR_TASK_FAILED, -1, wid, tk); }
+                    } else {
+                        uint32_t pos = ws.tail[q] + (uint32_t)(off + prk);
+                        __stcg(&myring[(size_t)q * (cap_mask + 1) + (pos & cap_mask)], id);
+                        dbg_log(P, id, 6, wid, iter, pos & 0xFFFF);
+                    }
                     if (prk == 0) ws.push_off[q] = off + __popc(grp);
                 }
                 __syncwarp();
@@ -978,14 +1124,20 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             // one fence, then one count increment per destination queue (PushBatch).  When every
             // staged task is retained nothing is published to other warps, so no fence is needed:
             // the warp's own lanes see the records through the warp barrier.
-            if (nkeep < nst) __threadfence();
-            __syncwarp();
-            if (lane < Q) {
-                int np = ws.push_off[lane];
-                if (np > 0) {
-                    ws.tail[lane] += (uint32_t)np;
-                    ws.hint[lane] += np;
-                    atomicAdd(&myq[lane].count, np);
+            if constexpr (SCHED == SCHED_GLOBAL) {
+                if (__any_sync(0xffffffffu, gbad)) break;
+                __syncwarp();
+                if (lane == 0 && nkeep < nst) atomicAdd(&P.ctl->gq_avail.v, (unsigned long long)(nst - nkeep));
+            } else {
+                if (nkeep < nst) __threadfence();
+                __syncwarp();
+                if (lane < Q) {
+                    int np = ws.push_off[lane];
+                    if (np > 0) {
+                        ws.tail[lane] += (uint32_t)np;
+                        ws.hint[lane] += np;
+                        atomicAdd(&myq[lane].count, np);
+                    }
                 }
             }
             if (lane == 0) {

@@ -30,11 +30,13 @@ enum ProgType : int {
     T_KCLIQUE_ROOT = 6,  // range of DAG edges
     T_KCLIQUE_EDGE = 7,  // one edge / a sub-range of a candidate set
     T_KCLIQUE_SET = 8,
+    T_BINTREE = 9,       // full binary tree microbenchmark (Sec. 6.1, 6.2)
     // block mode
     T_MSORT = 16,
     T_MMERGE = 17,
     T_INTEGRATE_BLK = 18,
     T_DTT = 19,
+    T_BINTREE_BLK = 20,
     T_MAX = 32
 };
 
@@ -45,11 +47,16 @@ enum ProgSet : unsigned {
     PS_UTS = 1u << 2,
     PS_INTEGRATE = 1u << 3,
     PS_KCLIQUE = 1u << 4,
-    PS_THREAD_ALL = PS_FIB | PS_NQUEENS | PS_UTS | PS_INTEGRATE | PS_KCLIQUE,
+    PS_BINTREE = 1u << 5,
+    PS_THREAD_ALL = PS_FIB | PS_NQUEENS | PS_UTS | PS_INTEGRATE | PS_KCLIQUE | PS_BINTREE,
     PS_MSORT = 1u << 8,
     PS_INTEGRATE_BLK = 1u << 9,
     PS_DTT = 1u << 10,
+    PS_BINTREE_BLK = 1u << 11,
 };
+
+// Thread-mode queue management (gtap_config.scheduler; Sec. 6.5).
+enum Sched : int { SCHED_BATCHED = 0, SCHED_GLOBAL = 1, SCHED_SINGLE = 2 };
 
 constexpr uint64_t kScratchBlock = 4096;   // bytes per recycled scratch block
 
@@ -100,6 +107,7 @@ struct DevControl {
     Line128 sc_enq, sc_deq, sc_avail;   // scratch free-block queue tickets / completed frees
     Line128 out_tail;          // serving: completions written to the outbox
     Line128 admitted;          // serving: requests admitted so far
+    Line128 gq_enq, gq_deq, gq_avail;   // central-queue scheduler: tickets and completed publications
     alignas(128) ErrorRecord err;
 };
 
@@ -193,6 +201,9 @@ struct KParams {
     unsigned int* fstate;     // debug: per-record state (0 free, 1 allocated, 2 running, 3 queued), or null
     unsigned long long* flog; // debug: last 8 events per record
     unsigned int* flogn;      // debug: event count per record
+    // central-queue scheduler (GTAP_SCHED_GLOBAL): slot words (sequence:32 | task id:32)
+    unsigned long long* gq;
+    uint64_t gq_mask;
 };
 
 // Debug-check failure codes (error detail = code << 32 | record id).

@@ -3,6 +3,7 @@
 #include "gtap_device.cuh"
 #include "programs_block.cuh"
 #include "programs_dtt.cuh"
+#include "programs_micro.cuh"
 
 namespace gtap {
 
@@ -22,6 +23,9 @@ struct BlockDispatch {
         case T_DTT:
             if constexpr ((PSET & PS_DTT) != 0) { dtt_step<BS>(c); return; }
             break;
+        case T_BINTREE_BLK:
+            if constexpr ((PSET & PS_BINTREE_BLK) != 0) { bintree_blk_step<BS>(c); return; }
+            break;
         default:
             break;
         }
@@ -35,9 +39,11 @@ __global__ void __launch_bounds__(BS, 768 / BS) block_kernel(KParams P) {
     block_mode_loop<BlockDispatch<PSET, BS>>(P, smem, BS);
 }
 
-constexpr unsigned PS_BLOCK_ALL = PS_MSORT | PS_INTEGRATE_BLK | PS_DTT;
+constexpr unsigned PS_BLOCK_ALL = PS_MSORT | PS_INTEGRATE_BLK | PS_DTT | PS_BINTREE_BLK;
+// The binary-tree microbenchmark also runs with one-warp blocks (Sec. 6.1 uses block size 32 in both modes).
 #define GTAP_BLOCK_SETS(X) X(PS_MSORT, 256) X(PS_INTEGRATE_BLK, 256) X(PS_DTT, 256) X(PS_BLOCK_ALL, 256) \
-                           X(PS_MSORT, 128) X(PS_INTEGRATE_BLK, 128) X(PS_DTT, 128) X(PS_BLOCK_ALL, 128)
+                           X(PS_MSORT, 128) X(PS_INTEGRATE_BLK, 128) X(PS_DTT, 128) X(PS_BLOCK_ALL, 128) \
+                           X(PS_BINTREE_BLK, 256) X(PS_BINTREE_BLK, 128) X(PS_BINTREE_BLK, 32)
 
 static const void* block_kernel_fn(unsigned pset, int bs) {
 #define X(S, B) if (pset == (S) && bs == (B)) return reinterpret_cast<const void*>(&block_kernel<(S), (B)>);
@@ -47,7 +53,7 @@ static const void* block_kernel_fn(unsigned pset, int bs) {
 }
 
 unsigned block_kernel_pset(unsigned registered) {
-    const unsigned singles[] = {PS_MSORT, PS_INTEGRATE_BLK, PS_DTT};
+    const unsigned singles[] = {PS_MSORT, PS_INTEGRATE_BLK, PS_DTT, PS_BINTREE_BLK};
     for (unsigned s : singles)
         if (registered != 0 && (registered & ~s) == 0) return s;
     return PS_BLOCK_ALL;
@@ -67,6 +73,7 @@ size_t block_prog_smem(unsigned pset, int bs) {
     if (pset & PS_MSORT) b = std::max(b, (size_t)(2 * kMsPadded * 4 + 8 * 260));
     if (pset & PS_INTEGRATE_BLK) b = std::max(b, (size_t)(8 * bs));
     if (pset & PS_DTT) b = std::max(b, sizeof(DttShared) + 16);
+    if (pset & PS_BINTREE_BLK) b = std::max(b, (size_t)(8 * 32));
     return b;
 }
 

@@ -2,6 +2,7 @@
 #include "launch.h"
 #include "gtap_device.cuh"
 #include "programs_thread.cuh"
+#include "programs_micro.cuh"
 
 namespace gtap {
 
@@ -30,6 +31,9 @@ struct ThreadDispatch {
         case T_KCLIQUE_SET:
             if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_set_step(c); return; }
             break;
+        case T_BINTREE:
+            if constexpr ((PSET & PS_BINTREE) != 0) { bintree_step(c); return; }
+            break;
         default:
             break;
         }
@@ -47,26 +51,30 @@ constexpr int thread_min_blocks() {
     return (PSET == PS_NQUEENS || PSET == PS_THREAD_ALL) ? 3 : 4;
 }
 
-template <unsigned PSET>
+template <unsigned PSET, int SCHED>
 __global__ void __launch_bounds__(256, thread_min_blocks<PSET>()) thread_kernel(KParams P) {
     extern __shared__ __align__(16) char smem[];
     const int wib = threadIdx.x >> 5;
-    thread_mode_loop<ThreadDispatch<PSET>>(P, smem + (size_t)wib * thread_warp_smem((int)P.maxspawn));
+    thread_mode_loop<ThreadDispatch<PSET>, SCHED>(P, smem + (size_t)wib * thread_warp_smem((int)P.maxspawn));
 }
 
-#define GTAP_THREAD_SETS(X) X(PS_FIB) X(PS_NQUEENS) X(PS_UTS) X(PS_INTEGRATE) X(PS_KCLIQUE) X(PS_THREAD_ALL)
+// Default scheduler for every program set; the Sec. 6.5 comparison variants for
+// the scheduler-bound microbenchmark programs.
+#define GTAP_THREAD_SETS(X)                                                                                       \
+    X(PS_FIB, SCHED_BATCHED) X(PS_NQUEENS, SCHED_BATCHED) X(PS_UTS, SCHED_BATCHED) X(PS_INTEGRATE, SCHED_BATCHED) \
+    X(PS_KCLIQUE, SCHED_BATCHED) X(PS_BINTREE, SCHED_BATCHED) X(PS_THREAD_ALL, SCHED_BATCHED)                     \
+    X(PS_FIB, SCHED_GLOBAL) X(PS_FIB, SCHED_SINGLE) X(PS_UTS, SCHED_GLOBAL) X(PS_UTS, SCHED_SINGLE)               \
+    X(PS_BINTREE, SCHED_GLOBAL) X(PS_BINTREE, SCHED_SINGLE)
 
-static const void* thread_kernel_fn(unsigned pset) {
-    switch (pset) {
-#define X(S) case S: return reinterpret_cast<const void*>(&thread_kernel<S>);
-        GTAP_THREAD_SETS(X)
+static const void* thread_kernel_fn(unsigned pset, int sched) {
+#define X(S, Q) if (pset == (S) && sched == (Q)) return reinterpret_cast<const void*>(&thread_kernel<(S), (Q)>);
+    GTAP_THREAD_SETS(X)
 #undef X
-    default: return nullptr;
-    }
+    return nullptr;
 }
 
 unsigned thread_kernel_pset(unsigned registered) {
-    const unsigned singles[] = {PS_FIB, PS_NQUEENS, PS_UTS, PS_INTEGRATE, PS_KCLIQUE};
+    const unsigned singles[] = {PS_FIB, PS_NQUEENS, PS_UTS, PS_INTEGRATE, PS_KCLIQUE, PS_BINTREE};
     for (unsigned s : singles)
         if (registered != 0 && (registered & ~s) == 0) return s;
     return PS_THREAD_ALL;
@@ -79,13 +87,15 @@ int thread_kernel_maxspawn(unsigned pset) {
     if (pset & PS_UTS) m = max(m, 8);
     if (pset & PS_INTEGRATE) m = max(m, 2);
     if (pset & PS_KCLIQUE) m = max(m, kKcFan);
+    if (pset & PS_BINTREE) m = max(m, 2);
     return m;
 }
 
 uint32_t thread_record_bytes(unsigned) { return 64; }
 
-cudaError_t launch_thread_kernel(unsigned pset, const KParams& P, int grid, int block, size_t smem, cudaStream_t s) {
-    const void* fn = thread_kernel_fn(pset);
+cudaError_t launch_thread_kernel(unsigned pset, int sched, const KParams& P, int grid, int block, size_t smem,
+                                 cudaStream_t s) {
+    const void* fn = thread_kernel_fn(pset, sched);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -93,8 +103,8 @@ cudaError_t launch_thread_kernel(unsigned pset, const KParams& P, int grid, int 
     return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
 }
 
-cudaError_t thread_kernel_occupancy(unsigned pset, int block, size_t smem, int* blocks_per_sm) {
-    const void* fn = thread_kernel_fn(pset);
+cudaError_t thread_kernel_occupancy(unsigned pset, int sched, int block, size_t smem, int* blocks_per_sm) {
+    const void* fn = thread_kernel_fn(pset, sched);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

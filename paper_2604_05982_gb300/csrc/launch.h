@@ -7,8 +7,10 @@
 namespace gtap {
 
 // Thread mode: persistent scheduler kernel for a program set.
-cudaError_t launch_thread_kernel(unsigned pset, const KParams& P, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t thread_kernel_occupancy(unsigned pset, int block, size_t smem, int* blocks_per_sm);
+// sched: GTAP_SCHED_* (the comparison variants exist for fib, N-Queens, the hashed tree and the binary tree).
+cudaError_t launch_thread_kernel(unsigned pset, int sched, const KParams& P, int grid, int block, size_t smem,
+                                 cudaStream_t s);
+cudaError_t thread_kernel_occupancy(unsigned pset, int sched, int block, size_t smem, int* blocks_per_sm);
 unsigned thread_kernel_pset(unsigned registered);   // instantiation that covers the registered programs
 int thread_kernel_maxspawn(unsigned pset);
 uint32_t thread_record_bytes(unsigned pset);

@@ -15,6 +15,13 @@ __global__ void reset_kernel(KParams P, int init_cq) {
         for (size_t i = tid; i <= P.ncq_mask; i += nth) P.cq_seq[i] = i;
     if (P.sq_seq != nullptr)
         for (size_t i = tid; i <= P.sq_mask; i += nth) P.sq_seq[i] = i;
+    if (P.gq != nullptr) {
+        // central queue: slot i holds root i (published: sequence i + 1), the rest are free (sequence i)
+        for (size_t i = tid; i <= P.gq_mask; i += nth) {
+            const bool root = i < P.n_roots;
+            P.gq[i] = ((unsigned long long)(uint32_t)(i + (root ? 1 : 0)) << 32) | (root ? (uint32_t)i : 0u);
+        }
+    }
     if (P.fstate != nullptr)
         for (size_t i = tid; i < P.n_frames; i += nth) P.fstate[i] = (i < P.n_roots) ? 3u : 0u;
     // root records
@@ -37,7 +44,7 @@ __global__ void reset_kernel(KParams P, int init_cq) {
     for (size_t w = tid; w < P.n_workers; w += nth) {
         uint32_t cnt[kMaxQueues];
         for (uint32_t q = 0; q < Q; ++q) cnt[q] = 0;
-        for (size_t r = w; r < P.n_roots; r += P.n_workers) {
+        for (size_t r = w; P.gq == nullptr && r < P.n_roots; r += P.n_workers) {
             const uint32_t q = P.root_desc[r].queue % Q;
             P.rings[((size_t)w * Q + q) * cap + cnt[q]] = (uint32_t)r;
             ++cnt[q];
@@ -65,6 +72,9 @@ __global__ void reset_kernel(KParams P, int init_cq) {
         P.ctl->admitted.v = 0;
         P.ctl->scratch_top.v = 0;
         P.ctl->inflight.v = 0;
+        P.ctl->gq_enq.v = P.gq ? P.n_roots : 0;
+        P.ctl->gq_deq.v = 0;
+        P.ctl->gq_avail.v = P.gq ? P.n_roots : 0;
         P.ctl->err.code = 0;
         P.ctl->err.task_type = -1;
         P.ctl->err.worker = -1;

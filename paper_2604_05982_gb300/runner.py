@@ -113,6 +113,17 @@ def uts(seed: int = 42, root_children: int = 2000, m: int = 5, threshold: int = 
         return RunResult([(v >> 32, v & 0xFFFFFFFF)], c.stats())
 
 
+def bintree(depth: int, iters: int, K: int = 1, route: int = 0, block: bool = False, cutoff: int = 0,
+            n_queues: int = 1, **cfg) -> RunResult:
+    """Full binary task tree (Sec. 6.1, 6.2): thread mode ("bintree") or block mode ("bintree_block")."""
+    mode = G.GTAP_MODE_BLOCK if block else G.GTAP_MODE_THREAD
+    with Context(mode, n_queues, **cfg) as c:
+        t = c.register("bintree_block" if block else "bintree")
+        h = c.spawn(t, G.gtap_bintree_args(depth, iters, K, route, cutoff, 0))
+        c.run()
+        return RunResult([c.result_u64(h)], c.stats())
+
+
 def integrate(a: float, b: float, eps: float, block: bool = False, **cfg) -> RunResult:
     mode = G.GTAP_MODE_BLOCK if block else G.GTAP_MODE_THREAD
     with Context(mode, 1, **cfg) as c:
