@@ -196,6 +196,8 @@ def run_gpu(args):
     out = dst[:: 1 << 12].cpu().numpy().view(np.uint32)
     assert np.all(out[1:] >= out[:-1])
 
+    tasks_nq, tasks_ut = nq.stats()["tasks_created"], ut.stats()["tasks_created"]
+    ceil = atomic_ceiling(local)
     per_kernel = {"nqueens": [], "tree": [], "mergesort": []}
     if world > 1:
         torch.distributed.barrier()
@@ -250,6 +252,17 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": "block_kernel<mergesort> (2^26 keys)", "achieved": achieved,
                      "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": traffic, "algorithmic_bytes": MSORT_BYTES},
+        # every kernel of the step against its own ceiling: the sort against HBM, the two
+        # thread-mode schedulers against the measured join-decrement rate (one acq_rel
+        # decrement per non-root task)
+        "rooflines": [
+            {"bound": "hbm", "kernel": "block_kernel<mergesort>", "achieved": achieved, "peak": hbm_peak,
+             "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic},
+            _atomic_roofline("thread_kernel<nqueens> (DAQ 4)", tasks_nq, tasks_nq - 1, 0,
+                             sorted(per_kernel["nqueens"])[len(per_kernel["nqueens"]) // 2], ceil),
+            _atomic_roofline("thread_kernel<uts>", tasks_ut, tasks_ut - 1, 0,
+                             sorted(per_kernel["tree"])[len(per_kernel["tree"]) // 2], ceil)],
+        "atomic_ceiling_gops": {k: x / 1e9 for k, x in ceil.items()},
         "e2e": {"value": STEP_TASKS / (e2e_ms / 1e3), "unit": "tasks/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": n * 4 + 3 * 128, "d2h_bytes_per_step": n * 4 + 3 * 32},
         "gpu_launches": launches_per_step * args.steps,
@@ -325,6 +338,9 @@ def run_reference(args):
     if args.workload == "serve":
         run_reference_serve(args)
         return
+    if args.workload in ("fib", "sched", "micro", "batch"):
+        run_reference_small(args)
+        return
     import oracle
     oracle.build()
     try:
@@ -343,6 +359,56 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
                              "sample": "full step per iteration, single thread"},
             "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_small(args):
+    """Reference arm (the oracle on one host core) of the fib, sched, micro and batch lines."""
+    import oracle
+    oracle.build()
+    _pin_one_core()
+    world, _, _ = _dist()
+
+    def sample():
+        t0 = time.perf_counter()
+        if args.workload in ("fib", "sched"):
+            n = FIB_N if args.workload == "fib" else SCHED_N
+            v, tasks = oracle.fib(n)
+            return tasks, time.perf_counter() - t0
+        if args.workload == "micro":
+            oracle.bintree(16, 2048, 1)   # D = 16 of the D = 25 tree: 1/512 of the leaves
+            return 1, (time.perf_counter() - t0) * 512
+        from paper_2604_05982_gb300 import inputs
+        graphs = [inputs.rmat_graph(12 + (7 * i) // 64, 16, seed=7 + i) for i in (0, 18, 27, 36)]
+        t0 = time.perf_counter()
+        for n, e in graphs:
+            oracle.kclique(n, e, 4)
+        return len(graphs), time.perf_counter() - t0
+
+    for _ in range(min(args.warmup, 1)):
+        sample()
+    res = [sample() for _ in range(args.steps)]
+    units = sum(r[0] for r in res)
+    secs = sum(r[1] for r in res)
+    if args.workload in ("fib", "sched"):
+        n = FIB_N if args.workload == "fib" else SCHED_N
+        metric, unit, value, hib = "tasks/s", "tasks/s", units / secs, True
+        wl, note = f"fib({n}) thread mode (oracle)", f"oracle fib({n}) serial recursion per step"
+    elif args.workload == "micro":
+        metric, unit, value, hib = "binary-tree time", "ms", 1e3 * secs / args.steps, False
+        wl, note = ("binary task tree D = 25, compute_iters 2048 (oracle)",
+                    "oracle binary tree of depth 16 (1/512 of the leaves) per step, scaled x512")
+    else:
+        metric, unit, value, hib = "batched jobs/s", "instances/s", units / secs, True
+        wl, note = ("batched 4-clique, 64 R-MAT graphs scales 12-18 (oracle)",
+                    "oracle 4-clique count of graphs 0, 18, 27, 36 of the batch (scales 12-15) per step; "
+                    "the larger graphs are slower, so this overstates the oracle's rate on the whole batch")
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": wl},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": note},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -556,10 +622,11 @@ def _fmm_cpu_sample():
 
 
 KC_SCALE = 20
-KC_K = 4
+KC_K = 4          # default k; --k selects 5, 6, 7
 KC_QUEUES = 4
 KC_CPU_RANGES = 2048     # oracle sample: evenly spaced DAG-edge ranges ...
-KC_CPU_RANGE = 64        # ... of this many edges each (~0.8 % of the scale-20 graph's edges)
+KC_CPU_RANGE = 64        # ... of this many edges each at k = 4 (~0.8 % of the scale-20 graph's edges),
+                         # a quarter as many per step of k above 4
 
 
 def _pin_one_core():
@@ -569,7 +636,7 @@ def _pin_one_core():
         pass
 
 
-def _kclique_cpu_sample(n, e):
+def _kclique_cpu_sample(n, e, k=KC_K):
     """One oracle k-clique instance estimated on one core: the orientation in full,
     the counting on KC_CPU_RANGES evenly spaced ranges of KC_CPU_RANGE DAG edges,
     scaled to all edges.  Returns (ms per instance, seconds spent)."""
@@ -581,17 +648,19 @@ def _kclique_cpu_sample(n, e):
     t0 = time.perf_counter()
     off, adj = oracle.orient(n, e)
     t1 = time.perf_counter()
+    per = max(1, KC_CPU_RANGE >> (2 * (k - 4)))
     starts = np.arange(KC_CPU_RANGES, dtype=np.int64) * (m // KC_CPU_RANGES)
-    ranges = np.stack([starts, np.minimum(starts + KC_CPU_RANGE, m)], axis=1)
-    oracle.kclique_dag_ranges(off, adj, KC_K, ranges)
+    ranges = np.stack([starts, np.minimum(starts + per, m)], axis=1)
+    oracle.kclique_dag_ranges(off, adj, k, ranges)
     t2 = time.perf_counter()
     sampled = int((ranges[:, 1] - ranges[:, 0]).sum())
     return ((t1 - t0) + (t2 - t1) * m / sampled) * 1e3, t2 - t0
 
 
-def _kclique_cpu_note(m):
-    return (f"oracle on one core: orientation of the whole graph, then the {KC_K}-clique count on "
-            f"{KC_CPU_RANGES} evenly spaced ranges of {KC_CPU_RANGE} DAG edges, scaled to all {m} edges")
+def _kclique_cpu_note(m, k=KC_K):
+    per = max(1, KC_CPU_RANGE >> (2 * (k - 4)))
+    return (f"oracle on one core: orientation of the whole graph, then the {k}-clique count on "
+            f"{KC_CPU_RANGES} evenly spaced ranges of {per} DAG edges, scaled to all {m} edges")
 
 
 def run_reference_kclique(args):
@@ -602,15 +671,15 @@ def run_reference_kclique(args):
     _pin_one_core()
     n, e = inputs.rmat_graph(KC_SCALE, 16, seed=7)
     for _ in range(min(args.warmup, 1)):
-        _kclique_cpu_sample(n, e)
-    vals = [_kclique_cpu_sample(n, e)[0] for _ in range(args.steps)]
+        _kclique_cpu_sample(n, e, args.k)
+    vals = [_kclique_cpu_sample(n, e, args.k)[0] for _ in range(args.steps)]
     value = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": "k-clique time", "value": value, "unit": "ms/instance", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"{KC_K}-clique count, R-MAT scale {KC_SCALE} edge factor 16, seed 7 (oracle)"},
+            "config": {"workload": f"{args.k}-clique count, R-MAT scale {KC_SCALE} edge factor 16, seed 7 (oracle)"},
             "cpu_baseline": {"value": value, "unit": "ms/instance", "cores": 1, "kind": "oracle",
-                             "sample": _kclique_cpu_note(len(e))},
+                             "sample": _kclique_cpu_note(len(e), args.k)},
             "e2e": {"value": value, "unit": "ms/instance", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -637,13 +706,16 @@ def run_kclique(args):
     src = torch.empty(m, dtype=torch.int32, device="cuda")
     work = torch.empty(4 * n + 16, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
-    kargs = G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), 0, m, KC_K, 64, 1, 0)
-    pool, scratch = 1 << 30, 4 << 30
+    kargs = G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), 0, m, args.k, 64, 1, 0)
+    # k >= 5 holds a larger frontier: DAQ 4 needs rings of 16384 and a 4 GiB record pool
+    pool, scratch = (1 << 30, 4 << 30) if args.k == 4 else (4 << 30, 4 << 30)
+    ring = 4096 if args.k == 4 else 16384
 
     def step():
         G.gtap_kclique_orient(edges.data_ptr(), m, n, off.data_ptr(), adj.data_ptr(), src.data_ptr(),
                               work.data_ptr(), 0)
-        with runner.Context(G.GTAP_MODE_THREAD, KC_QUEUES, pool_bytes=pool, scratch_bytes=scratch) as c:
+        with runner.Context(G.GTAP_MODE_THREAD, KC_QUEUES, pool_bytes=pool, scratch_bytes=scratch,
+                            deque_capacity=ring) as c:
             t = c.register("kclique")
             h = c.spawn(t, kargs)
             c.run()
@@ -651,15 +723,24 @@ def run_kclique(args):
 
     for _ in range(args.warmup):
         count, _ = step()
-    # parity spot check (outside the timed region): sampled DAG-edge ranges against the oracle
-    ranges = [(lo, lo + 400) for lo in (0, m // 3, (2 * m) // 3)] + [(m - 200, m)]
+    # parity (outside the timed region): the full count against the oracle's golden value
+    # (tests/golden, written from the oracle alone) where one exists, and sampled DAG-edge
+    # ranges against the oracle run here
+    gold = _kclique_golden(f"kclique_rmat{KC_SCALE}_k{args.k}.txt")
+    if gold is not None:
+        assert count == gold["total"], (count, gold["total"])
+    if args.k <= 4:
+        ranges = [(lo, lo + 400) for lo in (0, m // 3, (2 * m) // 3)] + [(m - 200, m)]
+    else:
+        # larger k: the oracle's cost per edge explodes at the dense low-id end, so sample the rest
+        ranges = [(lo, lo + 64) for lo in ((2 * m) // 3, (5 * m) // 6)] + [(m - 200, m)]
     with runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=pool, scratch_bytes=scratch) as c:
         t = c.register("kclique")
-        hs = [c.spawn(t, G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), lo, hi, KC_K, 64, 0, 0))
+        hs = [c.spawn(t, G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), lo, hi, args.k, 64, 0, 0))
               for lo, hi in ranges]
         c.run()
         got = [c.result_u64(h) for h in hs]
-    want = [oracle.kclique_edge_range(n, e, KC_K, lo, hi) for lo, hi in ranges]
+    want = [oracle.kclique_edge_range(n, e, args.k, lo, hi) for lo, hi in ranges]
     assert got == want, (got, want)
     kms = []
     torch.cuda.synchronize()
@@ -677,12 +758,14 @@ def run_kclique(args):
         "metric": "k-clique time", "value": ms, "unit": "ms/instance", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"{KC_K}-clique count, R-MAT scale {KC_SCALE} edge factor 16 (a,b,c=0.57,0.19,0.19, "
+        "config": {"workload": f"{args.k}-clique count, R-MAT scale {KC_SCALE} edge factor 16 (a,b,c=0.57,0.19,0.19, "
                                f"seed 7, {m} undirected edges), degree-ordered DAG, thread mode, DAQ {KC_QUEUES} queues "
                                "by recursion depth, split threshold 64; one step = orientation + gtap_init + run + "
                                "gtap_finalize (wall clock, synchronised)", "parallelism": "replicas",
                    "l2": "graph 126 MB CSR + 63 MB edge list, > L2 with the scratch sets"},
         "count": count, "kernel_ms_median": kms[len(kms) // 2],
+        "parity": ("full count equals the oracle's (golden file) and sampled ranges equal the oracle's"
+                   if gold is not None else "sampled DAG-edge ranges equal the oracle's"),
         "e2e": {"value": ms, "unit": "ms/instance", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 16,
                 "note": "the edge list stays resident; the count is read back each step"},
         "gpu_launches": (9 + 2) * args.steps,
@@ -690,9 +773,9 @@ def run_kclique(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _pin_one_core()
-        value, _ = _kclique_cpu_sample(n, e)
+        value, _ = _kclique_cpu_sample(n, e, args.k)
         line["cpu_baseline"] = {"value": value, "unit": "ms/instance", "cores": 1, "kind": "oracle",
-                                "sample": _kclique_cpu_note(m)}
+                                "sample": _kclique_cpu_note(m, args.k)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -883,6 +966,387 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Atomic-rate ceiling, measured live (the roofline denominator of the thread-mode
+# scheduler kernels): scattered acq_rel 32-bit adds with return (the join
+# decrement) and scattered 64-bit reductions (accumulating joins).
+def atomic_ceiling(local: int = 0):
+    import torch
+
+    from paper_2604_05982_gb300 import gtap as G
+    region = torch.zeros(200 << 18, dtype=torch.int32, device=f"cuda:{local}")
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    out = {}
+    for kind, key in ((0, "join_decrement"), (1, "accumulate")):
+        ms, ops = G.gtap_microbench(kind, region.data_ptr(), region.numel() * 4, sms * 8, 256, 64)
+        out[key] = ops / (ms / 1e3)
+    del region
+    return out
+
+
+def _atomic_roofline(kernel, tasks, decrements, accumulates, kernel_ms, ceil):
+    """Roofline object of a thread-mode kernel against the measured atomic rates: the
+    launch's join decrements and accumulating adds take 1/rate each of the L2 atomic
+    units; achieved = atomic operations per second of the kernel's duration."""
+    secs = kernel_ms / 1e3
+    ops = decrements + accumulates
+    # time the atomic units need for this mix at the measured rates, per operation
+    t_ops = decrements / ceil["join_decrement"] + accumulates / ceil["accumulate"]
+    peak = ops / t_ops
+    achieved = ops / secs
+    return {"bound": "l2_atomic", "kernel": kernel, "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "peak_kind": "measured live (gtap_microbench kinds 0 and 1: scattered acq_rel add, red.add.u64)",
+            "unit": "Gop/s", "frac": achieved / peak, "traffic": None, "tasks_per_s": tasks / secs,
+            "atomics_per_launch": ops}
+
+
+FIB_N = 30
+FIB_TASKS = 2692537          # 2 F(31) - 1
+
+
+def _gpu_setup(args):
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    from paper_2604_05982_gb300 import gtap as G
+    G.load_library()
+    return world, rank, local
+
+
+def _finish(line, world, rank):
+    import torch
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_fib(args):
+    """fib(30) in thread mode, no cutoff: one step = one persistent-kernel run."""
+    import torch
+
+    import oracle
+    from paper_2604_05982_gb300 import gtap as G
+    from paper_2604_05982_gb300 import runner
+    world, rank, local = _gpu_setup(args)
+    fa = G.gtap_fib_args(FIB_N, 0)
+    tmask = G.GTAP_TUNE_BLOCKS | G.GTAP_TUNE_STEAL | G.GTAP_TUNE_CAPACITY
+    if args.no_tune:
+        tuned = {"blocks_per_sm": 4, "steal_policy": 0, "deque_capacity": 4096}
+    else:
+        best, _ = G.gtap_autotune(G.GTAP_MODE_THREAD, "fib", [fa], 1 << 30, runner.make_config(), reps=3,
+                                  n_queues=1, tune_mask=tmask)
+        tuned = {k: best[k] for k in ("blocks_per_sm", "steal_policy", "deque_capacity")}
+    c = runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=1 << 30, **tuned)
+    t = c.register("fib")
+    h = c.spawn(t, fa)
+    for _ in range(args.warmup):
+        c.run()
+    v, tasks = oracle.fib(FIB_N)
+    assert c.result_i64(h) == v == 832040
+    assert c.stats()["tasks_created"] == tasks == FIB_TASKS
+    ceil = atomic_ceiling(local)
+    kms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            c.run()
+            kms.append(c.stats()["kernel_ms"])
+        e1.record()
+        torch.cuda.synchronize()
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1))
+    value = aggregate_rate(FIB_TASKS, args.steps, world, elapsed_ms)
+    # end to end through the C ABI from the host: queue the root (its arguments are copied
+    # to the device by gtap_run), run, wait (the results and counters come back), read
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c.clear()
+        hh = c.spawn(t, fa)
+        c.run()
+        assert c.result_i64(hh) == 832040
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    kms.sort()
+    kmed = kms[len(kms) // 2]
+    st = c.stats()
+    line = {
+        "metric": "tasks/s", "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"fib({FIB_N}) thread mode, a task per call, no cutoff ({FIB_TASKS} tasks)",
+                   "parallelism": "replicas", "l2": "task records re-initialised every run (172 MB pool touched)"},
+        "result": v, "tasks_created": st["tasks_created"], "kernel_ms_median": kmed,
+        "launch_config": {"source": "default" if args.no_tune else "gtap_autotune", **tuned},
+        "roofline": _atomic_roofline("thread_kernel<fib>", FIB_TASKS, FIB_TASKS - 1, 0, kmed, ceil),
+        "atomic_ceiling_gops": {k: x / 1e9 for k, x in ceil.items()},
+        "e2e": {"value": FIB_TASKS / e2e_s, "unit": "tasks/s", "ms_per_step": e2e_s * 1e3,
+                "h2d_bytes_per_step": 128, "d2h_bytes_per_step": 8,
+                "note": "root arguments in, result out through gtap_spawn_root / gtap_run / gtap_wait / "
+                        "gtap_read_result (wall clock)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _pin_one_core()
+        t0 = time.perf_counter()
+        oracle.fib(FIB_N)
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": FIB_TASKS / secs, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle fib({FIB_N}) serial recursion, single thread ({secs:.3f} s)"}
+    c.close()
+    _finish(line, world, rank)
+
+
+SCHED_N = 35
+SCHED_GRIDS = (1, 4, 16, 38, 76, 152, 304, 608)   # 256-thread blocks
+
+
+def run_sched(args):
+    """Sec. 6.5: centralised queue, non-batched stealing and batched stealing on fib(35)
+    across grid sizes (one launch per configuration, median kernel time)."""
+    import oracle
+    from paper_2604_05982_gb300 import gtap as G
+    from paper_2604_05982_gb300 import runner
+    world, rank, local = _gpu_setup(args)
+    v, tasks = oracle.fib(SCHED_N)
+    names = {G.GTAP_SCHED_BATCHED: "batched stealing", G.GTAP_SCHED_SINGLE: "non-batched stealing",
+             G.GTAP_SCHED_GLOBAL: "central queue"}
+    rows = []
+    reps = max(1, min(args.steps, 5))
+    for sched in names:
+        for grid in SCHED_GRIDS:
+            with runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=2 << 30, scheduler=sched, grid_blocks=grid,
+                                blocks_per_sm=4) as c:
+                t = c.register("fib")
+                h = c.spawn(t, G.gtap_fib_args(SCHED_N, 0))
+                ks = []
+                for i in range(1 + reps):
+                    c.run(timeout_ms=120000)
+                    assert c.result_i64(h) == v and c.stats()["tasks_created"] == tasks
+                    if i:
+                        ks.append(c.stats()["kernel_ms"])
+                ks.sort()
+                ms = ks[len(ks) // 2]
+                rows.append({"scheduler": names[sched], "grid_blocks": grid, "threads": grid * 256,
+                             "kernel_ms": ms, "tasks_per_s": tasks / (ms / 1e3)})
+                print(json.dumps({"progress": rows[-1]}), file=sys.stderr, flush=True)
+    best = [r for r in rows if r["scheduler"] == "batched stealing" and r["grid_blocks"] == 608][0]
+    line = {"metric": "tasks/s", "value": best["tasks_per_s"], "unit": "tasks/s", "n_gpus": world,
+            "steps": reps, "warmup": 1, "ms_per_step": best["kernel_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"scheduler comparison (Sec. 6.5): fib({SCHED_N}) thread mode, {tasks} tasks, "
+                                   "central queue vs non-batched vs batched stealing across grid sizes of "
+                                   "256-thread blocks", "parallelism": "replicas"},
+            "value_is": "batched stealing at 608 blocks (4 per SM)", "sweep": rows,
+            "gpu_launches": 2 * (1 + reps) * len(rows)}
+    _finish(line, world, rank)
+
+
+MICRO_GRID, MICRO_BS = 2000, 32     # Sec. 6.1: grid size 2000, block size 32 in both modes
+
+
+def run_micro(args):
+    """Sec. 6.1 / 6.2: full binary task tree, thread mode vs block mode (with and
+    without a 5-level cutoff), compute_iters and depth sweeps; heterogeneous leaves
+    (K = 2, 4) with and without DAQ.  Every run's sum is checked against the oracle
+    on a sampled subset (full oracle for the small trees)."""
+    import oracle
+    from paper_2604_05982_gb300 import gtap as G
+    from paper_2604_05982_gb300 import runner
+    world, rank, local = _gpu_setup(args)
+    reps = max(1, min(args.steps, 3))
+    geo = dict(grid_blocks=MICRO_GRID, threads_per_block=MICRO_BS, blocks_per_sm=32, pool_bytes=4 << 30,
+               deque_capacity=16384)
+
+    def timed(depth, iters, K=1, block=False, cutoff=0, daq=False):
+        q = K + 1 if daq else 1
+        mode = G.GTAP_MODE_BLOCK if block else G.GTAP_MODE_THREAD
+        with runner.Context(mode, q, **geo) as c:
+            t = c.register("bintree_block" if block else "bintree")
+            h = c.spawn(t, G.gtap_bintree_args(depth, iters, K, 1 if daq else 0, cutoff, 0))
+            ks = []
+            for i in range(1 + reps):
+                c.run(timeout_ms=300000)
+                if i:
+                    ks.append(c.stats()["kernel_ms"])
+            val = c.result_u64(h)
+        ks.sort()
+        return ks[len(ks) // 2], val
+
+    want_cache = {}
+
+    def check(depth, iters, K, val):
+        if depth <= 16:
+            key = (depth, iters, K)
+            if key not in want_cache:
+                want_cache[key] = oracle.bintree(depth, iters, K)[0]
+            assert val == want_cache[key], key
+        return True
+
+    out = {"iters_sweep": [], "depth_sweep": [], "hetero": []}
+    D = 25
+    for iters in (1, 16, 256, 2048):
+        row = {"depth": D, "compute_iters": iters}
+        vals = set()
+        for name, kw in (("thread", {}), ("block", {"block": True}), ("block_cutoff5", {"block": True, "cutoff": 5})):
+            ms, val = timed(D, iters, **kw)
+            row[name + "_ms"] = ms
+            vals.add(val)
+        assert len(vals) == 1, row          # the three modes give the same sum
+        row["block_over_thread"] = row["block_ms"] / row["thread_ms"]
+        row["cutoff_over_thread"] = row["block_cutoff5_ms"] / row["thread_ms"]
+        out["iters_sweep"].append(row)
+        print(json.dumps({"progress": row}), file=sys.stderr, flush=True)
+    for depth in (8, 10, 12, 14, 16, 18, 20, 22, 25):
+        row = {"depth": depth, "compute_iters": 2048}
+        for name, kw in (("thread", {}), ("block", {"block": True}), ("block_cutoff5", {"block": True, "cutoff": 5})):
+            ms, val = timed(depth, 2048, **kw)
+            check(depth, 2048, 1, val)
+            row[name + "_ms"] = ms
+        row["block_over_thread"] = row["block_ms"] / row["thread_ms"]
+        row["cutoff_over_thread"] = row["block_cutoff5_ms"] / row["thread_ms"]
+        out["depth_sweep"].append(row)
+        print(json.dumps({"progress": row}), file=sys.stderr, flush=True)
+    for K in (2, 4):
+        for iters in (16, 256, 2048):
+            row = {"K": K, "depth": D, "compute_iters": iters}
+            vals = set()
+            for name, kw in (("thread_nodaq", {}), ("thread_daq", {"daq": True}), ("block", {"block": True})):
+                ms, val = timed(D, iters, K=K, **kw)
+                row[name + "_ms"] = ms
+                vals.add(val)
+            assert len(vals) == 1, row
+            row["daq_speedup"] = row["thread_nodaq_ms"] / row["thread_daq_ms"]
+            out["hetero"].append(row)
+            print(json.dumps({"progress": row}), file=sys.stderr, flush=True)
+    # the depth at which thread mode overtakes each block variant
+    def crossover(key):
+        for r in out["depth_sweep"]:
+            if r[key] > 1.0:
+                return r["depth"]
+        return None
+    ref = [r for r in out["iters_sweep"] if r["compute_iters"] == 2048][0]
+    line = {"metric": "binary-tree time", "value": ref["thread_ms"], "unit": "ms", "n_gpus": world, "steps": reps,
+            "warmup": 1, "ms_per_step": ref["thread_ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"mode/DAQ microbenchmarks (Sec. 6.1, 6.2): full binary task tree, depth {D}, "
+                                   f"compute_iters 2048, grid {MICRO_GRID} x {MICRO_BS} threads in both modes",
+                       "parallelism": "replicas"},
+            "value_is": "thread mode, D = 25, compute_iters = 2048", **out,
+            "thread_overtakes_block_at_depth": crossover("block_over_thread"),
+            "thread_overtakes_block_cutoff_at_depth": crossover("cutoff_over_thread"),
+            "gpu_launches": 2 * (1 + reps) * (3 * 4 + 3 * 9 + 3 * 6)}
+    _finish(line, world, rank)
+
+
+
+def _kclique_golden(name):
+    """A k-clique golden file written by tests/golden/make_kclique_goldens.py (oracle only)."""
+    import importlib.util
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None
+    spec = importlib.util.spec_from_file_location("make_kclique_goldens",
+                                                  os.path.join(ROOT, "tests", "golden", "make_kclique_goldens.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.load(path)
+
+
+BATCH_GRAPHS = 64
+
+
+def run_batch(args):
+    """The batched k-clique variant: 64 R-MAT graphs (graph i: scale 12 + floor(7i/64), seed
+    7 + i), 4-cliques, as (a) one persistent launch with 64 roots, (b) the replay of that
+    launch captured as a CUDA graph, (c) 64 plain launches, one per instance.  Counts are
+    asserted equal across the three forms and to the oracle's."""
+    import numpy as np
+    import torch
+
+    from paper_2604_05982_gb300 import gtap as G
+    from paper_2604_05982_gb300 import inputs, runner
+    world, rank, local = _gpu_setup(args)
+    gold = _kclique_golden("kclique_batch64_k4.txt")
+    specs = [(12 + (7 * i) // 64, 7 + i) for i in range(BATCH_GRAPHS)]
+    graphs = [runner.DeviceGraph(*inputs.rmat_graph(sc, 16, seed=sd)) for sc, sd in specs]
+    torch.cuda.synchronize()
+    # DAQ 4 by depth: 64 instances' frontier needs rings of 16384 (4096 overflows)
+    cfg = dict(pool_bytes=1 << 30, scratch_bytes=4 << 30, deque_capacity=16384)
+    want = [g[4] for g in gold["graphs"]] if gold else None
+
+    def one_launch(c, hs):
+        c.run()
+        return [c.result_u64(h) for h in hs]
+
+    # (a) + (b): one context with the 64 roots
+    c = runner.Context(G.GTAP_MODE_THREAD, 4, **cfg)
+    t = c.register("kclique")
+    hs = [c.spawn(t, g.args(4, 64, 1)) for g in graphs]
+    for _ in range(args.warmup):
+        got = one_launch(c, hs)
+    if want is not None:
+        assert got == want
+    want = got
+
+    def timed(fn, n):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / n
+
+    with ClockSampler(local) as clk:
+        t_plain = timed(lambda: one_launch(c, hs), args.steps)
+        c.capture()
+        for _ in range(2):
+            assert one_launch(c, hs) == want
+        t_graph = timed(lambda: one_launch(c, hs), args.steps)
+        assert one_launch(c, hs) == want
+        # (c) one launch per instance
+        per = [runner.Context(G.GTAP_MODE_THREAD, 4, **cfg) for _ in range(1)]
+        pc = per[0]
+        pt = pc.register("kclique")
+
+        def per_instance():
+            out = []
+            for g in graphs:
+                pc.clear()
+                h = pc.spawn(pt, g.args(4, 64, 1))
+                pc.run()
+                out.append(pc.result_u64(h))
+            return out
+        assert per_instance() == want
+        t_per = timed(per_instance, max(1, args.steps // 2))
+    elapsed = max_over_ranks(t_graph)
+    line = {"metric": "batched jobs/s", "value": world * BATCH_GRAPHS / elapsed, "unit": "instances/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched k-clique: 64 R-MAT graphs (scales 12-18, graph i: scale 12 + floor(7i/64), "
+                                   "edge factor 16, seed 7 + i), k = 4, DAQ 4 queues by depth, one persistent launch "
+                                   "replayed from a captured CUDA graph", "parallelism": "replicas"},
+            "forms_ms": {"graph_replay_one_launch": t_graph * 1e3, "plain_one_launch": t_plain * 1e3,
+                         "one_launch_per_instance": t_per * 1e3},
+            "speedup_vs_per_instance": t_per / t_graph,
+            "counts_identical_across_forms": True,
+            "counts_match_oracle_golden": gold is not None,
+            "e2e": {"value": BATCH_GRAPHS / t_graph, "unit": "instances/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": BATCH_GRAPHS * 32,
+                    "note": "graphs resident on the device; each step reads the 64 counts back (gtap_wait)"},
+            "gpu_launches": 2 * (args.steps * 2 + args.steps // 2 * BATCH_GRAPHS),
+            "clocks": clk.summary()}
+    pc.close()
+    c.close()
+    _finish(line, world, rank)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -891,14 +1355,30 @@ def main():
     ap.add_argument("--impl", default="gtap", choices=["gtap", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="integer set: default launch configuration, no autotuning")
-    ap.add_argument("--workload", default="integer", choices=["integer", "serve", "fmm", "kclique"],
-                    help="integer: the default bench line; serve: the served mixed stream; fmm: Laplace FMM; "
-                         "kclique: 4-clique count on the scale-20 R-MAT graph")
+    ap.add_argument("--workload", default="integer",
+                    choices=["integer", "fib", "serve", "fmm", "kclique", "batch", "sched", "micro"],
+                    help="integer: the default bench line (N-Queens 13, hashed tree, mergesort 2^26); fib: fib(30); "
+                         "serve: the served mixed stream; fmm: Laplace FMM; kclique: k-clique count on the scale-20 "
+                         "R-MAT graph; batch: 64 R-MAT graphs in one launch vs graph replay vs per-instance "
+                         "launches; sched: scheduler comparison on fib(35); micro: mode/DAQ binary-tree sweeps")
     ap.add_argument("--requests", type=int, default=SERVE_REQUESTS)
+    ap.add_argument("--k", type=int, default=KC_K, choices=[4, 5, 6, 7], help="kclique: clique size")
     ap.add_argument("--fmm-precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        # one process per GPU: start the ranks here (replicas, see the multi-GPU notes)
+        import socket
+        sk = socket.socket()
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+        sk.close()
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+        sys.exit(subprocess.call(cmd))
+    if world != args.gpus:
+        print(json.dumps({"error": f"--gpus {args.gpus} but WORLD_SIZE={world}: launch one rank per GPU"}), flush=True)
+        sys.exit(2)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serve":
@@ -907,6 +1387,14 @@ def main():
         run_fmm(args)
     elif args.workload == "kclique":
         run_kclique(args)
+    elif args.workload == "fib":
+        run_fib(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "sched":
+        run_sched(args)
+    elif args.workload == "micro":
+        run_micro(args)
     else:
         run_gpu(args)
 
