@@ -68,6 +68,8 @@ def _load():
                 "orc_direct": (None, [i64, P, P, P, i64, P]),
                 "orc_taylor": (i32, [i32, f64, f64, f64, P]),
                 "orc_bintree": (u64, [i32, i32, i32, i32, P]),
+                "orc_fib_cutoff": (i64, [i32, i32, P]),
+                "orc_nqueens_cutoff": (u64, [i32, i32, P]),
                 "orc_bintree_leaf": (u64, [u64, i32, i32]),
             }
             for name, (res, args) in sigs.items():
@@ -91,6 +93,20 @@ def fib(n: int):
     t = ctypes.c_uint64(0)
     v = _load().orc_fib(n, ctypes.byref(t))
     return int(v), int(t.value)
+
+
+def fib_cutoff(n: int, cutoff: int):
+    """(fib(n), tasks) when calls below the cutoff run serially inside one leaf task."""
+    t = ctypes.c_uint64(0)
+    v = _load().orc_fib_cutoff(n, cutoff, ctypes.byref(t))
+    return int(v), int(t.value)
+
+
+def nqueens_cutoff(n: int, depth: int):
+    """(solutions, tasks) when boards with `depth` rows placed finish their search serially."""
+    t = ctypes.c_uint64(0)
+    s = _load().orc_nqueens_cutoff(n, depth, ctypes.byref(t))
+    return int(s), int(t.value)
 
 
 def nqueens(n: int, algorithm: str = "bitmask"):

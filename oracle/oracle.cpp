@@ -65,6 +65,24 @@ int64_t orc_fib(int n, uint64_t* tasks) {
     return v;
 }
 
+// Fibonacci with a sequential cutoff (Sec. 6.3.2, the DAQ experiment): a call
+// with n >= cutoff (and n >= 2) is a task that forks its two calls; a call
+// with n below the cutoff is a leaf task that computes fib(n) by the plain
+// serial recursion.  The value is unchanged; the task count is the number of
+// calls with n >= cutoff plus the leaf calls they make.
+static int64_t fib_serial(int n) { return n < 2 ? n : fib_serial(n - 1) + fib_serial(n - 2); }
+static int64_t fib_cut(int n, int cutoff, uint64_t* tasks) {
+    ++*tasks;
+    if (n < 2 || n < cutoff) return fib_serial(n);
+    return fib_cut(n - 1, cutoff, tasks) + fib_cut(n - 2, cutoff, tasks);
+}
+int64_t orc_fib_cutoff(int n, int cutoff, uint64_t* tasks) {
+    uint64_t t = 0;
+    int64_t v = fib_cut(n, cutoff, &t);
+    if (tasks) *tasks = t;
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // N-Queens by bitmask backtracking (Sec. 6.3, "N-Queens"), one task per
 // placed row: the root is the empty board at row 0, and a task at row r
@@ -86,6 +104,39 @@ uint64_t orc_nqueens_bitmask(int n, uint64_t* nodes) {
     uint64_t s = 0, t = 0;
     nq_bits(n, 0, 0, 0, 0, &s, &t);
     if (nodes) *nodes = t;
+    return s;
+}
+
+// N-Queens with a cutoff depth (Sec. 6.3.1 uses depth 7): a board with fewer
+// than `depth` rows placed is a task that forks one child per legal placement
+// in the next row; a board with `depth` rows placed (or a complete board) is a
+// leaf task that finishes the search serially.  Tasks = boards with at most
+// `depth` rows placed.
+static uint64_t nq_serial(int n, int row, uint32_t cols, uint32_t dl, uint32_t dr) {
+    if (row == n) return 1;
+    uint64_t s = 0;
+    const uint32_t full = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    for (uint32_t avail = ~(cols | dl | dr) & full; avail; avail &= avail - 1) {
+        uint32_t bit = avail & (0u - avail);
+        s += nq_serial(n, row + 1, cols | bit, (dl | bit) << 1, (dr | bit) >> 1);
+    }
+    return s;
+}
+static uint64_t nq_cut(int n, int depth, int row, uint32_t cols, uint32_t dl, uint32_t dr, uint64_t* tasks) {
+    ++*tasks;
+    if (row == n || row >= depth) return nq_serial(n, row, cols, dl, dr);
+    uint64_t s = 0;
+    const uint32_t full = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    for (uint32_t avail = ~(cols | dl | dr) & full; avail; avail &= avail - 1) {
+        uint32_t bit = avail & (0u - avail);
+        s += nq_cut(n, depth, row + 1, cols | bit, (dl | bit) << 1, (dr | bit) >> 1, tasks);
+    }
+    return s;
+}
+uint64_t orc_nqueens_cutoff(int n, int depth, uint64_t* tasks) {
+    uint64_t t = 0;
+    uint64_t s = nq_cut(n, depth, 0, 0, 0, 0, &t);
+    if (tasks) *tasks = t;
     return s;
 }
 

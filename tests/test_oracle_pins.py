@@ -71,7 +71,42 @@ def test_fib_binet():
         assert oracle.fib(n)[0] == round(phi ** n / 5 ** 0.5)
 
 
+def test_fib_cutoff_value_and_task_count_closed_form():
+    # calls below the cutoff c >= 2 are leaf tasks: T(n) = 1 for n < c, else 1 + T(n-1) + T(n-2),
+    # so T(n) + 1 follows the Fibonacci recurrence from T(c-2) + 1 = T(c-1) + 1 = 2:
+    # T(n) = 2 F(n - c + 3) - 1 for n >= c - 2
+    for c in range(2, 12):
+        for n in range(max(0, c - 2), 28):
+            v, t = oracle.fib_cutoff(n, c)
+            assert v == _fib_fast_doubling(n)
+            assert t == 2 * _fib_fast_doubling(n - c + 3) - 1, (n, c)
+    # cutoff 0, 1 and 2 are the no-cutoff program
+    for c in (0, 1, 2):
+        assert oracle.fib_cutoff(25, c) == oracle.fib(25)
+
+
 # --------------------------------------------------------------------------- n-queens
+def _partial_placements_rows(n, rows):
+    # brute force: valid placements of r queens in rows 0..r-1, for each r <= rows
+    total = 0
+    for r in range(min(rows, n) + 1):
+        for cols in permutations(range(n), r):
+            if all(abs(cols[i] - cols[j]) != j - i for i in range(r) for j in range(i + 1, r)):
+                total += 1
+    return total
+
+
+def test_nqueens_cutoff_solutions_and_task_count():
+    # the solutions do not depend on the cutoff; the tasks are the boards with at most
+    # `depth` rows placed (brute-force count of partial placements)
+    for n in range(1, 9):
+        for depth in range(0, n + 2):
+            s, t = oracle.nqueens_cutoff(n, depth)
+            assert s == oracle.nqueens(n)[0]
+            assert t == _partial_placements_rows(n, depth), (n, depth)
+    assert oracle.nqueens_cutoff(11, 30) == oracle.nqueens(11)
+
+
 def test_nqueens_published_counts():
     for n, sols in _read_golden("nqueens_solutions.txt"):
         n, sols = int(n), int(sols)
