@@ -69,6 +69,7 @@ def _load():
                 "orc_taylor": (i32, [i32, f64, f64, f64, P]),
                 "orc_bintree": (u64, [i32, i32, i32, i32, P]),
                 "orc_fib_cutoff": (i64, [i32, i32, P]),
+                "orc_cilksort": (u64, [P, P, u64, u64, u64]),
                 "orc_nqueens_cutoff": (u64, [i32, i32, P]),
                 "orc_bintree_leaf": (u64, [u64, i32, i32]),
             }
@@ -153,6 +154,14 @@ def sort_u32(keys: np.ndarray) -> np.ndarray:
     out = np.empty_like(keys)
     _load().orc_sort_u32(_ptr(keys), _ptr(out), keys.size)
     return out
+
+
+def cilksort(keys: np.ndarray, sort_cutoff: int = 64, merge_cutoff: int = 256):
+    """(sorted keys, tasks) of the thread-mode Cilksort recursion."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    out = np.empty_like(keys)
+    t = _load().orc_cilksort(_ptr(keys), _ptr(out), keys.size, sort_cutoff, merge_cutoff)
+    return out, int(t)
 
 
 def integrate_thread(a: float, b: float, eps: float):

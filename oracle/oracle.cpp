@@ -18,7 +18,7 @@
 // multiply-add, so floating-point programs round at every operation).
 //
 // Parity status per routine (see tests/test_oracle_pins.py):
-//   fib, nqueens, uts, sort, integrate, kclique, bintree: pinned.
+//   fib, nqueens, uts, sort, cilksort, integrate, kclique, bintree: pinned.
 //   fmm: pinned against the direct O(N^2) sum (exact regime and convergence).
 
 #include <algorithm>
@@ -235,6 +235,71 @@ void orc_uts_bfs(uint64_t seed, uint32_t root_children, uint32_t m, uint64_t thr
 void orc_sort_u32(const uint32_t* in, uint32_t* out, uint64_t n) {
     std::memcpy(out, in, n * sizeof(uint32_t));
     std::sort(out, out + n);
+}
+
+// Thread-mode Cilksort (Sec. 6.3, "Cilksort parallelizes merging"; Sec.
+// 6.3.2 runs it with three DAQ queues: recursive, serial-sort and
+// serial-merge tasks).  sort(range, into): a range of at most sort_cutoff keys
+// is a leaf task that sorts it serially into buffer `into`; a larger range
+// forks its two halves into the other buffer and then merges them into `into`.
+// merge(A, B -> out): at most merge_cutoff outputs is a leaf task that merges
+// serially; otherwise the longer run's middle element x is written straight
+// to its final place (after the keys of A before it and the keys of B less
+// than x), and the two sub-merges on either side of it are forked, so each
+// has fewer outputs than its parent.  The sorted output is whatever a correct
+// sort gives; the task count is that of this recursion.
+struct CilkState { std::vector<uint32_t> buf[2]; const uint32_t* src; uint64_t sort_cut, merge_cut, tasks; };
+
+static void cilk_merge(CilkState& st, int from, uint64_t a0, uint64_t a1, uint64_t b0, uint64_t b1, uint64_t out) {
+    ++st.tasks;
+    const std::vector<uint32_t>& X = st.buf[from];
+    std::vector<uint32_t>& Y = st.buf[1 - from];
+    uint64_t na = a1 - a0, nb = b1 - b0;
+    if (na + nb <= st.merge_cut) {
+        // plain two-finger merge
+        uint64_t i = a0, j = b0, k = out;
+        while (i < a1 && j < b1) Y[k++] = (X[j] < X[i]) ? X[j++] : X[i++];
+        while (i < a1) Y[k++] = X[i++];
+        while (j < b1) Y[k++] = X[j++];
+        return;
+    }
+    if (na < nb) { std::swap(a0, b0); std::swap(a1, b1); std::swap(na, nb); }
+    const uint64_t ma = a0 + na / 2;
+    const uint32_t x = X[ma];
+    // first position of the shorter run whose key is not less than x
+    const uint64_t mb = (uint64_t)(std::lower_bound(X.begin() + b0, X.begin() + b1, x) - X.begin());
+    const uint64_t at = out + (ma - a0) + (mb - b0);
+    Y[at] = x;
+    cilk_merge(st, from, a0, ma, b0, mb, out);
+    cilk_merge(st, from, ma + 1, a1, mb, b1, at + 1);
+}
+
+static void cilk_sort(CilkState& st, uint64_t lo, uint64_t hi, int into) {
+    ++st.tasks;
+    if (hi - lo <= st.sort_cut) {
+        std::vector<uint32_t> part(st.src + lo, st.src + hi);
+        std::sort(part.begin(), part.end());
+        std::copy(part.begin(), part.end(), st.buf[into].begin() + lo);
+        return;
+    }
+    const uint64_t mid = lo + (hi - lo) / 2;
+    cilk_sort(st, lo, mid, 1 - into);
+    cilk_sort(st, mid, hi, 1 - into);
+    cilk_merge(st, 1 - into, lo, mid, mid, hi, lo);
+}
+
+// Sorts in[0, n) into out; returns the number of tasks the recursion creates.
+uint64_t orc_cilksort(const uint32_t* in, uint32_t* out, uint64_t n, uint64_t sort_cutoff, uint64_t merge_cutoff) {
+    CilkState st;
+    st.buf[0].assign(n, 0);
+    st.buf[1].assign(n, 0);
+    st.src = in;
+    st.sort_cut = sort_cutoff < 1 ? 1 : sort_cutoff;
+    st.merge_cut = merge_cutoff < 1 ? 1 : merge_cutoff;
+    st.tasks = 0;
+    if (n > 0) cilk_sort(st, 0, n, 0);
+    std::copy(st.buf[0].begin(), st.buf[0].end(), out);
+    return st.tasks;
 }
 
 // ---------------------------------------------------------------------------

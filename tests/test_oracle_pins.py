@@ -221,6 +221,36 @@ def test_sort_is_sorted_permutation():
 
 
 # --------------------------------------------------------------------------- integrate
+def test_cilksort_sorts_and_counts_tasks():
+    rng = np.random.default_rng(5)
+    for n, sc, mc in [(0, 64, 256), (1, 64, 256), (63, 64, 256), (1000, 64, 256), (4096, 16, 32), (77777, 64, 256)]:
+        keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+        if n > 10:
+            keys[: n // 10] = keys[0]          # duplicates
+        out, tasks = oracle.cilksort(keys, sc, mc)
+        assert np.array_equal(out, np.sort(keys))
+        if n == 0:
+            assert tasks == 0
+    # merges never split (merge cutoff >= n): the tasks are the sort recursion's 2L - 1
+    # nodes (L leaves of <= sort_cutoff keys; n = 2^k * c splits into 2^k leaves) plus one
+    # merge per inner node
+    for k, c in [(0, 64), (3, 64), (6, 50)]:
+        n = (2 ** k) * c
+        _, tasks = oracle.cilksort(np.arange(n, dtype=np.uint32)[::-1].copy(), c, n)
+        assert tasks == (2 ** (k + 1) - 1) + (2 ** k - 1)
+    # merge cutoff 1: every merge task with more outputs places one key and forks two
+    # smaller merges, so the merge tasks form a binary tree with one split task per key
+    # placed: two leaves of one key (sort tasks 3) merge through 1 split + 2 leaf tasks
+    for keys in ([3, 1], [1, 3], [2, 2]):
+        out, tasks = oracle.cilksort(np.array(keys, dtype=np.uint32), 1, 1)
+        assert list(out) == sorted(keys) and tasks == 3 + 3
+    # every split task places one key and the leaves place the rest
+    for n in (5, 64, 999):
+        keys = rng.integers(0, 50, n, dtype=np.uint64).astype(np.uint32)
+        out, _ = oracle.cilksort(keys, 1, 1)
+        assert np.array_equal(out, np.sort(keys))
+
+
 def test_integrate_close_to_closed_form():
     exact = 0.4 * math.atan(5.0)   # integral of 1/(1+25x^2) over [-1, 1]
     v, t = oracle.integrate_thread(-1.0, 1.0, 1e-10)
