@@ -153,7 +153,7 @@ gtap_status gtap_arena_bytes(gtap_mode mode, int n_queues, size_t frame_pool_byt
 /* Select a built-in task program by name and get its type ID for
  * gtap_spawn_root (the programs of Sec. 6, written as the continuation state
  * machines Sec. 5.2 lowers tasks into).  Thread mode: "fib", "nqueens", "uts",
- * "kclique", "integrate", "bintree".  Block mode: "mergesort",
+ * "kclique", "integrate", "bintree", "cilksort".  Block mode: "mergesort",
  * "integrate_block", "fmm_dtt", "bintree_block".
  * Errors: GTAP_ERR_INVALID_ARG for an unknown name or the wrong mode. */
 gtap_status gtap_register_task(gtap_ctx* ctx, const char* program, int* out_type);
@@ -283,13 +283,18 @@ gtap_status gtap_finalize(gtap_ctx* ctx);
  * program semantics, Sec. 4.2).
  * ---------------------------------------------------------------------- */
 
-/* fib(n), no cutoff (Sec. 6.3).  Result: int64 fib(n).
- * route 1: recursive calls -> q0, leaves (n < 2) -> q1, continuations -> q2 (mod n_queues). */
-typedef struct { int32_t n; int32_t route; } gtap_fib_args;
+/* fib(n) (Sec. 6.3).  cutoff 0 (or <= 2): a task at every call.  cutoff c > 2:
+ * a call with n < c is a leaf task that computes fib(n) by the serial
+ * recursion in its lane (Sec. 6.3.2).  Result: int64 fib(n).
+ * route 1: recursive calls -> q0, leaves -> q1, continuations -> q2 (mod n_queues). */
+typedef struct { int32_t n; int32_t route; int32_t cutoff; int32_t pad; } gtap_fib_args;
 
-/* N-Queens by bitmask backtracking, one task per placed row (Sec. 6.3).
- * Result: uint64 solution count.  route 1: queue = depth mod n_queues. */
-typedef struct { int32_t n; int32_t route; } gtap_nqueens_args;
+/* N-Queens by bitmask backtracking (Sec. 6.3).  cutoff 0: one task per placed
+ * row; cutoff d > 0: a board with d rows placed is a leaf task that finishes
+ * the search serially (Sec. 6.3.1 uses d = 7).  Result: uint64 solution count.
+ * route 1: queue = depth mod n_queues; route 2: recursive tasks -> q0, cutoff
+ * leaves -> q1 (Sec. 6.3.2, two queues). */
+typedef struct { int32_t n; int32_t route; int32_t cutoff; int32_t pad; } gtap_nqueens_args;
 
 /* Unbalanced hashed tree: root id splitmix64(seed), root_children children at
  * the root, m children below iff splitmix64(v ^ 0xD1B54A32D192ED03) < threshold.
@@ -319,6 +324,19 @@ typedef struct { double a; double b; double eps; } gtap_integrate_args;
  * a node c levels above the leaves run its whole subtree as one task (thread
  * mode requires cutoff 0).  depth <= 30. */
 typedef struct { int32_t depth; int32_t iters; int32_t K; int32_t route; int32_t cutoff; int32_t pad; } gtap_bintree_args;
+
+/* Thread-mode Cilksort ("cilksort", Sec. 6.3; Sec. 6.3.2 runs it with three
+ * DAQ queues) of n < 2^32 uint32 keys from src (device, read only) into dst
+ * (device); tmp (device, n keys) is scratch; src may equal dst.  A range of at
+ * most sort_cutoff (<= 256, default 64) keys is a leaf task whose lane sorts it
+ * alone; a larger range sorts its halves into the other buffer and then merges
+ * them back.  A merge of at most merge_cutoff (default 256) outputs is a leaf
+ * task merging serially; a larger merge writes the longer run's middle key x
+ * to its final place and forks the merges on either side of it (the shorter
+ * run cut at its first key not less than x).  route 1: recursive tasks -> q0,
+ * serial sorts -> q1, serial merges -> q2.  Result: none (8 zero bytes). */
+typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; uint32_t sort_cutoff;
+                 uint32_t merge_cutoff; int32_t route; int32_t pad; } gtap_cilksort_args;
 
 /* Block-mode mergesort (Cilksort with a forked parallel merge, Sec. 6.3) of
  * n uint32 keys from src (device, read only) into dst (device); tmp (device,

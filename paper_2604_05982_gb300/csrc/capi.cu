@@ -36,6 +36,7 @@ const ProgInfo kPrograms[] = {
     {"integrate_block", GTAP_MODE_BLOCK, T_INTEGRATE_BLK, PS_INTEGRATE_BLK},
     {"fmm_dtt", GTAP_MODE_BLOCK, T_DTT, PS_DTT},
     {"bintree", GTAP_MODE_THREAD, T_BINTREE, PS_BINTREE},
+    {"cilksort", GTAP_MODE_THREAD, T_TSORT, PS_CILKSORT},
     {"bintree_block", GTAP_MODE_BLOCK, T_BINTREE_BLK, PS_BINTREE_BLK},
 };
 
@@ -383,8 +384,8 @@ static gtap_status make_root(gtap_ctx* c, int type, const void* args, size_t nby
         if (nbytes != sizeof(gtap_fib_args)) return GTAP_ERR_INVALID_ARG;
         gtap_fib_args a;
         std::memcpy(&a, args, sizeof(a));
-        if (a.n < 0 || a.n > 92) return GTAP_ERR_INVALID_ARG;
-        int32_t p[2] = {a.n, a.route ? 1 : 0};
+        if (a.n < 0 || a.n > 92 || a.cutoff < 0 || a.cutoff > 63) return GTAP_ERR_INVALID_ARG;
+        int32_t p[2] = {a.n, (a.route ? 1 : 0) | (a.cutoff << 8)};
         put(p, sizeof(p));
         return GTAP_OK;
     }
@@ -392,8 +393,10 @@ static gtap_status make_root(gtap_ctx* c, int type, const void* args, size_t nby
         if (nbytes != sizeof(gtap_nqueens_args)) return GTAP_ERR_INVALID_ARG;
         gtap_nqueens_args a;
         std::memcpy(&a, args, sizeof(a));
-        if (a.n < 1 || a.n > 16) return GTAP_ERR_INVALID_ARG;
-        uint32_t p[8] = {0, 0, 0, (uint32_t)(0 | (a.n << 8) | ((a.route ? 1 : 0) << 16)), 0, 0, 0, 0};
+        if (a.n < 1 || a.n > 16 || a.route < 0 || a.route > 2 || a.cutoff < 0 || a.cutoff > 16)
+            return GTAP_ERR_INVALID_ARG;
+        uint32_t p[8] = {0, 0, 0, (uint32_t)(0 | (a.n << 8) | ((uint32_t)a.route << 16) | ((uint32_t)a.cutoff << 24)),
+                         0, 0, 0, 0};
         put(p, sizeof(p));
         return GTAP_OK;
     }
@@ -448,6 +451,20 @@ static gtap_status make_root(gtap_ctx* c, int type, const void* args, size_t nby
             1ull, 0u, (uint32_t)a.depth, (uint32_t)a.iters,
             (uint32_t)a.K | ((a.route ? 1u : 0u) << 8) | ((uint32_t)a.cutoff << 16), 0ull};
         put(&p, sizeof(p));
+        return GTAP_OK;
+    }
+    case T_TSORT: {
+        if (nbytes != sizeof(gtap_cilksort_args)) return GTAP_ERR_INVALID_ARG;
+        gtap_cilksort_args a;
+        std::memcpy(&a, args, sizeof(a));
+        if (a.sort_cutoff == 0) a.sort_cutoff = 64;
+        if (a.merge_cutoff == 0) a.merge_cutoff = 256;
+        if (a.n >= (1ull << 32) || a.sort_cutoff > 256 || a.merge_cutoff < 1 ||
+            (a.n > 0 && (!a.src || !a.dst || !a.tmp)))
+            return GTAP_ERR_INVALID_ARG;
+        struct { uint32_t root, into, lo, hi; } p{root_index, 0u, 0u, (uint32_t)a.n};
+        put(&p, sizeof(p));
+        std::memcpy(d->env, &a, sizeof(a));
         return GTAP_OK;
     }
     case T_INTEGRATE_BLK: {

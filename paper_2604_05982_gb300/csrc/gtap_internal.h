@@ -31,6 +31,8 @@ enum ProgType : int {
     T_KCLIQUE_EDGE = 7,  // one edge / a sub-range of a candidate set
     T_KCLIQUE_SET = 8,
     T_BINTREE = 9,       // full binary tree microbenchmark (Sec. 6.1, 6.2)
+    T_TSORT = 10,        // thread-mode Cilksort: sort a range
+    T_TMERGE = 11,       // thread-mode Cilksort: merge two runs
     // block mode
     T_MSORT = 16,
     T_MMERGE = 17,
@@ -48,7 +50,8 @@ enum ProgSet : unsigned {
     PS_INTEGRATE = 1u << 3,
     PS_KCLIQUE = 1u << 4,
     PS_BINTREE = 1u << 5,
-    PS_THREAD_ALL = PS_FIB | PS_NQUEENS | PS_UTS | PS_INTEGRATE | PS_KCLIQUE | PS_BINTREE,
+    PS_CILKSORT = 1u << 6,
+    PS_THREAD_ALL = PS_FIB | PS_NQUEENS | PS_UTS | PS_INTEGRATE | PS_KCLIQUE | PS_BINTREE | PS_CILKSORT,
     PS_MSORT = 1u << 8,
     PS_INTEGRATE_BLK = 1u << 9,
     PS_DTT = 1u << 10,

@@ -34,6 +34,12 @@ struct ThreadDispatch {
         case T_BINTREE:
             if constexpr ((PSET & PS_BINTREE) != 0) { bintree_step(c); return; }
             break;
+        case T_TSORT:
+            if constexpr ((PSET & PS_CILKSORT) != 0) { cilksort_sort_step(c); return; }
+            break;
+        case T_TMERGE:
+            if constexpr ((PSET & PS_CILKSORT) != 0) { cilksort_merge_step(c); return; }
+            break;
         default:
             break;
         }
@@ -62,7 +68,8 @@ __global__ void __launch_bounds__(256, thread_min_blocks<PSET>()) thread_kernel(
 // the scheduler-bound microbenchmark programs.
 #define GTAP_THREAD_SETS(X)                                                                                       \
     X(PS_FIB, SCHED_BATCHED) X(PS_NQUEENS, SCHED_BATCHED) X(PS_UTS, SCHED_BATCHED) X(PS_INTEGRATE, SCHED_BATCHED) \
-    X(PS_KCLIQUE, SCHED_BATCHED) X(PS_BINTREE, SCHED_BATCHED) X(PS_THREAD_ALL, SCHED_BATCHED)                     \
+    X(PS_KCLIQUE, SCHED_BATCHED) X(PS_BINTREE, SCHED_BATCHED) X(PS_CILKSORT, SCHED_BATCHED)                       \
+    X(PS_THREAD_ALL, SCHED_BATCHED)                                                                               \
     X(PS_FIB, SCHED_GLOBAL) X(PS_FIB, SCHED_SINGLE) X(PS_UTS, SCHED_GLOBAL) X(PS_UTS, SCHED_SINGLE)               \
     X(PS_BINTREE, SCHED_GLOBAL) X(PS_BINTREE, SCHED_SINGLE)
 
@@ -74,7 +81,7 @@ static const void* thread_kernel_fn(unsigned pset, int sched) {
 }
 
 unsigned thread_kernel_pset(unsigned registered) {
-    const unsigned singles[] = {PS_FIB, PS_NQUEENS, PS_UTS, PS_INTEGRATE, PS_KCLIQUE, PS_BINTREE};
+    const unsigned singles[] = {PS_FIB, PS_NQUEENS, PS_UTS, PS_INTEGRATE, PS_KCLIQUE, PS_BINTREE, PS_CILKSORT};
     for (unsigned s : singles)
         if (registered != 0 && (registered & ~s) == 0) return s;
     return PS_THREAD_ALL;
@@ -88,6 +95,7 @@ int thread_kernel_maxspawn(unsigned pset) {
     if (pset & PS_INTEGRATE) m = max(m, 2);
     if (pset & PS_KCLIQUE) m = max(m, kKcFan);
     if (pset & PS_BINTREE) m = max(m, 2);
+    if (pset & PS_CILKSORT) m = max(m, 2);
     return m;
 }
 

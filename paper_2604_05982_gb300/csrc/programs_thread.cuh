@@ -9,19 +9,39 @@
 namespace gtap {
 
 // ---------------------------------------------------------------------------
-// fib(n) with a task at every call (Sec. 6.3 "Fibonacci").
-// record: [16] n, route  [24] l  [32] r
-struct FibSpawn { int32_t n; int32_t route; };
+// fib(n) with a task at every call (Sec. 6.3 "Fibonacci"), or with a
+// sequential cutoff (Sec. 6.3.2): a call with n below the cutoff is a leaf
+// task that computes fib(n) by the serial recursion inside its lane.
+// record: [16] n, route | cutoff << 8  [24] l  [32] r
+struct FibSpawn { int32_t n; int32_t rc; };
 constexpr uint32_t kFibSlotL = 3, kFibSlotR = 4;
+
+// The serial recursion fib(n) = fib(n-1) + fib(n-2) with an explicit stack of
+// pending calls (n < 64, so at most n + 1 entries).
+__device__ __forceinline__ long long fib_serial(int n) {
+    int stack[64];
+    int sp = 0;
+    long long acc = 0;
+    stack[sp++] = n;
+    while (sp > 0) {
+        const int m = stack[--sp];
+        if (m < 2) { acc += m; continue; }
+        stack[sp++] = m - 1;
+        stack[sp++] = m - 2;
+    }
+    return acc;
+}
 
 __device__ __forceinline__ void fib_step(TaskCtx& c) {
     const FibSpawn a = c.load<FibSpawn>();
+    const int route = a.rc & 0xFF, cutoff = a.rc >> 8;
     // route 1 (DAQ with three queues, Sec. 6.3.2): recursive calls, leaves, continuations
-    const int qrec = 0, qleaf = a.route ? 1 : 0, qcont = a.route ? 2 : 0;
+    const int qrec = 0, qleaf = route ? 1 : 0, qcont = route ? 2 : 0;
     if (c.pc() == 0) {
-        if (a.n < 2) { c.ret((unsigned long long)(long long)a.n); return; }
-        c.spawn(T_FIB, kFibSlotL, (a.n - 1 >= 2) ? qrec : qleaf, FibSpawn{a.n - 1, a.route});
-        c.spawn(T_FIB, kFibSlotR, (a.n - 2 >= 2) ? qrec : qleaf, FibSpawn{a.n - 2, a.route});
+        if (a.n < 2 || a.n < cutoff) { c.ret((unsigned long long)fib_serial(a.n)); return; }
+        const int n1 = a.n - 1, n2 = a.n - 2;
+        c.spawn(T_FIB, kFibSlotL, (n1 >= 2 && n1 >= cutoff) ? qrec : qleaf, FibSpawn{n1, a.rc});
+        c.spawn(T_FIB, kFibSlotR, (n2 >= 2 && n2 >= cutoff) ? qrec : qleaf, FibSpawn{n2, a.rc});
         c.join(1, qcont);
     } else {
         const long long l = (long long)c.word<kFibSlotL>();
@@ -31,28 +51,56 @@ __device__ __forceinline__ void fib_step(TaskCtx& c) {
 }
 
 // ---------------------------------------------------------------------------
-// N-Queens by bitmask backtracking, one task per placed row (Sec. 6.3).
-// record: [16] cols, diag_l, diag_r, row|n<<8|route<<16  [32] acc (u64, children add into it)
+// N-Queens by bitmask backtracking, one task per placed row (Sec. 6.3), or
+// with a cutoff depth (Sec. 6.3.1): a board with `depth` rows placed is a leaf
+// task that finishes the search serially in its lane.
+// record: [16] cols, diag_l, diag_r, row | n << 8 | route << 16 | depth << 24  [32] acc (u64, children add into it)
 struct NqSpawn { uint32_t cols, dl, dr, meta; unsigned long long acc; unsigned long long pad; };
 constexpr uint32_t kNqSlotAcc = 4;
+
+// Serial backtracking from a partial board: one (cols, dl, dr, remaining
+// candidates) frame per placed row, at most 16 rows.
+__device__ __forceinline__ unsigned long long nq_serial(int n, int row, uint32_t cols, uint32_t dl, uint32_t dr) {
+    if (row == n) return 1ull;
+    const uint32_t full = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    uint32_t sc[17], sl[17], sr[17], sa[17];
+    int top = 0;
+    sc[0] = cols; sl[0] = dl; sr[0] = dr; sa[0] = ~(cols | dl | dr) & full;
+    unsigned long long sols = 0;
+    const int rows_left = n - row;
+    while (top >= 0) {
+        const uint32_t avail = sa[top];
+        if (avail == 0) { --top; continue; }
+        const uint32_t bit = avail & (0u - avail);
+        sa[top] = avail ^ bit;
+        if (top + 1 == rows_left) { ++sols; continue; }
+        const uint32_t c2 = sc[top] | bit, l2 = (sl[top] | bit) << 1, r2 = (sr[top] | bit) >> 1;
+        ++top;
+        sc[top] = c2; sl[top] = l2; sr[top] = r2; sa[top] = ~(c2 | l2 | r2) & full;
+    }
+    return sols;
+}
 
 __device__ __forceinline__ void nqueens_step(TaskCtx& c) {
     if (c.pc() == 0) {
         const uint4 a = c.load<uint4>();
-        const int row = (int)(a.w & 0xFF), n = (int)((a.w >> 8) & 0xFF), route = (int)(a.w >> 16);
+        const int row = (int)(a.w & 0xFF), n = (int)((a.w >> 8) & 0xFF), route = (int)((a.w >> 16) & 0xFF);
+        const int depth = (int)(a.w >> 24);
         if (row == n) { c.ret(1ull); return; }
+        if (depth > 0 && row >= depth) { c.ret(nq_serial(n, row, a.x, a.y, a.z)); return; }
         const uint32_t full = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
         uint32_t avail = ~(a.x | a.y | a.z) & full;
         if (avail == 0) { c.ret(0ull); return; }
-        const uint32_t meta = (uint32_t)(row + 1) | ((uint32_t)n << 8) | ((uint32_t)route << 16);
-        const int qchild = route ? (row + 1) : 0;  // DAQ: queue = depth mod n_queues
+        const uint32_t meta = (uint32_t)(row + 1) | (a.w & 0xFFFFFF00u);
+        // DAQ: route 1 = queue depth mod n_queues; route 2 = recursive tasks q0, cutoff leaves q1
+        const int qchild = route == 1 ? (row + 1) : (route == 2 ? ((depth > 0 && row + 1 >= depth) ? 1 : 0) : 0);
         while (avail) {
             const uint32_t bit = avail & (0u - avail);
             avail ^= bit;
             NqSpawn s{a.x | bit, (a.y | bit) << 1, (a.z | bit) >> 1, meta, 0ull, 0ull};
             c.spawn(T_NQUEENS, kNqSlotAcc, qchild, s, kFlagAccumulate);
         }
-        c.join(1, route ? row : 0);
+        c.join(1, route == 1 ? row : 0);
     } else {
         c.ret(c.word<kNqSlotAcc>());
     }
@@ -446,6 +494,103 @@ static __device__ void kclique_set_step(TaskCtx& c) {
     }
     st_cg64(c.frame + kKcSetLocal, local);
     c.join(1, kc_queue(e, depth));
+}
+
+}  // namespace gtap
+
+namespace gtap {
+
+// ---------------------------------------------------------------------------
+// Thread-mode Cilksort (Sec. 6.3: sort halves in parallel and merge with a
+// forked parallel merge; Sec. 6.3.2 routes recursive, serial-sort and
+// serial-merge tasks to three DAQ queues).  One lane is one task, so a leaf
+// sorts or merges its keys alone (these lanes touch unrelated data: the
+// accesses of a warp are not coalesced, the structural cost the paper names).
+// Buffers: 0 = dst, 1 = tmp; sort leaves read src.
+// Records:  TSORT  [16] root, into  [24] lo, hi (u32)
+//           TMERGE [16] root, from  [24] a0, a1, b0, b1  [40] out
+struct CsSortSpawn { uint32_t root, into, lo, hi; };
+struct CsMergeSpawn { uint32_t root, from, a0, a1, b0, b1, out, pad; };
+constexpr uint32_t kCsSlot = 7;       // void results: accumulate 0, nothing written
+constexpr int kCsMaxSortCut = 256;
+
+__device__ __forceinline__ gtap_cilksort_args cs_env(const KParams& P, uint32_t root) {
+    return P.serving ? ld_obj<gtap_cilksort_args>(P.root_desc[root].env)
+                     : ld_obj_ro<gtap_cilksort_args>(P.root_desc[root].env);
+}
+__device__ __forceinline__ uint32_t* cs_buf(const gtap_cilksort_args& e, uint32_t b) { return b ? e.tmp : e.dst; }
+__device__ __forceinline__ int cs_queue(const gtap_cilksort_args& e, int kind) { return e.route ? kind : 0; }
+
+__device__ __forceinline__ void cs_merge_spawn(TaskCtx& c, const gtap_cilksort_args& e, uint32_t root, uint32_t from,
+                                               uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1, uint32_t out) {
+    const bool leaf = (a1 - a0) + (b1 - b0) <= e.merge_cutoff;
+    c.spawn(T_TMERGE, kCsSlot, cs_queue(e, leaf ? 2 : 0), CsMergeSpawn{root, from, a0, a1, b0, b1, out, 0u},
+            kFlagAccumulate);
+}
+
+__device__ __forceinline__ void cilksort_sort_step(TaskCtx& c) {
+    const CsSortSpawn a = c.load<CsSortSpawn>();
+    const gtap_cilksort_args e = cs_env(c.P, a.root);
+    const uint32_t n = a.hi - a.lo, mid = a.lo + n / 2;
+    if (c.pc() == 0) {
+        if (n <= e.sort_cutoff) {
+            // serial leaf: insertion sort of the range in the lane's local memory
+            uint32_t k[kCsMaxSortCut];
+            for (uint32_t i = 0; i < n; ++i) {
+                const uint32_t x = __ldcg(e.src + a.lo + i);
+                uint32_t j = i;
+                while (j > 0 && k[j - 1] > x) { k[j] = k[j - 1]; --j; }
+                k[j] = x;
+            }
+            uint32_t* out = cs_buf(e, a.into) + a.lo;
+            for (uint32_t i = 0; i < n; ++i) __stcg(out + i, k[i]);
+            c.ret(0ull);
+            return;
+        }
+        const uint32_t other = 1u - a.into;
+        const uint32_t h0 = mid - a.lo, h1 = a.hi - mid;
+        c.spawn(T_TSORT, kCsSlot, cs_queue(e, h0 <= e.sort_cutoff ? 1 : 0), CsSortSpawn{a.root, other, a.lo, mid}, kFlagAccumulate);
+        c.spawn(T_TSORT, kCsSlot, cs_queue(e, h1 <= e.sort_cutoff ? 1 : 0), CsSortSpawn{a.root, other, mid, a.hi}, kFlagAccumulate);
+        c.join(1, 0);
+    } else if (c.pc() == 1) {
+        // the halves are sorted in the other buffer: merge them back into this task's buffer
+        cs_merge_spawn(c, e, a.root, 1u - a.into, a.lo, mid, mid, a.hi, a.lo);
+        c.join(2, 0);
+    } else {
+        c.ret(0ull);
+    }
+}
+
+__device__ __forceinline__ void cilksort_merge_step(TaskCtx& c) {
+    const CsMergeSpawn a = c.load<CsMergeSpawn>();
+    if (c.pc() != 0) { c.ret(0ull); return; }
+    const gtap_cilksort_args e = cs_env(c.P, a.root);
+    const uint32_t* X = cs_buf(e, a.from);
+    uint32_t* Y = cs_buf(e, 1u - a.from);
+    uint32_t a0 = a.a0, a1 = a.a1, b0 = a.b0, b1 = a.b1;
+    if ((a1 - a0) + (b1 - b0) <= e.merge_cutoff) {
+        // serial leaf: two-finger merge
+        uint32_t i = a0, j = b0, k = a.out;
+        uint32_t x = i < a1 ? __ldcg(X + i) : 0u, y = j < b1 ? __ldcg(X + j) : 0u;
+        while (i < a1 && j < b1) {
+            if (y < x) { __stcg(Y + k++, y); if (++j < b1) y = __ldcg(X + j); }
+            else { __stcg(Y + k++, x); if (++i < a1) x = __ldcg(X + i); }
+        }
+        for (; i < a1; ++i) __stcg(Y + k++, __ldcg(X + i));
+        for (; j < b1; ++j) __stcg(Y + k++, __ldcg(X + j));
+        c.ret(0ull);
+        return;
+    }
+    if (a1 - a0 < b1 - b0) { uint32_t t = a0; a0 = b0; b0 = t; t = a1; a1 = b1; b1 = t; }
+    const uint32_t ma = a0 + (a1 - a0) / 2;
+    const uint32_t x = __ldcg(X + ma);
+    uint32_t lo = b0, hi = b1;   // first position of B whose key is not less than x
+    while (lo < hi) { const uint32_t m = lo + (hi - lo) / 2; if (__ldcg(X + m) < x) lo = m + 1; else hi = m; }
+    const uint32_t at = a.out + (ma - a0) + (lo - b0);
+    __stcg(Y + at, x);
+    cs_merge_spawn(c, e, a.root, a.from, a0, ma, b0, lo, a.out);
+    cs_merge_spawn(c, e, a.root, a.from, ma + 1, a1, lo, b1, at + 1);
+    c.join(1, 0);
 }
 
 }  // namespace gtap

@@ -64,11 +64,11 @@ class gtap_error_info(ctypes.Structure):
 
 
 class gtap_fib_args(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int32), ("route", ctypes.c_int32)]
+    _fields_ = [("n", ctypes.c_int32), ("route", ctypes.c_int32), ("cutoff", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class gtap_nqueens_args(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int32), ("route", ctypes.c_int32)]
+    _fields_ = [("n", ctypes.c_int32), ("route", ctypes.c_int32), ("cutoff", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class gtap_uts_args(ctypes.Structure):
@@ -89,6 +89,12 @@ class gtap_kclique_args(ctypes.Structure):
 class gtap_bintree_args(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int32), ("iters", ctypes.c_int32), ("K", ctypes.c_int32), ("route", ctypes.c_int32),
                 ("cutoff", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class gtap_cilksort_args(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("tmp", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("sort_cutoff", ctypes.c_uint32), ("merge_cutoff", ctypes.c_uint32), ("route", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class gtap_mergesort_args(ctypes.Structure):

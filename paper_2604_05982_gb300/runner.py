@@ -84,20 +84,20 @@ class Context:
         self.close()
 
 
-def fib(ns, n_queues: int = 1, route: int = 0, **cfg) -> RunResult:
+def fib(ns, n_queues: int = 1, route: int = 0, cutoff: int = 0, **cfg) -> RunResult:
     ns = [ns] if isinstance(ns, int) else list(ns)
     with Context(G.GTAP_MODE_THREAD, n_queues, **cfg) as c:
         t = c.register("fib")
-        hs = [c.spawn(t, G.gtap_fib_args(n, route)) for n in ns]
+        hs = [c.spawn(t, G.gtap_fib_args(n, route, cutoff, 0)) for n in ns]
         c.run()
         return RunResult([c.result_i64(h) for h in hs], c.stats())
 
 
-def nqueens(ns, n_queues: int = 1, route: int = 0, **cfg) -> RunResult:
+def nqueens(ns, n_queues: int = 1, route: int = 0, cutoff: int = 0, **cfg) -> RunResult:
     ns = [ns] if isinstance(ns, int) else list(ns)
     with Context(G.GTAP_MODE_THREAD, n_queues, **cfg) as c:
         t = c.register("nqueens")
-        hs = [c.spawn(t, G.gtap_nqueens_args(n, route)) for n in ns]
+        hs = [c.spawn(t, G.gtap_nqueens_args(n, route, cutoff, 0)) for n in ns]
         c.run()
         return RunResult([c.result_u64(h) for h in hs], c.stats())
 
@@ -139,6 +139,16 @@ def mergesort_ptrs(src: int, dst: int, tmp: int, n: int, leaf: int = 4096, merge
     with Context(G.GTAP_MODE_BLOCK, 1, pool_bytes=256 << 20, **cfg) as c:
         t = c.register("mergesort")
         c.spawn(t, G.gtap_mergesort_args(src, dst, tmp, n, leaf, merge_cutoff))
+        c.run()
+        return RunResult([], c.stats())
+
+
+def cilksort_ptrs(src: int, dst: int, tmp: int, n: int, sort_cutoff: int = 64, merge_cutoff: int = 256,
+                  n_queues: int = 1, route: int = 0, **cfg) -> RunResult:
+    """Thread-mode Cilksort of n uint32 keys at device address src into dst (tmp: n-key scratch)."""
+    with Context(G.GTAP_MODE_THREAD, n_queues, **cfg) as c:
+        t = c.register("cilksort")
+        c.spawn(t, G.gtap_cilksort_args(src, dst, tmp, n, sort_cutoff, merge_cutoff, route, 0))
         c.run()
         return RunResult([], c.stats())
 

@@ -27,19 +27,22 @@ def main(argv=None):
     ap.add_argument("--K", type=int, default=1, help="bintree: leaf compute functions")
     ap.add_argument("--block", type=int, default=0, help="bintree: 1 block mode")
     ap.add_argument("--grid", type=int, default=0, help="explicit grid size (0: the default)")
+    ap.add_argument("--cutoff", type=int, default=0, help="fib / nqueens: sequential cutoff (0: none)")
+    ap.add_argument("--sub", type=int, default=0, help="mergesort: log2 keys per independent sort (0: one sort)")
     args = ap.parse_args(argv)
 
-    from paper_2604_05982_gb300 import gtap as G  # noqa: F401
+    from paper_2604_05982_gb300 import gtap as G
     from paper_2604_05982_gb300 import inputs, runner
     geo = {"grid_blocks": args.grid} if args.grid else {}
 
     if args.case == "fib":
         for _ in range(args.reps):
-            r = runner.fib(args.n or 30, n_queues=args.queues, route=args.route, scheduler=args.sched, **geo)
+            r = runner.fib(args.n or 30, n_queues=args.queues, route=args.route, cutoff=args.cutoff,
+                           scheduler=args.sched, **geo)
             print("fib", r.values, r.stats["kernel_ms"])
     elif args.case == "nqueens":
         for _ in range(args.reps):
-            r = runner.nqueens(args.n or 13, n_queues=args.queues, route=args.route, **geo)
+            r = runner.nqueens(args.n or 13, n_queues=args.queues, route=args.route, cutoff=args.cutoff, **geo)
             print("nqueens", r.values, r.stats["kernel_ms"])
     elif args.case == "tree":
         for _ in range(args.reps):
@@ -55,11 +58,19 @@ def main(argv=None):
         dst = torch.empty_like(src)
         tmp = torch.empty_like(src)
         torch.cuda.synchronize()
+        sub = (1 << args.sub) if args.sub else n      # independent sorts of `sub` keys, one root each
         for _ in range(args.reps):
-            r = runner.mergesort_ptrs(src.data_ptr(), dst.data_ptr(), tmp.data_ptr(), n, merge_cutoff=65536)
-            print("mergesort", n, r.stats["kernel_ms"])
-        out = dst.cpu().numpy().view(np.uint32)
-        assert np.all(out[1:] >= out[:-1])
+            with runner.Context(G.GTAP_MODE_BLOCK, 1, pool_bytes=256 << 20, max_roots=max(4096, n // sub),
+                                blocks_per_sm=3, **geo) as c:
+                t = c.register("mergesort")
+                for r0 in range(0, n, sub):
+                    o = r0 * 4
+                    c.spawn(t, G.gtap_mergesort_args(src.data_ptr() + o, dst.data_ptr() + o, tmp.data_ptr() + o,
+                                                     sub, 4096, 65536))
+                c.run()
+                print("mergesort", n, sub, c.stats()["kernel_ms"])
+        out = dst.cpu().numpy().view(np.uint32).reshape(-1, sub)
+        assert np.all(out[:, 1:] >= out[:, :-1])
     elif args.case == "kclique":
         n, e = inputs.rmat_graph(args.n or 16, 16, seed=7)
         g = runner.DeviceGraph(n, e)

@@ -40,6 +40,28 @@ def test_fib_daq(q, route):
     assert r.values == [oracle.fib(27)[0]]
 
 
+@pytest.mark.parametrize("cutoff", [3, 10, 18])
+@pytest.mark.parametrize("q,route", [(1, 0), (3, 1)])
+def test_fib_sequential_cutoff(cutoff, q, route):
+    # calls below the cutoff run the serial recursion in their lane (Sec. 6.3.2);
+    # DAQ routes recursive calls, cutoff leaves and continuations to three queues
+    for n in (0, 1, 2, cutoff - 1, cutoff, 27):
+        want, tasks = oracle.fib_cutoff(n, cutoff)
+        r = runner.fib(n, n_queues=q, route=route, cutoff=cutoff)
+        assert r.values == [want], n
+        assert r.stats["tasks_created"] == tasks
+
+
+@pytest.mark.parametrize("depth", [1, 4, 7, 13])
+@pytest.mark.parametrize("q,route", [(1, 0), (2, 2), (4, 1)])
+def test_nqueens_cutoff_depth(depth, q, route):
+    # boards with `depth` rows placed finish their search serially (Sec. 6.3.1 uses 7)
+    sols, tasks = oracle.nqueens_cutoff(13, depth)
+    r = runner.nqueens(13, n_queues=q, route=route, cutoff=depth)
+    assert r.values == [sols] == [73712]
+    assert r.stats["tasks_created"] == tasks
+
+
 @pytest.mark.parametrize("n", list(range(1, 12)))
 def test_nqueens_small(n):
     r = runner.nqueens(n)
@@ -129,3 +151,27 @@ def test_graph_replay_same_results_and_reset():
         h2 = c.spawn(t, G.gtap_nqueens_args(8, 1))
         c.run()
         assert c.result_u64(h2) == 92 and c.result_u64(hs[1]) == 352
+
+
+@pytest.mark.parametrize("n,sc,mc", [(1, 64, 256), (64, 64, 256), (1000, 64, 256), (100_003, 64, 256),
+                                     (1 << 20, 64, 256), (50_000, 16, 1), (77_777, 256, 4096)])
+@pytest.mark.parametrize("q,route", [(1, 0), (3, 1)])
+def test_cilksort_thread_mode(n, sc, mc, q, route):
+    # thread-mode Cilksort (Sec. 6.3), DAQ with recursive / serial-sort / serial-merge queues
+    import numpy as np
+    import torch
+    from paper_2604_05982_gb300 import inputs
+    keys = inputs.keys_u32(n, seed=7)
+    keys[: n // 7] = keys[0]        # runs of equal keys
+    src = torch.from_numpy(keys.view(np.int32)).cuda()
+    dst = torch.full_like(src, -1)
+    tmp = torch.empty_like(src)
+    torch.cuda.synchronize()
+    r = runner.cilksort_ptrs(src.data_ptr(), dst.data_ptr(), tmp.data_ptr(), n, sc, mc, n_queues=q, route=route,
+                             pool_bytes=1 << 30)
+    want, tasks = oracle.cilksort(keys, sc, mc)
+    assert np.array_equal(dst.cpu().numpy().view(np.uint32), want)
+    assert r.stats["tasks_created"] == tasks
+    # in place (src == dst)
+    runner.cilksort_ptrs(src.data_ptr(), src.data_ptr(), tmp.data_ptr(), n, sc, mc, pool_bytes=1 << 30)
+    assert np.array_equal(src.cpu().numpy().view(np.uint32), want)

@@ -48,7 +48,9 @@ def test_struct_layouts_match_header(lib_path, tmp_path):
     # sizes and field offsets as the C compiler lays out include/gtap.h
     structs = {"gtap_config": G.gtap_config, "gtap_stats": G.gtap_stats, "gtap_error_info": G.gtap_error_info,
                "gtap_kclique_args": G.gtap_kclique_args, "gtap_uts_args": G.gtap_uts_args,
-               "gtap_mergesort_args": G.gtap_mergesort_args}
+               "gtap_mergesort_args": G.gtap_mergesort_args, "gtap_fib_args": G.gtap_fib_args,
+               "gtap_nqueens_args": G.gtap_nqueens_args, "gtap_bintree_args": G.gtap_bintree_args,
+               "gtap_integrate_args": G.gtap_integrate_args}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gtap.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
@@ -64,7 +66,7 @@ def test_struct_layouts_match_header(lib_path, tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
-    assert ctypes.sizeof(G.gtap_fib_args) == 8
+    assert ctypes.sizeof(G.gtap_fib_args) == 16
     assert ctypes.sizeof(G.gtap_uts_args) == 32
     assert ctypes.sizeof(G.gtap_mergesort_args) == 40
     assert ctypes.sizeof(G.gtap_integrate_args) == 24
