@@ -18,7 +18,7 @@ constexpr uint32_t kFibSlotL = 3, kFibSlotR = 4;
 
 // The serial recursion fib(n) = fib(n-1) + fib(n-2) with an explicit stack of
 // pending calls (n < 64, so at most n + 1 entries).
-__device__ __forceinline__ long long fib_serial(int n) {
+static __device__ __noinline__ long long fib_serial(int n) {
     int stack[64];
     int sp = 0;
     long long acc = 0;
@@ -60,7 +60,7 @@ constexpr uint32_t kNqSlotAcc = 4;
 
 // Serial backtracking from a partial board: one (cols, dl, dr, remaining
 // candidates) frame per placed row, at most 16 rows.
-__device__ __forceinline__ unsigned long long nq_serial(int n, int row, uint32_t cols, uint32_t dl, uint32_t dr) {
+static __device__ __noinline__ unsigned long long nq_serial(int n, int row, uint32_t cols, uint32_t dl, uint32_t dr) {
     if (row == n) return 1ull;
     const uint32_t full = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
     uint32_t sc[17], sl[17], sr[17], sa[17];

@@ -10,6 +10,8 @@ Files (one ``key value`` or ``range lo hi count`` record per line):
   (a, b, c) = (0.57, 0.19, 0.19), seed 7, oriented by (degree, id).  The DAG
   edges [0, m) are cut into 64 contiguous ranges of (nearly) equal length; the
   file holds the count of each range and their sum, the whole graph's count.
+* ``kclique_rmat20_k{K}_sampled.txt``: for k whose whole-graph count is out of
+  the oracle's reach, ranges of a few DAG edges at evenly spaced starts.
 * ``kclique_batch64_k4.txt``: the 64-graph batch, graph i of scale
   12 + floor(7 i / 64) and seed 7 + i, one 4-clique count per graph.
 
@@ -18,6 +20,7 @@ sub-ranges (or graphs) over worker processes and adds the integer results.
 
     python tests/golden/make_kclique_goldens.py rmat20 --k 4 --workers 8
     python tests/golden/make_kclique_goldens.py batch64 --workers 8
+    python tests/golden/make_kclique_goldens.py rmat20 --k 6 --sample 256 --width 4 --workers 8
 """
 from __future__ import annotations
 
@@ -110,6 +113,39 @@ def make_rmat20(k: int, workers: int, out: str):
     print(f"total {total} ({time.perf_counter() - t0:.0f} s wall)")
 
 
+def sampled_ranges(m: int, n_ranges: int, width: int):
+    """n_ranges ranges of `width` DAG edges at evenly spaced starts over [0, m)."""
+    return [(i * (m // n_ranges), min(m, i * (m // n_ranges) + width)) for i in range(n_ranges)]
+
+
+def make_rmat20_sampled(k: int, workers: int, n_ranges: int, width: int, out: str):
+    from paper_2604_05982_gb300 import inputs
+    n, e = inputs.rmat_graph(20, 16, seed=7)
+    m = len(e)
+    ranges = sampled_ranges(m, n_ranges, width)
+    ctx = mp.get_context("spawn")
+    counts = [0] * len(ranges)
+    t0 = time.perf_counter()
+    cpu = 0.0
+    with ctx.Pool(workers, initializer=_init_rmat, initargs=(20, 7)) as pool:
+        jobs = [(r, lo, hi, k) for r, (lo, hi) in enumerate(ranges)]
+        for done, (r, c, secs) in enumerate(pool.imap_unordered(_count_range, jobs, chunksize=1)):
+            counts[r] = c
+            cpu += secs
+            if done % 32 == 0:
+                print(f"  {done}/{len(jobs)} ranges, {time.perf_counter() - t0:.0f} s", flush=True)
+    with open(out, "w") as f:
+        f.write(f"# {k}-clique counts of sampled DAG-edge ranges of the R-MAT graph scale 20, edge factor 16,\n")
+        f.write("# a/b/c 0.57/0.19/0.19, seed 7, oriented by (degree, id) (Sec. 6.4.2): the whole graph's count\n")
+        f.write(f"# is out of the oracle's reach at this k, so {n_ranges} ranges of {width} edges at evenly spaced\n")
+        f.write(f"# starts.  Written by tests/golden/make_kclique_goldens.py from the CPU oracle only "
+                f"({cpu:.0f} s of oracle time).\n")
+        f.write(f"n {n}\nm {m}\nk {k}\n")
+        for (lo, hi), c in zip(ranges, counts):
+            f.write(f"range {lo} {hi} {c}\n")
+    print(f"done ({time.perf_counter() - t0:.0f} s wall)")
+
+
 def make_batch64(k: int, workers: int, out: str):
     ctx = mp.get_context("spawn")
     rows = [None] * 64
@@ -152,8 +188,13 @@ def main():
     ap.add_argument("what", choices=["rmat20", "batch64"])
     ap.add_argument("--k", type=int, default=4)
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--sample", type=int, default=0, help="rmat20: sampled ranges instead of the whole graph")
+    ap.add_argument("--width", type=int, default=4, help="rmat20 --sample: DAG edges per range")
     a = ap.parse_args()
-    if a.what == "rmat20":
+    if a.what == "rmat20" and a.sample:
+        make_rmat20_sampled(a.k, a.workers, a.sample, a.width,
+                            os.path.join(HERE, f"kclique_rmat20_k{a.k}_sampled.txt"))
+    elif a.what == "rmat20":
         make_rmat20(a.k, a.workers, os.path.join(HERE, f"kclique_rmat20_k{a.k}.txt"))
     else:
         make_batch64(a.k, a.workers, os.path.join(HERE, f"kclique_batch64_k{a.k}.txt"))

@@ -139,6 +139,19 @@ def test_scale20_full_count_and_64_ranges_match_oracle_golden(rmat20, k):
     assert r.values == [c for _, _, c in gold["ranges"]]
 
 
+@pytest.mark.parametrize("k", [6, 7])
+def test_scale20_sampled_ranges_match_oracle_golden(rmat20, k):
+    # k = 6, 7: the whole-graph count is out of the oracle's reach, so sampled ranges of
+    # DAG edges (evenly spaced over the graph) as roots of one launch
+    gold, _ = _golden(f"kclique_rmat20_k{k}_sampled.txt")
+    n, e, g = rmat20
+    assert (gold["n"], gold["m"]) == (n, g.m)
+    ranges = [(lo, hi) for lo, hi, _ in gold["ranges"]]
+    r = runner.kclique([g] * len(ranges), k, split_threshold=64, ranges=ranges, n_queues=4, route=1,
+                       scratch_bytes=4 << 30, deque_capacity=16384)
+    assert r.values == [c for _, _, c in gold["ranges"]]
+
+
 def test_batch64_one_launch_matches_oracle_golden():
     # 64 R-MAT graphs of scales 12..18 (graph i: scale 12 + floor(7i/64), seed 7 + i)
     # in one persistent launch, each count against the oracle's
