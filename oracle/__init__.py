@@ -70,6 +70,7 @@ def _load():
                 "orc_bintree": (u64, [i32, i32, i32, i32, P]),
                 "orc_fib_cutoff": (i64, [i32, i32, P]),
                 "orc_cilksort": (u64, [P, P, u64, u64, u64]),
+                "orc_kclique_pivot": (u64, [i64, P, i64, i32, i64, i64, P]),
                 "orc_nqueens_cutoff": (u64, [i32, i32, P]),
                 "orc_bintree_leaf": (u64, [u64, i32, i32]),
             }
@@ -184,6 +185,15 @@ def kclique(n: int, edges: np.ndarray, k: int, order: str = "degree", per_edge: 
     total = _load().orc_kclique(n, _ptr(edges), m, k, {"degree": 0, "id": 1}[order],
                                 _ptr(pe) if pe is not None else None)
     return (int(total), pe[:m]) if per_edge else int(total)
+
+
+def kclique_pivot(n: int, edges: np.ndarray, k: int, lo: int = 0, hi: int | None = None):
+    """(k-clique count, recursion nodes) by pivoting over DAG edges [lo, hi) (all by default)."""
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    m = edges.shape[0]
+    nodes = ctypes.c_uint64(0)
+    c = _load().orc_kclique_pivot(n, _ptr(edges), m, k, lo, m if hi is None else hi, ctypes.byref(nodes))
+    return int(c), int(nodes.value)
 
 
 def orient(n: int, edges: np.ndarray, order: str = "degree"):

@@ -18,7 +18,7 @@
 // multiply-add, so floating-point programs round at every operation).
 //
 // Parity status per routine (see tests/test_oracle_pins.py):
-//   fib, nqueens, uts, sort, cilksort, integrate, kclique, bintree: pinned.
+//   fib, nqueens, uts, sort, cilksort, integrate, kclique (orientation and pivoting), bintree: pinned.
 //   fmm: pinned against the direct O(N^2) sum (exact regime and convergence).
 
 #include <algorithm>
@@ -480,6 +480,93 @@ uint64_t orc_kclique_dag_ranges(int64_t n, const int64_t* off, const int32_t* ad
             else if ((int)C.size() >= k - 2) total += count_in(g, C, k - 2);
         }
     }
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// k-clique counting by pivoting (Sec. 6.4.2, the second algorithm of the
+// k-clique study; Jain and Seshadhri's succinct clique tree).  For every DAG
+// edge (u, v) the candidate set is S = N+(u) n N+(v) with u and v "held".
+// A node (S, h held, p pivots) with S empty is a leaf and stands for the
+// cliques made of its held vertices plus any subset of its pivots: it adds
+// C(p, k - h) k-cliques.  Otherwise the pivot x is the vertex of S with the
+// most neighbours inside S (ties: the smallest id); the branches are the
+// vertices w of S not adjacent to x (x itself first among them, in S's order);
+// branch i recurses on S n N(w_i) minus the earlier branch vertices, with w_i
+// counted as a pivot when it is x and as held otherwise.  N is the undirected
+// neighbourhood.  Every k-clique is counted once; the recursion depth is
+// bounded by the pivots, so the search is shallow compared with orientation.
+static uint64_t binom_u64(uint64_t n, int r) {
+    if (r < 0 || (uint64_t)r > n) return 0;
+    unsigned __int128 c = 1;
+    for (int i = 1; i <= r; ++i) c = c * (n - (uint64_t)r + (uint64_t)i) / (uint64_t)i;
+    return (uint64_t)c;
+}
+
+struct UndirectedCsr { std::vector<int64_t> off; std::vector<int32_t> adj; };
+
+static UndirectedCsr undirected(int64_t n, const int32_t* edges, int64_t m) {
+    UndirectedCsr g;
+    g.off.assign(n + 1, 0);
+    for (int64_t e = 0; e < m; ++e) { ++g.off[edges[2 * e] + 1]; ++g.off[edges[2 * e + 1] + 1]; }
+    for (int64_t v = 0; v < n; ++v) g.off[v + 1] += g.off[v];
+    g.adj.assign(2 * m, 0);
+    std::vector<int64_t> fill(g.off.begin(), g.off.end() - 1);
+    for (int64_t e = 0; e < m; ++e) {
+        g.adj[fill[edges[2 * e]]++] = edges[2 * e + 1];
+        g.adj[fill[edges[2 * e + 1]]++] = edges[2 * e];
+    }
+    for (int64_t v = 0; v < n; ++v) std::sort(g.adj.begin() + g.off[v], g.adj.begin() + g.off[v + 1]);
+    return g;
+}
+
+static uint64_t pivot_count(const UndirectedCsr& g, const std::vector<int32_t>& S, int h, int p, int k,
+                            uint64_t* nodes) {
+    ++*nodes;
+    if (h > k) return 0;
+    if (S.empty()) return binom_u64((uint64_t)p, k - h);
+    // the pivot: most neighbours inside S, the smallest id on ties (S is sorted by id)
+    int32_t x = S[0];
+    size_t best = 0;
+    bool first = true;
+    for (int32_t y : S) {
+        std::vector<int32_t> t = intersect(g.adj.data() + g.off[y], g.off[y + 1] - g.off[y], S.data(), (int64_t)S.size());
+        if (first || t.size() > best) { best = t.size(); x = y; first = false; }
+    }
+    std::vector<int32_t> nx = intersect(g.adj.data() + g.off[x], g.off[x + 1] - g.off[x], S.data(), (int64_t)S.size());
+    // branch vertices: x, then the vertices of S not adjacent to x, in S's order
+    std::vector<int32_t> branch{x};
+    for (int32_t y : S)
+        if (y != x && !std::binary_search(nx.begin(), nx.end(), y)) branch.push_back(y);
+    uint64_t total = 0;
+    std::vector<int32_t> done;   // earlier branch vertices, kept sorted
+    for (int32_t w : branch) {
+        std::vector<int32_t> nw = intersect(g.adj.data() + g.off[w], g.off[w + 1] - g.off[w], S.data(), (int64_t)S.size());
+        std::vector<int32_t> Sw;
+        std::set_difference(nw.begin(), nw.end(), done.begin(), done.end(), std::back_inserter(Sw));
+        total += (w == x) ? pivot_count(g, Sw, h, p + 1, k, nodes) : pivot_count(g, Sw, h + 1, p, k, nodes);
+        done.insert(std::upper_bound(done.begin(), done.end(), w), w);
+    }
+    return total;
+}
+
+// Total k-clique count by pivoting over the DAG edges [lo, hi) of the
+// (degree, id) orientation (all edges: lo = 0, hi = m); *nodes (optional)
+// receives the number of recursion nodes.
+uint64_t orc_kclique_pivot(int64_t n, const int32_t* edges, int64_t m, int k, int64_t lo, int64_t hi, uint64_t* nodes) {
+    if (k < 3) return 0;
+    Dag d = orient(n, edges, m, 0);
+    UndirectedCsr g = undirected(n, edges, m);
+    uint64_t total = 0, nd = 0;
+    int64_t u = 0;
+    for (int64_t e = lo; e < hi && e < m; ++e) {
+        while (d.off[u + 1] <= e) ++u;
+        const int32_t v = d.adj[e];
+        std::vector<int32_t> C = intersect(d.adj.data() + d.off[u], d.off[u + 1] - d.off[u], d.adj.data() + d.off[v],
+                                           d.off[v + 1] - d.off[v]);
+        total += pivot_count(g, C, 2, 0, k, &nd);
+    }
+    if (nodes) *nodes = nd;
     return total;
 }
 

@@ -304,6 +304,35 @@ def test_kclique_multipartite():
         assert oracle.kclique(n, edges, k) == _ek(sizes, k)
 
 
+def test_kclique_pivoting_against_brute_force_and_closed_forms():
+    # pivoting is a second, independent counting algorithm: brute force on small random
+    # graphs, C(n, k) on complete graphs, e_k on complete multipartite graphs
+    for seed in range(4):
+        n, e = inputs.random_graph(22, 0.45, seed)
+        for k in (3, 4, 5, 6):
+            assert oracle.kclique_pivot(n, e, k)[0] == oracle.kclique_brute(n, e, k), (seed, k)
+    n = 30
+    e = np.array(list(combinations(range(n), 2)), dtype=np.int32)
+    for k in (3, 7, 12):
+        assert oracle.kclique_pivot(n, e, k)[0] == math.comb(n, k)
+    sizes = [3, 1, 4, 2, 5]
+    part = np.repeat(np.arange(len(sizes)), sizes)
+    nn = len(part)
+    edges = np.array([(i, j) for i, j in combinations(range(nn), 2) if part[i] != part[j]], dtype=np.int32)
+    for k in range(3, 6):
+        assert oracle.kclique_pivot(nn, edges, k)[0] == _ek(sizes, k)
+
+
+def test_kclique_pivoting_equals_orientation_on_rmat():
+    # the two algorithms agree on every k, whole graph and per DAG-edge range
+    n, e = inputs.rmat_graph(10, 16, seed=7)
+    m = len(e)
+    for k in (3, 4, 5, 6, 7):
+        assert oracle.kclique_pivot(n, e, k)[0] == oracle.kclique(n, e, k), k
+    for lo, hi in [(0, 100), (m // 2, m // 2 + 57), (m - 30, m)]:
+        assert oracle.kclique_pivot(n, e, 5, lo, hi)[0] == oracle.kclique_edge_range(n, e, 5, lo, hi)
+
+
 def test_kclique_triangles_trace():
     n, edges = inputs.random_graph(120, 0.2, 11)
     A = np.zeros((n, n), dtype=np.int64)
