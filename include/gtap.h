@@ -356,10 +356,22 @@ typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; 
  * range; smaller ones are counted in the lane with 64-bit bitsets.  A
  * first-level set is written by its own task when that task starts (waiting
  * first-level tasks hold no scratch); deeper sets by the task that spawns them.
- * route 1: queue = recursion depth mod n_queues.  k in [3, 16].  Result: uint64 count. */
+ * route 1: queue = recursion depth mod n_queues.  k in [3, 16].  Result: uint64 count.
+ *
+ * algorithm 1 (GTAP_KCLIQUE_PIVOT) counts by pivoting instead (Sec. 6.4.2, the
+ * second algorithm): candidate sets of at most split_threshold vertices are
+ * encoded as 64-bit adjacency rows in the lane and counted by a pivot search
+ * (the pivot is the vertex with the most neighbours in the set, ties to the
+ * lowest position; its non-neighbours and itself are the branches; an empty
+ * set adds C(pivots, vertices still to choose)); sets of up to 64 vertices are
+ * encoded as a bitset subgraph in the scratch arena and their branch range is
+ * split over child tasks ("bitset-encoded split"); larger sets branch on each
+ * member as in orientation until they fit 64 bits.  Same count either way. */
+#define GTAP_KCLIQUE_ORIENT 0
+#define GTAP_KCLIQUE_PIVOT 1
 typedef struct { const int64_t* off; const int32_t* adj; const int32_t* src;
                  int64_t edge_begin, edge_end;   /* the root counts DAG edges [edge_begin, edge_end) */
-                 int32_t k; int32_t split_threshold; int32_t route; int32_t pad; } gtap_kclique_args;
+                 int32_t k; int32_t split_threshold; int32_t route; int32_t algorithm; } gtap_kclique_args;
 
 /* Orient an undirected simple graph (each edge once, as m int32 pairs in edges,
  * device) by the order (degree, id): outputs off[n+1] (int64), adj[m] (out-lists

@@ -430,6 +430,7 @@ static gtap_status make_root(gtap_ctx* c, int type, const void* args, size_t nby
         std::memcpy(&a, args, sizeof(a));
         if (a.split_threshold == 0) a.split_threshold = 64;
         if (a.k < 3 || a.k > 16 || a.split_threshold < 2 || a.split_threshold > 64 || a.edge_begin < 0 ||
+            a.algorithm < 0 || a.algorithm > 1 ||
             a.edge_end < a.edge_begin || a.edge_end >= (1ll << 32) ||
             (a.edge_end > a.edge_begin && (!a.off || !a.adj || !a.src)))
             return GTAP_ERR_INVALID_ARG;

@@ -33,6 +33,7 @@ enum ProgType : int {
     T_BINTREE = 9,       // full binary tree microbenchmark (Sec. 6.1, 6.2)
     T_TSORT = 10,        // thread-mode Cilksort: sort a range
     T_TMERGE = 11,       // thread-mode Cilksort: merge two runs
+    T_KCLIQUE_PIV = 12,  // k-clique by pivoting: branch range of a bitset-encoded candidate subgraph
     // block mode
     T_MSORT = 16,
     T_MMERGE = 17,

@@ -377,6 +377,118 @@ static __device__ unsigned long long kc_count_small(const int* S, int ns, int j,
     return total;
 }
 
+// ---------------------------------------------------------------------------
+// Pivoting (Sec. 6.4.2, the second k-clique algorithm).  A candidate set of at
+// most 64 vertices is encoded as 64-bit adjacency rows: bit b of row a says
+// that members a and b are adjacent (in either direction of the DAG).  The
+// pivot search counts the cliques of the set that contain exactly r more
+// vertices: at a node (S, r still to choose, p pivots) the pivot x is the
+// member of S with the most neighbours in S (lowest position on ties); the
+// branches are x and the members of S not adjacent to x, in position order;
+// branch w recurses on S n N(w) without the earlier branch vertices, w counted
+// as a pivot when it is x and as chosen otherwise.  An empty S adds C(p, r);
+// r = 0 adds 1 (only the all-pivot path leads to a leaf); a node with fewer
+// than r members and pivots together adds nothing.
+struct LocalRows { const unsigned long long* r; __device__ unsigned long long operator()(int i) const { return r[i]; } };
+struct ScratchRows { const unsigned long long* r; __device__ unsigned long long operator()(int i) const { return __ldcg(r + i); } };
+
+__device__ __forceinline__ unsigned long long kp_binom(int n, int r) {
+    if (r < 0 || r > n) return 0ull;
+    unsigned long long c = 1;
+    for (int i = 1; i <= r; ++i) c = c * (unsigned long long)(n - r + i) / (unsigned long long)i;   // n <= 64, r <= 16
+    return c;
+}
+
+template <class R>
+__device__ __forceinline__ int kp_pivot(R row, unsigned long long S) {
+    int best = -1, bx = 0;
+    for (unsigned long long t = S; t; t &= t - 1) {
+        const int x = __ffsll((long long)t) - 1;
+        const int c = __popcll(row(x) & S);
+        if (c > best) { best = c; bx = x; }
+    }
+    return bx;
+}
+
+constexpr int kKpStack = 66;   // every child set is smaller than its parent's: depth <= 64 + 1
+
+template <class R>
+static __device__ __noinline__ unsigned long long kp_count(R row, unsigned long long S0, int r0, int p0) {
+    unsigned long long st_s[kKpStack], st_rem[kKpStack];
+    unsigned char st_r[kKpStack], st_p[kKpStack], st_x[kKpStack];
+    int top = -1;
+    unsigned long long total = 0;
+    auto enter = [&](unsigned long long S, int r, int p) {
+        if (r < 0) return;
+        if (r == 0) { total += 1; return; }
+        if (__popcll(S) + p < r) return;
+        if (S == 0) { total += kp_binom(p, r); return; }
+        const int x = kp_pivot(row, S);
+        ++top;
+        st_s[top] = S;
+        st_rem[top] = S & ~row(x);
+        st_r[top] = (unsigned char)r;
+        st_p[top] = (unsigned char)p;
+        st_x[top] = (unsigned char)x;
+    };
+    enter(S0, r0, p0);
+    while (top >= 0) {
+        const unsigned long long rem = st_rem[top];
+        if (rem == 0) { --top; continue; }
+        const int w = __ffsll((long long)rem) - 1;
+        st_rem[top] = rem & (rem - 1);
+        const unsigned long long branches = st_s[top] & ~row(st_x[top]);
+        const unsigned long long Sw = row(w) & st_s[top] & ~(branches & ((1ull << w) - 1ull));
+        if (w == (int)st_x[top]) enter(Sw, st_r[top], st_p[top] + 1);
+        else enter(Sw, st_r[top] - 1, st_p[top]);
+    }
+    return total;
+}
+
+// Adjacency rows of the candidate set S[0 .. ns) (ns <= 64, sorted by id), both
+// directions: each DAG edge inside S is found from its earlier endpoint's
+// out-list, then mirrored.
+static __device__ void kp_rows(const int* S, int ns, const int64_t* off, const int* adj, unsigned long long* row) {
+    for (int a = 0; a < ns; ++a) {
+        const long long b0 = (long long)__ldg(reinterpret_cast<const long long*>(off) + S[a]);
+        const int len = (int)((long long)__ldg(reinterpret_cast<const long long*>(off) + S[a] + 1) - b0);
+        const int* nb = adj + b0;
+        unsigned long long bits = 0;
+        int i = 0, b = 0;
+        if (len > 4 * ns) {
+            int lo = 0;
+            for (b = 0; b < ns && lo < len; ++b) {
+                const int x = S[b];
+                int hi = len;
+                while (lo < hi) { const int mid = (lo + hi) >> 1; if (__ldg(nb + mid) < x) lo = mid + 1; else hi = mid; }
+                if (lo < len && __ldg(nb + lo) == x) { bits |= 1ull << b; ++lo; }
+            }
+        } else {
+            while (i < len && b < ns) {
+                const int x = __ldg(nb + i), y = S[b];
+                if (x < y) ++i;
+                else if (y < x) ++b;
+                else { bits |= 1ull << b; ++i; ++b; }
+            }
+        }
+        row[a] = bits;
+    }
+    // mirror: adding the mirror of a mirrored bit changes nothing, so one pass in place is enough
+    for (int b = 0; b < ns; ++b)
+        for (unsigned long long t = row[b]; t; t &= t - 1) row[__ffsll((long long)t) - 1] |= 1ull << b;
+}
+
+// r-cliques of the candidate set S[0 .. ns) by the pivot search, in the lane.
+static __device__ __noinline__ unsigned long long kp_count_small(const int* S, int ns, int r, const int64_t* off,
+                                                                 const int* adj) {
+    if (r == 1) return (unsigned long long)ns;
+    if (ns < r) return 0;
+    unsigned long long row[kKcMaxThr];
+    kp_rows(S, ns, off, adj, row);
+    const unsigned long long full = (ns == 64) ? ~0ull : ((1ull << ns) - 1ull);
+    return kp_count(LocalRows{row}, full, r, 0);
+}
+
 // Candidate sets in the scratch arena: a set that fits one block is recycled
 // when the set task that owns it is done with it.
 __device__ __forceinline__ int* kc_scratch_alloc(TaskCtx& c, int n, bool* pooled) {
@@ -386,6 +498,84 @@ __device__ __forceinline__ int* kc_scratch_alloc(TaskCtx& c, int n, bool* pooled
 __device__ __forceinline__ int kc_queue(const gtap_kclique_args& e, int depth) { return e.route ? depth : 0; }
 __device__ __forceinline__ long long kc_off(const gtap_kclique_args& e, long long v) {
     return __ldg(reinterpret_cast<const long long*>(e.off) + v);
+}
+
+// Bitset-encoded split (Sec. 6.4.2, pivoting): a candidate set too heavy for
+// one lane (more than split_threshold members, at most 64) is encoded as its
+// adjacency rows in a recycled scratch block, and a task over its pivot's
+// branch range is forked; that task splits the range over child tasks (each
+// re-applies the test) or runs its branches itself.
+// Record: [16] root  [20] r:8 | p:8 | lo:8 | hi:8  [24] rows  [32] S  [40] branches (0: not chosen yet)
+//         [48] x:8 | own:8 | depth:8  [56] acc
+struct KpSpawn { uint32_t root, meta; unsigned long long rows, S, vp; uint32_t xo, pad; unsigned long long acc; };
+constexpr uint32_t kKpSlotAcc = 7;
+constexpr uint32_t kKpRows = 24, kKpBranches = 40, kKpXo = 48;
+
+__device__ __forceinline__ bool kp_spawn_split(TaskCtx& c, const gtap_kclique_args& e, uint32_t root, const int* S,
+                                               int ns, int r, int depth, uint32_t slot) {
+    unsigned long long row[kKcMaxThr];
+    kp_rows(S, ns, e.off, e.adj, row);
+    bool pooled;
+    unsigned long long* blk = reinterpret_cast<unsigned long long*>(scratch_alloc(c.P, (uint64_t)ns * 8, &pooled, c.type(), c.worker));
+    if (!blk) return false;
+    for (int a = 0; a < ns; ++a) __stcg(blk + a, row[a]);
+    const unsigned long long full = (ns == 64) ? ~0ull : ((1ull << ns) - 1ull);
+    c.spawn(T_KCLIQUE_PIV, slot, kc_queue(e, depth),
+            KpSpawn{root, (uint32_t)r | (255u << 24), (unsigned long long)blk, full, 0ull,
+                    (pooled ? 1u : 0u) << 8 | ((uint32_t)depth << 16), 0u, 0ull},
+            kFlagAccumulate);
+    return true;
+}
+
+static __device__ void kclique_piv_step(TaskCtx& c) {
+    const KpSpawn a = c.load<KpSpawn>();
+    const unsigned long long* rows = reinterpret_cast<const unsigned long long*>(a.rows);
+    const bool own = ((a.xo >> 8) & 0xFF) != 0;
+    if (c.pc() != 0) {
+        if (own) scratch_free(c.P, rows, c.type(), c.worker);
+        c.ret(a.acc);
+        return;
+    }
+    const gtap_kclique_args e = kc_env(c.P, a.root);
+    const ScratchRows row{rows};
+    const int r = (int)(a.meta & 0xFF), p = (int)((a.meta >> 8) & 0xFF);
+    const int depth = (int)((a.xo >> 16) & 0xFF);
+    unsigned long long vp = a.vp;
+    int x = (int)(a.xo & 0xFF);
+    if (vp == 0) {
+        // first run on this set: choose the pivot; the branches are x and its non-neighbours
+        x = kp_pivot(row, a.S);
+        vp = a.S & ~row(x);
+        st_cg64(c.frame + kKpBranches, vp);
+    }
+    const int nb = __popcll(vp);
+    const int lo = (int)((a.meta >> 16) & 0xFF), hi = min((int)(a.meta >> 24), nb);
+    if (hi - lo > kKcFan) {
+        const int per = (hi - lo + kKcFan - 1) / kKcFan;
+        for (int s0 = lo; s0 < hi; s0 += per)
+            c.spawn(T_KCLIQUE_PIV, kKpSlotAcc, kc_queue(e, depth + 1),
+                    KpSpawn{a.root, (uint32_t)r | ((uint32_t)p << 8) | ((uint32_t)s0 << 16) | ((uint32_t)min(hi, s0 + per) << 24),
+                            a.rows, a.S, vp, (uint32_t)x | ((uint32_t)(depth + 1) << 16), 0u, 0ull},
+                    kFlagAccumulate);
+        if (own) {
+            // the owner frees the rows once its children are done
+            st_cg64(c.frame + kKpXo, (unsigned long long)((uint32_t)x | (1u << 8) | ((uint32_t)depth << 16)));
+        }
+        c.join(1, kc_queue(e, depth));
+        return;
+    }
+    // branches lo .. hi-1 (in bit order) in this lane
+    unsigned long long total = 0;
+    unsigned long long t = vp;
+    for (int i = 0; i < lo; ++i) t &= t - 1;
+    for (int i = lo; i < hi; ++i) {
+        const int w = __ffsll((long long)t) - 1;
+        t &= t - 1;
+        const unsigned long long Sw = row(w) & a.S & ~(vp & ((1ull << w) - 1ull));
+        total += (w == x) ? kp_count(row, Sw, r, p + 1) : kp_count(row, Sw, r - 1, p);
+    }
+    if (own) scratch_free(c.P, rows, c.type(), c.worker);
+    c.ret(total);
 }
 
 static __device__ void kclique_range_step(TaskCtx& c) {
@@ -403,16 +593,24 @@ static __device__ void kclique_range_step(TaskCtx& c) {
     }
     const int thr = e.split_threshold;
     const int need = e.k - 2;
+    const bool pivot = e.algorithm == GTAP_KCLIQUE_PIVOT;
     unsigned long long local = 0;
     int C[kKcMaxThr];
     for (uint32_t ei = a.lo; ei < a.hi; ++ei) {
         const int u = __ldg(e.src + ei), v = __ldg(e.adj + ei);
         const long long ou = kc_off(e, u), ov = kc_off(e, v);
         const int nu = (int)(kc_off(e, u + 1) - ou), nv = (int)(kc_off(e, v + 1) - ov);
-        const int cn = kc_intersect(e.adj + ou, nu, AdjLoad{}, e.adj + ov, nv, AdjLoad{}, C, thr);
+        const int cn = kc_intersect(e.adj + ou, nu, AdjLoad{}, e.adj + ov, nv, AdjLoad{}, C, pivot ? kKcMaxThr : thr);
         if (need == 1) { local += (unsigned)cn; continue; }
         if (cn < need) continue;
-        if (cn <= thr) { local += kc_count_small(C, cn, need, e.off, e.adj); continue; }
+        if (cn <= thr) {
+            local += pivot ? kp_count_small(C, cn, need, e.off, e.adj) : kc_count_small(C, cn, need, e.off, e.adj);
+            continue;
+        }
+        if (pivot && cn <= kKcMaxThr) {
+            if (!kp_spawn_split(c, e, a.root, C, cn, need, 1, kKcRangeSlotAcc)) return;
+            continue;
+        }
         // the child materialises N+(u) n N+(v) when it runs and adds its count
         // into this range task's accumulator
         c.spawn(T_KCLIQUE_SET, kKcRangeSlotAcc, kc_queue(e, 1),
@@ -467,16 +665,24 @@ static __device__ void kclique_set_step(TaskCtx& c) {
     }
     const int thr = e.split_threshold;
     const int need = (int)a.j - 1;
+    const bool pivot = e.algorithm == GTAP_KCLIQUE_PIVOT;
     unsigned long long local = 0;
     int C[kKcMaxThr];
     for (uint32_t i = lo; i < hi; ++i) {
         const int w = __ldcg(set + i);
         const long long ow = kc_off(e, w);
         const int nw = (int)(kc_off(e, w + 1) - ow);
-        const int cn = kc_intersect(set, (int)len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, C, thr);
+        const int cn = kc_intersect(set, (int)len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, C, pivot ? kKcMaxThr : thr);
         if (need == 1) { local += (unsigned)cn; continue; }
         if (cn < need) continue;
-        if (cn <= thr) { local += kc_count_small(C, cn, need, e.off, e.adj); continue; }
+        if (cn <= thr) {
+            local += pivot ? kp_count_small(C, cn, need, e.off, e.adj) : kc_count_small(C, cn, need, e.off, e.adj);
+            continue;
+        }
+        if (pivot && cn <= kKcMaxThr) {
+            if (!kp_spawn_split(c, e, a.root, C, cn, need, depth + 1, kKcSetSlotAcc)) return;
+            continue;
+        }
         // deeper sets are materialised here, by the spawning lane (see the header)
         bool pooled;
         int* S = kc_scratch_alloc(c, cn, &pooled);

@@ -22,6 +22,8 @@ GTAP_STEAL_ONE = 4
 GTAP_SCHED_BATCHED = 0
 GTAP_SCHED_GLOBAL = 1
 GTAP_SCHED_SINGLE = 2
+GTAP_KCLIQUE_ORIENT = 0
+GTAP_KCLIQUE_PIVOT = 1
 
 STATUS = {
     0: "GTAP_OK", 1: "GTAP_ERR_INVALID_ARG", 2: "GTAP_ERR_NO_MEMORY", 3: "GTAP_ERR_POOL_EXHAUSTED",
@@ -83,7 +85,7 @@ class gtap_integrate_args(ctypes.Structure):
 class gtap_kclique_args(ctypes.Structure):
     _fields_ = [("off", ctypes.c_void_p), ("adj", ctypes.c_void_p), ("src", ctypes.c_void_p),
                 ("edge_begin", ctypes.c_int64), ("edge_end", ctypes.c_int64), ("k", ctypes.c_int32),
-                ("split_threshold", ctypes.c_int32), ("route", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("split_threshold", ctypes.c_int32), ("route", ctypes.c_int32), ("algorithm", ctypes.c_int32)]
 
 
 class gtap_bintree_args(ctypes.Structure):

@@ -171,21 +171,23 @@ class DeviceGraph:
         G.gtap_kclique_orient(e.data_ptr(), m, n, self.off.data_ptr(), self.adj.data_ptr(), self.src.data_ptr(),
                               self.work.data_ptr(), stream)
 
-    def args(self, k: int, split_threshold: int = 64, route: int = 0, begin: int = 0, end: int | None = None):
+    def args(self, k: int, split_threshold: int = 64, route: int = 0, begin: int = 0, end: int | None = None,
+             algorithm: int = 0):
         return G.gtap_kclique_args(self.off.data_ptr(), self.adj.data_ptr(), self.src.data_ptr(), begin,
-                                   self.m if end is None else end, k, split_threshold, route, 0)
+                                   self.m if end is None else end, k, split_threshold, route, algorithm)
 
 
 def kclique(graphs, k: int, split_threshold: int = 64, n_queues: int = 1, route: int = 0,
-            scratch_bytes: int = 1 << 30, ranges=None, **cfg) -> RunResult:
-    """Count k-cliques of one or more DeviceGraphs in one persistent launch (one root each)."""
+            scratch_bytes: int = 1 << 30, ranges=None, algorithm: int = 0, **cfg) -> RunResult:
+    """Count k-cliques of one or more DeviceGraphs in one persistent launch (one root each);
+    algorithm 0: orientation, 1: pivoting."""
     graphs = [graphs] if isinstance(graphs, DeviceGraph) else list(graphs)
     with Context(G.GTAP_MODE_THREAD, n_queues, scratch_bytes=scratch_bytes, **cfg) as c:
         t = c.register("kclique")
         hs = []
         for i, g in enumerate(graphs):
             b, e = (0, g.m) if ranges is None else ranges[i]
-            hs.append(c.spawn(t, g.args(k, split_threshold, route, b, e), queue=0))
+            hs.append(c.spawn(t, g.args(k, split_threshold, route, b, e, algorithm), queue=0))
         c.run()
         return RunResult([c.result_u64(h) for h in hs], c.stats())
 

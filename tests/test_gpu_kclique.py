@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_2604_05982_gb300 import gtap as G
 from paper_2604_05982_gb300 import inputs, runner
 
 pytestmark = pytest.mark.gpu
@@ -170,3 +171,46 @@ def test_batch64_one_launch_matches_oracle_golden():
     # the same instances one launch each give the same counts
     for i in (0, 31, 63):
         assert runner.kclique(graphs[i], 4, **cfg).values == [want[i]]
+
+
+# --------------------------------------------------------------------------- pivoting (Sec. 6.4.2)
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_pivoting_random_graphs_brute_force(k):
+    for seed in range(3):
+        n, e = inputs.random_graph(26, 0.5, seed)
+        want = oracle.kclique_brute(n, e, k)
+        assert runner.kclique(_graph(n, e), k, algorithm=G.GTAP_KCLIQUE_PIVOT).values == [want]
+
+
+def test_pivoting_complete_graph_all_paths():
+    # K_48 (sets up to 46 members), K_70 (sets beyond 64 branch orientation-style first);
+    # thresholds route the same sets through the lane, the bitset split and deeper splits
+    for n in (48, 70):
+        e = np.array(list(combinations(range(n), 2)), dtype=np.int32)
+        g = _graph(n, e)
+        for k, thr in [(4, 64), (5, 8), (6, 2), (7, 32), (9, 16)]:
+            r = runner.kclique(g, k, split_threshold=thr, algorithm=G.GTAP_KCLIQUE_PIVOT, scratch_bytes=1 << 30)
+            assert r.values == [math.comb(n, k)], (n, k, thr)
+
+
+@pytest.mark.parametrize("thr,q,route", [(64, 1, 0), (16, 1, 0), (4, 1, 0), (32, 4, 1)])
+def test_pivoting_rmat_against_both_oracles(thr, q, route):
+    n, e = inputs.rmat_graph(11, 16, seed=7)
+    g = _graph(n, e)
+    for k in (3, 4, 5, 7):
+        want = oracle.kclique(n, e, k)
+        assert oracle.kclique_pivot(n, e, k)[0] == want
+        r = runner.kclique(g, k, split_threshold=thr, n_queues=q, route=route, algorithm=G.GTAP_KCLIQUE_PIVOT)
+        assert r.values == [want], (k, thr, q)
+
+
+@pytest.mark.parametrize("k", [4, 6])
+def test_pivoting_scale20_golden_ranges(rmat20, k):
+    # the oracle's golden ranges (whole-graph partition for k = 4, sampled ranges for k = 6)
+    name = f"kclique_rmat20_k{k}.txt" if k == 4 else f"kclique_rmat20_k{k}_sampled.txt"
+    gold, _ = _golden(name)
+    n, e, g = rmat20
+    ranges = [(lo, hi) for lo, hi, _ in gold["ranges"]]
+    r = runner.kclique([g] * len(ranges), k, split_threshold=32, ranges=ranges, n_queues=4, route=1,
+                       scratch_bytes=4 << 30, deque_capacity=16384, algorithm=G.GTAP_KCLIQUE_PIVOT)
+    assert r.values == [c for _, _, c in gold["ranges"]]
