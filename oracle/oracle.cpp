@@ -550,6 +550,69 @@ static uint64_t pivot_count(const UndirectedCsr& g, const std::vector<int32_t>& 
     return total;
 }
 
+// The same recursion counting every clique size at once: a leaf (h, p) adds
+// C(p, j - h) to count[j] for every j (the pivot search does not depend on k,
+// only the pruning h > k does, which the all-sizes form leaves out).
+static void pivot_count_all(const UndirectedCsr& g, const std::vector<int32_t>& S, int h, int p, int kmax,
+                            uint64_t* count) {
+    if (h > kmax) return;
+    if (S.empty()) {
+        for (int j = h; j <= kmax && j - h <= p; ++j) count[j] += binom_u64((uint64_t)p, j - h);
+        return;
+    }
+    int32_t x = S[0];
+    size_t best = 0;
+    bool first = true;
+    for (int32_t y : S) {
+        std::vector<int32_t> t = intersect(g.adj.data() + g.off[y], g.off[y + 1] - g.off[y], S.data(), (int64_t)S.size());
+        if (first || t.size() > best) { best = t.size(); x = y; first = false; }
+    }
+    std::vector<int32_t> nx = intersect(g.adj.data() + g.off[x], g.off[x + 1] - g.off[x], S.data(), (int64_t)S.size());
+    std::vector<int32_t> branch{x};
+    for (int32_t y : S)
+        if (y != x && !std::binary_search(nx.begin(), nx.end(), y)) branch.push_back(y);
+    std::vector<int32_t> done;
+    for (int32_t w : branch) {
+        std::vector<int32_t> nw = intersect(g.adj.data() + g.off[w], g.off[w + 1] - g.off[w], S.data(), (int64_t)S.size());
+        std::vector<int32_t> Sw;
+        std::set_difference(nw.begin(), nw.end(), done.begin(), done.end(), std::back_inserter(Sw));
+        if (w == x) pivot_count_all(g, Sw, h, p + 1, kmax, count);
+        else pivot_count_all(g, Sw, h + 1, p, kmax, count);
+        done.insert(std::upper_bound(done.begin(), done.end(), w), w);
+    }
+}
+
+// The undirected CSR (sorted lists) of a graph, for the all-sizes count below.
+void orc_undirected(int64_t n, const int32_t* edges, int64_t m, int64_t* uoff, int32_t* uadj) {
+    UndirectedCsr g = undirected(n, edges, m);
+    std::memcpy(uoff, g.off.data(), (n + 1) * sizeof(int64_t));
+    std::memcpy(uadj, g.adj.data(), 2 * m * sizeof(int32_t));
+}
+
+// Clique counts of every size 3 .. kmax by pivoting, over the DAG edges of the
+// given ranges of a graph already oriented (off/adj as orc_orient returns them)
+// with its undirected CSR (uoff/uadj as orc_undirected returns them):
+// count[j] for j = 0 .. kmax (entries below 3 stay 0).
+void orc_kclique_pivot_all(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* uoff, const int32_t* uadj,
+                           const int64_t* ranges, int64_t n_ranges, int kmax, uint64_t* count) {
+    for (int j = 0; j <= kmax; ++j) count[j] = 0;
+    UndirectedCsr g;
+    g.off.assign(uoff, uoff + n + 1);
+    g.adj.assign(uadj, uadj + uoff[n]);
+    const int64_t m = off[n];
+    std::vector<uint64_t> c(kmax + 1, 0);
+    for (int64_t r = 0; r < n_ranges; ++r) {
+        int64_t u = 0;
+        for (int64_t e = ranges[2 * r]; e < ranges[2 * r + 1] && e < m; ++e) {
+            while (off[u + 1] <= e) ++u;
+            const int32_t v = adj[e];
+            std::vector<int32_t> C = intersect(adj + off[u], off[u + 1] - off[u], adj + off[v], off[v + 1] - off[v]);
+            pivot_count_all(g, C, 2, 0, kmax, c.data());
+        }
+    }
+    for (int j = 3; j <= kmax; ++j) count[j] = c[j];
+}
+
 // Total k-clique count by pivoting over the DAG edges [lo, hi) of the
 // (degree, id) orientation (all edges: lo = 0, hi = m); *nodes (optional)
 // receives the number of recursion nodes.
