@@ -72,7 +72,7 @@ def _load():
                 "orc_cilksort": (u64, [P, P, u64, u64, u64]),
                 "orc_kclique_pivot": (u64, [i64, P, i64, i32, i64, i64, P]),
                 "orc_undirected": (None, [i64, P, i64, P, P]),
-                "orc_kclique_pivot_all": (None, [i64, P, P, P, P, P, i64, i32, P]),
+                "orc_kclique_pivot_all": (None, [i64, P, P, P, i64, i32, P]),
                 "orc_nqueens_cutoff": (u64, [i32, i32, P]),
                 "orc_bintree_leaf": (u64, [u64, i32, i32]),
             }
@@ -208,16 +208,14 @@ def undirected(n: int, edges: np.ndarray):
     return uoff, uadj[: 2 * m]
 
 
-def kclique_pivot_all(off: np.ndarray, adj: np.ndarray, uoff: np.ndarray, uadj: np.ndarray, ranges, kmax: int):
-    """Clique counts of every size (list indexed by size, 0..kmax) by pivoting over DAG-edge ranges."""
+def kclique_pivot_all(off: np.ndarray, adj: np.ndarray, ranges, kmax: int):
+    """Clique counts of every size (list indexed by size, 0..kmax) by pivoting over DAG-edge
+    ranges of a graph oriented by `orient`."""
     off = np.ascontiguousarray(off, dtype=np.int64)
     adj = np.ascontiguousarray(adj, dtype=np.int32)
-    uoff = np.ascontiguousarray(uoff, dtype=np.int64)
-    uadj = np.ascontiguousarray(uadj, dtype=np.int32)
     rg = np.ascontiguousarray(np.asarray(ranges, dtype=np.int64).reshape(-1, 2))
     out = np.zeros(kmax + 1, dtype=np.uint64)
-    _load().orc_kclique_pivot_all(off.shape[0] - 1, _ptr(off), _ptr(adj), _ptr(uoff), _ptr(uadj), _ptr(rg),
-                                  rg.shape[0], kmax, _ptr(out))
+    _load().orc_kclique_pivot_all(off.shape[0] - 1, _ptr(off), _ptr(adj), _ptr(rg), rg.shape[0], kmax, _ptr(out))
     return [int(x) for x in out]
 
 

@@ -552,9 +552,13 @@ static uint64_t pivot_count(const UndirectedCsr& g, const std::vector<int32_t>& 
 
 // The same recursion counting every clique size at once: a leaf (h, p) adds
 // C(p, j - h) to count[j] for every j (the pivot search does not depend on k,
-// only the pruning h > k does, which the all-sizes form leaves out).
-static void pivot_count_all(const UndirectedCsr& g, const std::vector<int32_t>& S, int h, int p, int kmax,
-                            uint64_t* count) {
+// only the pruning h > k does, which the all-sizes form leaves out).  It runs
+// on the subgraph induced by the edge's candidate set C: nbr[a] lists the
+// members of C adjacent to member a (local indices in C's id order, so the
+// smallest-id tie rule is the smallest index), found from the members' DAG
+// out-lists and mirrored.
+static void pivot_all_induced(const std::vector<std::vector<int32_t>>& nbr, const std::vector<int32_t>& S, int h, int p,
+                              int kmax, uint64_t* count) {
     if (h > kmax) return;
     if (S.empty()) {
         for (int j = h; j <= kmax && j - h <= p; ++j) count[j] += binom_u64((uint64_t)p, j - h);
@@ -564,20 +568,20 @@ static void pivot_count_all(const UndirectedCsr& g, const std::vector<int32_t>& 
     size_t best = 0;
     bool first = true;
     for (int32_t y : S) {
-        std::vector<int32_t> t = intersect(g.adj.data() + g.off[y], g.off[y + 1] - g.off[y], S.data(), (int64_t)S.size());
+        std::vector<int32_t> t = intersect(nbr[y].data(), (int64_t)nbr[y].size(), S.data(), (int64_t)S.size());
         if (first || t.size() > best) { best = t.size(); x = y; first = false; }
     }
-    std::vector<int32_t> nx = intersect(g.adj.data() + g.off[x], g.off[x + 1] - g.off[x], S.data(), (int64_t)S.size());
+    std::vector<int32_t> nx = intersect(nbr[x].data(), (int64_t)nbr[x].size(), S.data(), (int64_t)S.size());
     std::vector<int32_t> branch{x};
     for (int32_t y : S)
         if (y != x && !std::binary_search(nx.begin(), nx.end(), y)) branch.push_back(y);
     std::vector<int32_t> done;
     for (int32_t w : branch) {
-        std::vector<int32_t> nw = intersect(g.adj.data() + g.off[w], g.off[w + 1] - g.off[w], S.data(), (int64_t)S.size());
+        std::vector<int32_t> nw = intersect(nbr[w].data(), (int64_t)nbr[w].size(), S.data(), (int64_t)S.size());
         std::vector<int32_t> Sw;
         std::set_difference(nw.begin(), nw.end(), done.begin(), done.end(), std::back_inserter(Sw));
-        if (w == x) pivot_count_all(g, Sw, h, p + 1, kmax, count);
-        else pivot_count_all(g, Sw, h + 1, p, kmax, count);
+        if (w == x) pivot_all_induced(nbr, Sw, h, p + 1, kmax, count);
+        else pivot_all_induced(nbr, Sw, h + 1, p, kmax, count);
         done.insert(std::upper_bound(done.begin(), done.end(), w), w);
     }
 }
@@ -593,12 +597,9 @@ void orc_undirected(int64_t n, const int32_t* edges, int64_t m, int64_t* uoff, i
 // given ranges of a graph already oriented (off/adj as orc_orient returns them)
 // with its undirected CSR (uoff/uadj as orc_undirected returns them):
 // count[j] for j = 0 .. kmax (entries below 3 stay 0).
-void orc_kclique_pivot_all(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* uoff, const int32_t* uadj,
-                           const int64_t* ranges, int64_t n_ranges, int kmax, uint64_t* count) {
+void orc_kclique_pivot_all(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* ranges, int64_t n_ranges,
+                           int kmax, uint64_t* count) {
     for (int j = 0; j <= kmax; ++j) count[j] = 0;
-    UndirectedCsr g;
-    g.off.assign(uoff, uoff + n + 1);
-    g.adj.assign(uadj, uadj + uoff[n]);
     const int64_t m = off[n];
     std::vector<uint64_t> c(kmax + 1, 0);
     for (int64_t r = 0; r < n_ranges; ++r) {
@@ -607,7 +608,21 @@ void orc_kclique_pivot_all(int64_t n, const int64_t* off, const int32_t* adj, co
             while (off[u + 1] <= e) ++u;
             const int32_t v = adj[e];
             std::vector<int32_t> C = intersect(adj + off[u], off[u + 1] - off[u], adj + off[v], off[v + 1] - off[v]);
-            pivot_count_all(g, C, 2, 0, kmax, c.data());
+            // the subgraph induced by C, in local indices
+            std::vector<std::vector<int32_t>> nbr(C.size());
+            for (size_t a = 0; a < C.size(); ++a) {
+                const int32_t y = C[a];
+                std::vector<int32_t> out = intersect(adj + off[y], off[y + 1] - off[y], C.data(), (int64_t)C.size());
+                for (int32_t z : out) {
+                    const int32_t b = (int32_t)(std::lower_bound(C.begin(), C.end(), z) - C.begin());
+                    nbr[a].push_back(b);
+                    nbr[b].push_back((int32_t)a);
+                }
+            }
+            for (auto& l : nbr) std::sort(l.begin(), l.end());
+            std::vector<int32_t> S(C.size());
+            for (size_t a = 0; a < C.size(); ++a) S[a] = (int32_t)a;
+            pivot_all_induced(nbr, S, 2, 0, kmax, c.data());
         }
     }
     for (int j = 3; j <= kmax; ++j) count[j] = c[j];

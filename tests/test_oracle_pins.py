@@ -337,19 +337,17 @@ def test_kclique_pivoting_all_sizes_matches_per_k():
     # one pass for every size equals the per-k pivot counts and the orientation counts
     n, e = inputs.rmat_graph(9, 16, seed=11)
     off, adj = oracle.orient(n, e)
-    uoff, uadj = oracle.undirected(n, e)
     m = len(e)
-    allk = oracle.kclique_pivot_all(off, adj, uoff, uadj, [(0, m)], 9)
+    allk = oracle.kclique_pivot_all(off, adj, [(0, m)], 9)
     for k in range(3, 10):
         assert allk[k] == oracle.kclique_pivot(n, e, k)[0] == oracle.kclique(n, e, k), k
     # ranges add up
-    parts = [oracle.kclique_pivot_all(off, adj, uoff, uadj, [(lo, min(m, lo + 700))], 6) for lo in range(0, m, 700)]
+    parts = [oracle.kclique_pivot_all(off, adj, [(lo, min(m, lo + 700))], 6) for lo in range(0, m, 700)]
     assert [sum(p[k] for p in parts) for k in range(7)] == allk[:7]
     # complete graph
     kn = np.array(list(combinations(range(25), 2)), dtype=np.int32)
     o2, a2 = oracle.orient(25, kn)
-    u2, ua2 = oracle.undirected(25, kn)
-    got = oracle.kclique_pivot_all(o2, a2, u2, ua2, [(0, len(kn))], 12)
+    got = oracle.kclique_pivot_all(o2, a2, [(0, len(kn))], 12)
     assert got[3:] == [math.comb(25, k) for k in range(3, 13)]
 
 
