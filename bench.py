@@ -706,10 +706,12 @@ def run_kclique(args):
     src = torch.empty(m, dtype=torch.int32, device="cuda")
     work = torch.empty(4 * n + 16, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
-    kargs = G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), 0, m, args.k, 64, 1, 0)
-    # k >= 5 holds a larger frontier: DAQ 4 needs rings of 16384 and a 4 GiB record pool
-    pool, scratch = (1 << 30, 4 << 30) if args.k == 4 else (4 << 30, 4 << 30)
-    ring = 4096 if args.k == 4 else 16384
+    algo = G.GTAP_KCLIQUE_PIVOT if args.algorithm == "pivot" else G.GTAP_KCLIQUE_ORIENT
+    thr = 32 if algo == G.GTAP_KCLIQUE_PIVOT else 64
+    kargs = G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), 0, m, args.k, thr, 1, algo)
+    big = args.k > 4 or args.algorithm == "pivot"   # larger frontier: rings of 16384, 4 GiB pool
+    pool, scratch = (4 << 30, 4 << 30) if big else (1 << 30, 4 << 30)
+    ring = 16384 if big else 4096
 
     def step():
         G.gtap_kclique_orient(edges.data_ptr(), m, n, off.data_ptr(), adj.data_ptr(), src.data_ptr(),
@@ -734,13 +736,20 @@ def run_kclique(args):
     else:
         # larger k: the oracle's cost per edge explodes at the dense low-id end, so sample the rest
         ranges = [(lo, lo + 64) for lo in ((2 * m) // 3, (5 * m) // 6)] + [(m - 200, m)]
-    with runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=pool, scratch_bytes=scratch) as c:
+    want = [oracle.kclique_edge_range(n, e, args.k, lo, hi) for lo, hi in ranges]
+    sampled = _kclique_golden(f"kclique_rmat{KC_SCALE}_k{args.k}_sampled.txt")
+    if sampled is not None:
+        # the oracle's sampled ranges over the whole graph (written ahead by the golden script)
+        ranges += [(lo, hi) for lo, hi, _ in sampled["ranges"]]
+        want += [cnt for _, _, cnt in sampled["ranges"]]
+    with runner.Context(G.GTAP_MODE_THREAD, 4, pool_bytes=pool, scratch_bytes=scratch, deque_capacity=ring,
+                        max_roots=max(4096, len(ranges))) as c:
         t = c.register("kclique")
-        hs = [c.spawn(t, G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), lo, hi, args.k, 64, 0, 0))
+        hs = [c.spawn(t, G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), lo, hi, args.k, thr, 1,
+                                             algo))
               for lo, hi in ranges]
         c.run()
         got = [c.result_u64(h) for h in hs]
-    want = [oracle.kclique_edge_range(n, e, args.k, lo, hi) for lo, hi in ranges]
     assert got == want, (got, want)
     kms = []
     torch.cuda.synchronize()
@@ -758,12 +767,14 @@ def run_kclique(args):
         "metric": "k-clique time", "value": ms, "unit": "ms/instance", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"{args.k}-clique count, R-MAT scale {KC_SCALE} edge factor 16 (a,b,c=0.57,0.19,0.19, "
-                               f"seed 7, {m} undirected edges), degree-ordered DAG, thread mode, DAQ {KC_QUEUES} queues "
-                               "by recursion depth, split threshold 64; one step = orientation + gtap_init + run + "
-                               "gtap_finalize (wall clock, synchronised)", "parallelism": "replicas",
+        "config": {"workload": f"{args.k}-clique count by {'pivoting' if algo else 'orientation'}, R-MAT scale "
+                               f"{KC_SCALE} edge factor 16 (a,b,c=0.57,0.19,0.19, seed 7, {m} undirected edges), "
+                               f"degree-ordered DAG, thread mode, DAQ {KC_QUEUES} queues by recursion depth, split "
+                               f"threshold {thr}; one step = orientation + gtap_init + run + gtap_finalize (wall "
+                               "clock, synchronised)", "parallelism": "replicas",
                    "l2": "graph 126 MB CSR + 63 MB edge list, > L2 with the scratch sets"},
         "count": count, "kernel_ms_median": kms[len(kms) // 2],
+        "algorithm": args.algorithm,
         "parity": ("full count equals the oracle's (golden file) and sampled ranges equal the oracle's"
                    if gold is not None else "sampled DAG-edge ranges equal the oracle's"),
         "e2e": {"value": ms, "unit": "ms/instance", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 16,
@@ -1277,8 +1288,8 @@ def run_batch(args):
     specs = [(12 + (7 * i) // 64, 7 + i) for i in range(BATCH_GRAPHS)]
     graphs = [runner.DeviceGraph(*inputs.rmat_graph(sc, 16, seed=sd)) for sc, sd in specs]
     torch.cuda.synchronize()
-    # DAQ 4 by depth: 64 instances' frontier needs rings of 16384 (4096 overflows)
-    cfg = dict(pool_bytes=1 << 30, scratch_bytes=4 << 30, deque_capacity=16384)
+    # DAQ 4 by depth: 64 instances' frontier can exceed rings of 16384 on one warp
+    cfg = dict(pool_bytes=1 << 30, scratch_bytes=4 << 30, deque_capacity=65536)
     want = [g[4] for g in gold["graphs"]] if gold else None
 
     def one_launch(c, hs):
@@ -1363,6 +1374,8 @@ def main():
                          "launches; sched: scheduler comparison on fib(35); micro: mode/DAQ binary-tree sweeps")
     ap.add_argument("--requests", type=int, default=SERVE_REQUESTS)
     ap.add_argument("--k", type=int, default=KC_K, choices=[4, 5, 6, 7], help="kclique: clique size")
+    ap.add_argument("--algorithm", default="orient", choices=["orient", "pivot"],
+                    help="kclique: orientation or pivoting (Sec. 6.4.2)")
     ap.add_argument("--fmm-precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -76,6 +76,9 @@ struct gtap_ctx {
     unsigned long long* sq_seq = nullptr;
     uint32_t* sq_ids = nullptr;
     uint64_t sq_mask = 0;
+    unsigned long long* lq_seq = nullptr;
+    uint32_t* lq_ids = nullptr;
+    uint64_t lq_mask = 0;
     char* blocks = nullptr;
     uint64_t blocks_bytes = 0;
     unsigned* fstate = nullptr;
@@ -323,11 +326,17 @@ gtap_status gtap_init(gtap_mode mode, int n_queues, size_t frame_pool_bytes, con
         const uint64_t nb0 = cfg.scratch_bytes / kScratchBlock;
         if (nb0 < 2) { free_all(c); return GTAP_ERR_INVALID_ARG; }
         const uint64_t nq = next_pow2((uint32_t)std::min<uint64_t>(nb0 + 1, 1ull << 31));
-        const uint64_t qbytes = align_up(nq * (sizeof(unsigned long long) + sizeof(uint32_t)), kScratchBlock);
+        // the large-chunk queue after it: one slot per chunk the arena can hold
+        const uint64_t nlq = next_pow2((uint32_t)std::min<uint64_t>(nb0 / kScratchLargeBlocks + 1, 1ull << 31));
+        const size_t slot = sizeof(unsigned long long) + sizeof(uint32_t);
+        const uint64_t qbytes = align_up((nq + nlq) * slot, kScratchBlock);
         if (qbytes + kScratchBlock > cfg.scratch_bytes) { free_all(c); return GTAP_ERR_INVALID_ARG; }
         c->sq_seq = reinterpret_cast<unsigned long long*>(c->scratch);
         c->sq_ids = reinterpret_cast<uint32_t*>(c->scratch + nq * sizeof(unsigned long long));
         c->sq_mask = nq - 1;
+        c->lq_seq = reinterpret_cast<unsigned long long*>(c->scratch + nq * slot);
+        c->lq_ids = reinterpret_cast<uint32_t*>(c->scratch + nq * slot + nlq * sizeof(unsigned long long));
+        c->lq_mask = nlq - 1;
         c->blocks = c->scratch + qbytes;
         c->blocks_bytes = (cfg.scratch_bytes - qbytes) / kScratchBlock * kScratchBlock;
     }
@@ -685,6 +694,9 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
     P.sq_seq = c->sq_seq;
     P.sq_ids = c->sq_ids;
     P.sq_mask = c->sq_mask;
+    P.lq_seq = c->lq_seq;
+    P.lq_ids = c->lq_ids;
+    P.lq_mask = c->lq_mask;
     P.fstate = c->fstate;
     P.flog = c->flog;
     P.flogn = c->flogn;

@@ -188,46 +188,104 @@ __device__ __forceinline__ bool abort_requested(const KParams& P, bool check_hos
 // completed-free counter (the frame pool's chunk-queue protocol, one block per
 // slot), fresh ones from a bump counter.  Buffers larger than one block take
 // consecutive fresh blocks and are not recycled.
-__device__ __forceinline__ char* scratch_alloc(const KParams& P, uint64_t bytes, bool* pooled, int type, int worker) {
-    const uint64_t nblocks = P.scratch_bytes / kScratchBlock;
-    *pooled = bytes <= kScratchBlock;
-    if (*pooled) {
-        const long long a = (long long)atomicAdd(&P.ctl->sc_avail.v, ~0ull);   // reserve one completed free
-        if (a > 0) {
-            const unsigned long long d = atomicAdd(&P.ctl->sc_deq.v, 1ull);
-            for (int it = 0; it < (1 << 20); ++it) {
-                if (ld_acquire_u64(&P.sq_seq[d & P.sq_mask]) == d + 1) {
-                    const uint32_t id = __ldcg(&P.sq_ids[d & P.sq_mask]);
-                    st_release_u64(&P.sq_seq[d & P.sq_mask], d + P.sq_mask + 1);
-                    return P.scratch + (uint64_t)id * kScratchBlock;
-                }
-                __nanosleep(64);
-            }
-            raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, d);
-            return nullptr;
+// A bounded MPMC queue of free ids (the frame pool's chunk-queue protocol, one id per slot).
+struct FreeQ {
+    unsigned long long* seq;
+    uint32_t* ids;
+    uint64_t mask;
+    unsigned long long *enq, *deq, *avail;
+};
+__device__ __forceinline__ FreeQ small_free_q(const KParams& P) {
+    return FreeQ{P.sq_seq, P.sq_ids, P.sq_mask, &P.ctl->sc_enq.v, &P.ctl->sc_deq.v, &P.ctl->sc_avail.v};
+}
+__device__ __forceinline__ FreeQ large_free_q(const KParams& P) {
+    return FreeQ{P.lq_seq, P.lq_ids, P.lq_mask, &P.ctl->lc_enq.v, &P.ctl->lc_deq.v, &P.ctl->lc_avail.v};
+}
+
+// Take a free id: >= 0 the id, -1 none free, -2 a wait ran out (error raised).
+__device__ __forceinline__ long long freeq_take(const KParams& P, const FreeQ& q, int type, int worker) {
+    const long long a = (long long)atomicAdd(q.avail, ~0ull);   // reserve one completed free
+    if (a <= 0) { atomicAdd(q.avail, 1ull); return -1; }
+    const unsigned long long d = atomicAdd(q.deq, 1ull);
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (ld_acquire_u64(&q.seq[d & q.mask]) == d + 1) {
+            const uint32_t id = __ldcg(&q.ids[d & q.mask]);
+            st_release_u64(&q.seq[d & q.mask], d + q.mask + 1);
+            return (long long)id;
         }
-        atomicAdd(&P.ctl->sc_avail.v, 1ull);
+        __nanosleep(64);
     }
+    raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, d);
+    return -2;
+}
+
+__device__ __forceinline__ void freeq_give(const KParams& P, const FreeQ& q, uint32_t id, int type, int worker) {
+    const unsigned long long t = atomicAdd(q.enq, 1ull);
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (ld_acquire_u64(&q.seq[t & q.mask]) == t) {
+            __stcg(&q.ids[t & q.mask], id);
+            __threadfence();
+            st_release_u64(&q.seq[t & q.mask], t + 1);
+            atomicAdd(q.avail, 1ull);
+            return;
+        }
+        __nanosleep(64);
+    }
+    raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, t);
+}
+
+// Scratch buffers.  kind: 1 = one recycled block (<= kScratchBlock bytes),
+// 2 = a recycled large chunk (<= kScratchLargeBlocks blocks), 0 = larger,
+// consecutive fresh blocks that are not recycled.  Returns null after raising
+// GTAP_ERR_TASK_FAILED when the arena is exhausted.
+__device__ __forceinline__ char* scratch_alloc_kind(const KParams& P, uint64_t bytes, int* kind, int type, int worker) {
+    const uint64_t nblocks = P.scratch_bytes / kScratchBlock;
+    uint64_t k = (bytes + kScratchBlock - 1) / kScratchBlock;
+    *kind = 0;
+    if (k <= 1) {
+        *kind = 1;
+        k = 1;
+        const long long id = freeq_take(P, small_free_q(P), type, worker);
+        if (id == -2) return nullptr;
+        if (id >= 0) return P.scratch + (uint64_t)id * kScratchBlock;
+    } else if (k <= kScratchLargeBlocks && P.lq_seq != nullptr) {
+        *kind = 2;
+        k = kScratchLargeBlocks;
+        const long long id = freeq_take(P, large_free_q(P), type, worker);
+        if (id == -2) return nullptr;
+        if (id >= 0) return P.scratch + (uint64_t)id * kScratchBlock;
+    }
+    const unsigned long long b = atomicAdd(&P.ctl->scratch_top.v, (unsigned long long)k);
+    if (b + k > nblocks) { raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, (b + k) * kScratchBlock); return nullptr; }
+    return P.scratch + b * kScratchBlock;
+}
+
+__device__ __forceinline__ char* scratch_alloc(const KParams& P, uint64_t bytes, bool* pooled, int type, int worker) {
+    // one recycled block, or consecutive fresh blocks that are not recycled
+    if (bytes <= kScratchBlock) {
+        int kind;
+        char* p = scratch_alloc_kind(P, bytes, &kind, type, worker);
+        *pooled = true;
+        return p;
+    }
+    *pooled = false;
+    const uint64_t nblocks = P.scratch_bytes / kScratchBlock;
     const uint64_t k = (bytes + kScratchBlock - 1) / kScratchBlock;
     const unsigned long long b = atomicAdd(&P.ctl->scratch_top.v, (unsigned long long)k);
     if (b + k > nblocks) { raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, (b + k) * kScratchBlock); return nullptr; }
     return P.scratch + b * kScratchBlock;
 }
 
+__device__ __forceinline__ uint32_t scratch_block_id(const KParams& P, const void* p) {
+    return (uint32_t)((reinterpret_cast<const char*>(p) - P.scratch) / kScratchBlock);
+}
 __device__ __forceinline__ void scratch_free(const KParams& P, const void* p, int type, int worker) {
-    const uint32_t id = (uint32_t)((reinterpret_cast<const char*>(p) - P.scratch) / kScratchBlock);
-    const unsigned long long t = atomicAdd(&P.ctl->sc_enq.v, 1ull);
-    for (int it = 0; it < (1 << 20); ++it) {
-        if (ld_acquire_u64(&P.sq_seq[t & P.sq_mask]) == t) {
-            __stcg(&P.sq_ids[t & P.sq_mask], id);
-            __threadfence();
-            st_release_u64(&P.sq_seq[t & P.sq_mask], t + 1);
-            atomicAdd(&P.ctl->sc_avail.v, 1ull);
-            return;
-        }
-        __nanosleep(64);
-    }
-    raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, t);
+    freeq_give(P, small_free_q(P), scratch_block_id(P, p), type, worker);
+}
+// Release a buffer by the kind scratch_alloc_kind returned (kind 0 is never recycled).
+__device__ __forceinline__ void scratch_free_kind(const KParams& P, const void* p, int kind, int type, int worker) {
+    if (kind == 1) freeq_give(P, small_free_q(P), scratch_block_id(P, p), type, worker);
+    else if (kind == 2) freeq_give(P, large_free_q(P), scratch_block_id(P, p), type, worker);
 }
 
 // ---------------------------------------------------------------------------

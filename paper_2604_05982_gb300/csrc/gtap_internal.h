@@ -34,6 +34,7 @@ enum ProgType : int {
     T_TSORT = 10,        // thread-mode Cilksort: sort a range
     T_TMERGE = 11,       // thread-mode Cilksort: merge two runs
     T_KCLIQUE_PIV = 12,  // k-clique by pivoting: branch range of a bitset-encoded candidate subgraph
+    T_KCLIQUE_PIVB = 13, // k-clique by pivoting: a node of a candidate subgraph of more than 64 vertices
     // block mode
     T_MSORT = 16,
     T_MMERGE = 17,
@@ -63,6 +64,7 @@ enum ProgSet : unsigned {
 enum Sched : int { SCHED_BATCHED = 0, SCHED_GLOBAL = 1, SCHED_SINGLE = 2 };
 
 constexpr uint64_t kScratchBlock = 4096;   // bytes per recycled scratch block
+constexpr uint64_t kScratchLargeBlocks = 16; // blocks per recycled large chunk (64 KiB)
 
 // Frame header flag bits.
 constexpr uint32_t kFlagAccumulate = 1u;  // child result is added (u64) into the parent slot
@@ -109,6 +111,7 @@ struct DevControl {
     Line128 inflight;          // serving: roots admitted and not yet completed
     Line128 cq_avail;          // chunks whose enqueue has completed and that no dequeuer reserved
     Line128 sc_enq, sc_deq, sc_avail;   // scratch free-block queue tickets / completed frees
+    Line128 lc_enq, lc_deq, lc_avail;   // the same for recycled large chunks (kScratchLargeBlocks blocks each)
     Line128 out_tail;          // serving: completions written to the outbox
     Line128 admitted;          // serving: requests admitted so far
     Line128 gq_enq, gq_deq, gq_avail;   // central-queue scheduler: tickets and completed publications
@@ -194,6 +197,9 @@ struct KParams {
     unsigned long long* sq_seq;   // free-block queue: sequence numbers and block ids
     uint32_t* sq_ids;
     uint64_t sq_mask;
+    unsigned long long* lq_seq;   // free large-chunk queue: sequence numbers and first-block ids
+    uint32_t* lq_ids;
+    uint64_t lq_mask;
     // serving mode (resident kernel)
     int serving;
     uint32_t inbox_cap, outbox_cap;

@@ -34,6 +34,9 @@ struct ThreadDispatch {
         case T_KCLIQUE_PIV:
             if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_piv_step(c); return; }
             break;
+        case T_KCLIQUE_PIVB:
+            if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_pivb_step(c); return; }
+            break;
         case T_BINTREE:
             if constexpr ((PSET & PS_BINTREE) != 0) { bintree_step(c); return; }
             break;

@@ -578,6 +578,204 @@ static __device__ void kclique_piv_step(TaskCtx& c) {
     c.ret(total);
 }
 
+// Pivoting on candidate sets of more than 64 vertices (multi-word bitsets).
+// The first run of an edge's node materialises C = P n N+(w) and the rows of
+// the subgraph C induces (ceil(|C| / 64) words per member, both directions)
+// in one scratch allocation; every node keeps its own set S and branch set
+// (the pivot and its non-neighbours) in a small block.  A node chooses its
+// pivot on its first run; a node with more than kKcFan branches splits the
+// branch range over child tasks; otherwise it runs its branches: a branch set
+// of at most 64 members is compacted to 64-bit rows and counted in the lane,
+// a larger one becomes a child node.
+// Record: [16] root  [20] r:8 | p:8 | W:8 | flags:8 (1 lazy, 2 owns rows, 4 owns set, 8 branches chosen,
+//         16 rows block pooled, 32 set block pooled)
+//         (16/32: the rows / set block is a recycled one-block buffer; 64/128: a recycled large chunk)
+//         [24] rows (lazy: P = N+(u))  [32] set block (lazy: w | |P| << 32)
+//         [40] lo:16 | hi:16 | x:16 | depth:8 (lazy: |C| in lo/hi)  [48] local  [56] acc
+struct KpbSpawn { uint32_t root, meta; unsigned long long rows, set, range, local, acc; };
+constexpr uint32_t kKpbSlotAcc = 7;
+constexpr uint32_t kKpbMeta = 16, kKpbRows = 24, kKpbSet = 32, kKpbRange = 40, kKpbLocal = 48;
+constexpr int kKpbMaxW = 16;   // members up to 1024 (the DAG's out-lists are at most 8192, C is much smaller in practice)
+constexpr uint32_t kKpbLazy = 1, kKpbOwnRows = 2, kKpbOwnSet = 4, kKpbChosen = 8, kKpbRowsPooled = 16, kKpbSetPooled = 32,
+                   kKpbRowsLarge = 64, kKpbSetLarge = 128;
+
+// Release the blocks a node owns (each block once: a root's set lies inside its rows block).
+__device__ __forceinline__ void kpb_release(TaskCtx& c, uint32_t flags, const void* rows, const void* setb) {
+    if (flags & kKpbOwnSet) scratch_free_kind(c.P, setb, (flags & kKpbSetPooled) ? 1 : ((flags & kKpbSetLarge) ? 2 : 0),
+                                              c.type(), c.worker);
+    if (flags & kKpbOwnRows) scratch_free_kind(c.P, rows, (flags & kKpbRowsPooled) ? 1 : ((flags & kKpbRowsLarge) ? 2 : 0),
+                                               c.type(), c.worker);
+}
+
+__device__ __forceinline__ unsigned long long kpb_range(uint32_t lo, uint32_t hi, uint32_t x, uint32_t depth) {
+    return (unsigned long long)(lo & 0xFFFF) | ((unsigned long long)(hi & 0xFFFF) << 16) |
+           ((unsigned long long)(x & 0xFFFF) << 32) | ((unsigned long long)(depth & 0xFF) << 48);
+}
+
+// A branch set of at most 64 members as a compact 64-bit subgraph, then the pivot count.
+__device__ __forceinline__ unsigned long long kpb_count_compact(const unsigned long long* rows, int W,
+                                                                 const unsigned long long* Sw, int r, int p) {
+    int m[kKcMaxThr];
+    int c = 0;
+    for (int t = 0; t < W; ++t)
+        for (unsigned long long b = Sw[t]; b; b &= b - 1) m[c++] = t * 64 + __ffsll((long long)b) - 1;
+    unsigned long long row[kKcMaxThr];
+    for (int i = 0; i < c; ++i) {
+        const unsigned long long* ri = rows + (size_t)m[i] * W;
+        unsigned long long bits = 0;
+        for (int j = 0; j < c; ++j)
+            if ((__ldcg(ri + (m[j] >> 6)) >> (m[j] & 63)) & 1ull) bits |= 1ull << j;
+        row[i] = bits;
+    }
+    const unsigned long long full = (c == 64) ? ~0ull : ((1ull << c) - 1ull);
+    return kp_count(LocalRows{row}, full, r, p);
+}
+
+static __device__ void kclique_pivb_step(TaskCtx& c) {
+    const KpbSpawn a = c.load<KpbSpawn>();
+    uint32_t flags = a.meta >> 24;
+    const int r = (int)(a.meta & 0xFF), p = (int)((a.meta >> 8) & 0xFF);
+    int W = (int)((a.meta >> 16) & 0xFF);
+    if (c.pc() != 0) {
+        kpb_release(c, flags, reinterpret_cast<const void*>(a.rows), reinterpret_cast<const void*>(a.set));
+        c.ret(a.acc + a.local);
+        return;
+    }
+    const gtap_kclique_args e = kc_env(c.P, a.root);
+    unsigned long long* rows = reinterpret_cast<unsigned long long*>(a.rows);
+    unsigned long long* setb = reinterpret_cast<unsigned long long*>(a.set);
+    uint32_t depth = (uint32_t)((a.range >> 48) & 0xFF);
+    uint32_t lo = (uint32_t)(a.range & 0xFFFF), hi = (uint32_t)((a.range >> 16) & 0xFFFF);
+    uint32_t x = (uint32_t)((a.range >> 32) & 0xFFFF);
+    unsigned long long S[kKpbMaxW], V[kKpbMaxW];
+    if (flags & kKpbLazy) {
+        // materialise C = P n N+(w) and the rows of the subgraph it induces, in one allocation
+        const int* P = reinterpret_cast<const int*>(a.rows);
+        const int w = (int)(a.set & 0xFFFFFFFFull), np = (int)(a.set >> 32);
+        const int cn = (int)lo;
+        W = (cn + 63) / 64;
+        if (W > kKpbMaxW) { c.fail(GTAP_ERR_INVALID_ARG, (unsigned long long)cn); return; }
+        const uint64_t words = (uint64_t)cn * W + 2 * (uint64_t)W;
+        int kind;
+        char* blk = scratch_alloc_kind(c.P, words * 8 + (uint64_t)cn * 4, &kind, c.type(), c.worker);
+        if (!blk) return;
+        rows = reinterpret_cast<unsigned long long*>(blk);
+        setb = rows + (size_t)cn * W;
+        int* C = reinterpret_cast<int*>(setb + 2 * W);
+        const long long ow = kc_off(e, w);
+        kc_intersect(P, np, AdjLoad{}, e.adj + ow, (int)(kc_off(e, w + 1) - ow), AdjLoad{}, C, cn);
+        for (uint64_t i = 0; i < (uint64_t)cn * W; ++i) __stcg(rows + i, 0ull);
+        // DAG edges inside C from each member's out-list, set in both rows
+        for (int i = 0; i < cn; ++i) {
+            const int y = __ldcg(C + i);
+            const long long oy = kc_off(e, y);
+            const int ny = (int)(kc_off(e, y + 1) - oy);
+            int u0 = 0, v0 = 0;
+            while (u0 < ny && v0 < cn) {
+                const int s0 = __ldg(e.adj + oy + u0), t0 = __ldcg(C + v0);
+                if (s0 < t0) ++u0;
+                else if (t0 < s0) ++v0;
+                else {
+                    unsigned long long* ri = rows + (size_t)i * W + (v0 >> 6);
+                    __stcg(ri, __ldcg(ri) | (1ull << (v0 & 63)));
+                    unsigned long long* rj = rows + (size_t)v0 * W + (i >> 6);
+                    __stcg(rj, __ldcg(rj) | (1ull << (i & 63)));
+                    ++u0; ++v0;
+                }
+            }
+        }
+        for (int t = 0; t < W; ++t) {
+            const int rem_bits = cn - t * 64;
+            S[t] = rem_bits >= 64 ? ~0ull : ((1ull << rem_bits) - 1ull);
+        }
+        // the set block lies inside the rows allocation: freeing the rows frees it (one free per block)
+        flags = kKpbOwnRows | (kind == 1 ? kKpbRowsPooled : 0u) | (kind == 2 ? kKpbRowsLarge : 0u);
+        lo = 0;
+        hi = 0xFFFF;
+        // what the resume needs: the blocks to free
+        st_cg64(c.frame + kKpbRows, (unsigned long long)rows);
+        st_cg64(c.frame + kKpbSet, (unsigned long long)setb);
+        st_cg32(c.frame + kKpbMeta, (uint32_t)r | ((uint32_t)p << 8) | ((uint32_t)W << 16) | (flags << 24));
+    } else {
+        for (int t = 0; t < W; ++t) S[t] = __ldcg(setb + t);
+    }
+    if (!(flags & kKpbChosen)) {
+        // the pivot: most neighbours inside S, lowest position on ties; the branches: x and its non-neighbours
+        int best = -1;
+        for (int t = 0; t < W; ++t)
+            for (unsigned long long b = S[t]; b; b &= b - 1) {
+                const int y = t * 64 + __ffsll((long long)b) - 1;
+                int cnt = 0;
+                for (int q = 0; q < W; ++q) cnt += __popcll(__ldcg(rows + (size_t)y * W + q) & S[q]);
+                if (cnt > best) { best = cnt; x = (uint32_t)y; }
+            }
+        for (int t = 0; t < W; ++t) {
+            V[t] = S[t] & ~__ldcg(rows + (size_t)x * W + t);
+            __stcg(setb + W + t, V[t]);
+        }
+        flags |= kKpbChosen;
+    } else {
+        for (int t = 0; t < W; ++t) V[t] = __ldcg(setb + W + t);
+    }
+    int nb = 0;
+    for (int t = 0; t < W; ++t) nb += __popcll(V[t]);
+    hi = min(hi, (uint32_t)nb);
+    if (hi - lo > (uint32_t)kKcFan) {
+        const uint32_t per = (hi - lo + kKcFan - 1) / kKcFan;
+        for (uint32_t s0 = lo; s0 < hi; s0 += per)
+            c.spawn(T_KCLIQUE_PIVB, kKpbSlotAcc, kc_queue(e, (int)depth + 1),
+                    KpbSpawn{a.root, (uint32_t)r | ((uint32_t)p << 8) | ((uint32_t)W << 16) | (kKpbChosen << 24),
+                             (unsigned long long)rows, (unsigned long long)setb,
+                             kpb_range(s0, min(hi, s0 + per), x, depth + 1), 0ull, 0ull},
+                    kFlagAccumulate);
+        st_cg32(c.frame + kKpbMeta, (uint32_t)r | ((uint32_t)p << 8) | ((uint32_t)W << 16) | (flags << 24));
+        c.join(1, kc_queue(e, (int)depth));
+        return;
+    }
+    // branches lo .. hi-1 of V, in bit order
+    unsigned long long local = 0;
+    int idx = 0;
+    for (int t = 0; t < W && idx < (int)hi; ++t) {
+        for (unsigned long long b = V[t]; b && idx < (int)hi; b &= b - 1, ++idx) {
+            if (idx < (int)lo) continue;
+            const int bit = __ffsll((long long)b) - 1;
+            const int w = t * 64 + bit;
+            const bool is_x = (uint32_t)w == x;
+            const int r2 = is_x ? r : r - 1, p2 = is_x ? p + 1 : p;
+            if (r2 < 0) continue;
+            if (r2 == 0) { local += 1; continue; }
+            // S_w = row(w) n S without the branch vertices before w
+            unsigned long long Sw[kKpbMaxW];
+            int cnt = 0;
+            for (int q = 0; q < W; ++q) {
+                const unsigned long long before = q < t ? V[q] : (q == t ? (V[q] & ((1ull << bit) - 1ull)) : 0ull);
+                Sw[q] = __ldcg(rows + (size_t)w * W + q) & S[q] & ~before;
+                cnt += __popcll(Sw[q]);
+            }
+            if (cnt + p2 < r2) continue;
+            if (cnt == 0) { local += kp_binom(p2, r2); continue; }
+            if (cnt <= kKcMaxThr) { local += kpb_count_compact(rows, W, Sw, r2, p2); continue; }
+            int kind;
+            unsigned long long* nb2 = reinterpret_cast<unsigned long long*>(scratch_alloc_kind(c.P, (uint64_t)W * 16, &kind, c.type(), c.worker));
+            if (!nb2) return;
+            for (int q = 0; q < W; ++q) __stcg(nb2 + q, Sw[q]);
+            c.spawn(T_KCLIQUE_PIVB, kKpbSlotAcc, kc_queue(e, (int)depth + 1),
+                    KpbSpawn{a.root, (uint32_t)r2 | ((uint32_t)p2 << 8) | ((uint32_t)W << 16) |
+                                         ((kKpbOwnSet | (kind == 1 ? kKpbSetPooled : 0u) | (kind == 2 ? kKpbSetLarge : 0u)) << 24),
+                             (unsigned long long)rows, (unsigned long long)nb2, kpb_range(0, 0xFFFF, 0, depth + 1), 0ull, 0ull},
+                    kFlagAccumulate);
+        }
+    }
+    if (c.nspawned == 0) {
+        kpb_release(c, flags, rows, setb);
+        c.ret(local);
+        return;
+    }
+    st_cg64(c.frame + kKpbLocal, local);
+    st_cg32(c.frame + kKpbMeta, (uint32_t)r | ((uint32_t)p << 8) | ((uint32_t)W << 16) | (flags << 24));
+    c.join(1, kc_queue(e, (int)depth));
+}
+
 static __device__ void kclique_range_step(TaskCtx& c) {
     const KcRangeSpawn a = c.load<KcRangeSpawn>();
     const gtap_kclique_args& e = kc_env(c.P, a.root);
@@ -609,6 +807,15 @@ static __device__ void kclique_range_step(TaskCtx& c) {
         }
         if (pivot && cn <= kKcMaxThr) {
             if (!kp_spawn_split(c, e, a.root, C, cn, need, 1, kKcRangeSlotAcc)) return;
+            continue;
+        }
+        if (pivot) {
+            // more than 64 members: a pivot node over multi-word bitsets, materialised when it runs
+            c.spawn(T_KCLIQUE_PIVB, kKcRangeSlotAcc, kc_queue(e, 1),
+                    KpbSpawn{a.root, (uint32_t)need | (kKpbLazy << 24), (unsigned long long)(e.adj + ou),
+                             (unsigned long long)(uint32_t)v | ((unsigned long long)(uint32_t)nu << 32),
+                             kpb_range((uint32_t)cn, (uint32_t)cn, 0, 1), 0ull, 0ull},
+                    kFlagAccumulate);
             continue;
         }
         // the child materialises N+(u) n N+(v) when it runs and adds its count

@@ -15,6 +15,8 @@ __global__ void reset_kernel(KParams P, int init_cq) {
         for (size_t i = tid; i <= P.ncq_mask; i += nth) P.cq_seq[i] = i;
     if (P.sq_seq != nullptr)
         for (size_t i = tid; i <= P.sq_mask; i += nth) P.sq_seq[i] = i;
+    if (P.lq_seq != nullptr)
+        for (size_t i = tid; i <= P.lq_mask; i += nth) P.lq_seq[i] = i;
     if (P.gq != nullptr) {
         // central queue: slot i holds root i (published: sequence i + 1), the rest are free (sequence i)
         for (size_t i = tid; i <= P.gq_mask; i += nth) {
@@ -68,6 +70,9 @@ __global__ void reset_kernel(KParams P, int init_cq) {
         P.ctl->sc_enq.v = 0;
         P.ctl->sc_deq.v = 0;
         P.ctl->sc_avail.v = 0;
+        P.ctl->lc_enq.v = 0;
+        P.ctl->lc_deq.v = 0;
+        P.ctl->lc_avail.v = 0;
         P.ctl->out_tail.v = 0;
         P.ctl->admitted.v = 0;
         P.ctl->scratch_top.v = 0;

@@ -133,7 +133,8 @@ def test_scale20_full_count_and_64_ranges_match_oracle_golden(rmat20, k):
     gold, _ = _golden(f"kclique_rmat20_k{k}.txt")
     n, e, g = rmat20
     assert (gold["n"], gold["m"]) == (n, g.m)
-    cfg = dict(n_queues=4, route=1, scratch_bytes=4 << 30, deque_capacity=16384)
+    # k = 5 runs about 25 s: a device deadline above that
+    cfg = dict(n_queues=4, route=1, scratch_bytes=4 << 30, deque_capacity=16384, timeout_ns=180 * 10 ** 9)
     assert runner.kclique(g, k, split_threshold=64, **cfg).values == [gold["total"]]
     ranges = [(lo, hi) for lo, hi, _ in gold["ranges"]]
     r = runner.kclique([g] * len(ranges), k, split_threshold=64, ranges=ranges, **cfg)
@@ -164,8 +165,8 @@ def test_batch64_one_launch_matches_oracle_golden():
         assert len(e) == m
         graphs.append(_graph(n, e))
     want = [c for *_, c in gold["graphs"]]
-    # DAQ 4 by depth: the frontier of 64 instances needs rings of 16384 (4096 overflows)
-    cfg = dict(n_queues=4, route=1, scratch_bytes=4 << 30, deque_capacity=16384)
+    # DAQ 4 by depth: the frontier of 64 instances can exceed rings of 16384 on one warp
+    cfg = dict(n_queues=4, route=1, scratch_bytes=4 << 30, deque_capacity=65536)
     r = runner.kclique(graphs, 4, **cfg)
     assert r.values == want
     # the same instances one launch each give the same counts
@@ -204,13 +205,24 @@ def test_pivoting_rmat_against_both_oracles(thr, q, route):
         assert r.values == [want], (k, thr, q)
 
 
-@pytest.mark.parametrize("k", [4, 6])
-def test_pivoting_scale20_golden_ranges(rmat20, k):
-    # the oracle's golden ranges (whole-graph partition for k = 4, sampled ranges for k = 6)
-    name = f"kclique_rmat20_k{k}.txt" if k == 4 else f"kclique_rmat20_k{k}_sampled.txt"
-    gold, _ = _golden(name)
+@pytest.mark.parametrize("k", [6, 7])
+def test_pivoting_scale20_sampled_golden_ranges(rmat20, k):
+    # the oracle's sampled ranges of the scale-20 graph, counted by pivoting (one queue:
+    # the depth-first order bounds the live candidate subgraphs)
+    gold, _ = _golden(f"kclique_rmat20_k{k}_sampled.txt")
     n, e, g = rmat20
     ranges = [(lo, hi) for lo, hi, _ in gold["ranges"]]
-    r = runner.kclique([g] * len(ranges), k, split_threshold=32, ranges=ranges, n_queues=4, route=1,
-                       scratch_bytes=4 << 30, deque_capacity=16384, algorithm=G.GTAP_KCLIQUE_PIVOT)
+    r = runner.kclique([g] * len(ranges), k, split_threshold=32, ranges=ranges, scratch_bytes=8 << 30,
+                       algorithm=G.GTAP_KCLIQUE_PIVOT)
     assert r.values == [c for _, _, c in gold["ranges"]]
+
+
+def test_pivoting_rmat14_deep_cliques_against_orientation():
+    # k = 8 on scale 14: pivoting's task count does not grow with k, orientation's does
+    n, e = inputs.rmat_graph(14, 16, seed=7)
+    g = _graph(n, e)
+    cfg = dict(scratch_bytes=8 << 30, pool_bytes=2 << 30)
+    piv = runner.kclique(g, 8, split_threshold=32, algorithm=G.GTAP_KCLIQUE_PIVOT, **cfg)
+    ori = runner.kclique(g, 8, **cfg)
+    assert piv.values == ori.values
+    assert piv.stats["tasks_created"] < ori.stats["tasks_created"]
