@@ -67,6 +67,11 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # a timed region shorter than the sampling period still gets a sample on
+            # each side: wait for the first one here and for one more in __exit__
+            t0 = time.perf_counter()
+            while not self.samples and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
         return self
@@ -77,6 +82,9 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         if self.proc:
+            n0, t0 = len(self.samples), time.perf_counter()
+            while len(self.samples) == n0 and time.perf_counter() - t0 < 1.0 and self.proc.poll() is None:
+                time.sleep(0.01)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -801,24 +809,26 @@ SERVE_CPU_SAMPLE = 200   # oracle sample: the first requests of the trace
 def _serve_cpu_sample(reqs, n_sample):
     """The oracle answering the first n_sample requests of the trace one after
     another on one core (arrival times ignored, i.e. a saturated server).
-    Returns (requests/s, seconds spent)."""
+    Returns (requests/s, the oracle's answers)."""
     import oracle
     from paper_2604_05982_gb300 import inputs
     oracle.build()
     graphs = {s: inputs.rmat_graph(s, 16, seed=7) for s in range(10, 15)}
     sample = reqs[:n_sample]
+    answers = []
     t0 = time.perf_counter()
     for i, (kind, x) in enumerate(sample):
         if kind == "fib":
-            oracle.fib(x)
+            answers.append(oracle.fib(x)[0])
         elif kind == "nqueens":
-            oracle.nqueens(x)
+            answers.append(oracle.nqueens(x)[0])
         elif kind == "kclique":
-            oracle.kclique(*graphs[x], 4)
+            answers.append(oracle.kclique(*graphs[x], 4))
         else:
-            oracle.uts(seed=1000 + i, root_children=x, m=5)
+            nodes, leaves = oracle.uts(seed=1000 + i, root_children=x, m=5)
+            answers.append((nodes << 32) | leaves)
     secs = time.perf_counter() - t0
-    return len(sample) / secs, secs
+    return len(sample) / secs, answers
 
 
 def _serve_cpu_note(n_sample):
@@ -907,6 +917,9 @@ def run_serve(args):
         t0 = time.perf_counter()
         nxt, ndone = 0, 0
         failure = None
+        # where requests wait: sampled every 2 ms from gtap_serve_progress
+        # (submitted - admitted = inbox backlog; admitted - polled = on the device)
+        backlog, on_device, last_sample = [], [], -1.0
         try:
             while ndone < n_req:
                 now = time.perf_counter() - t0
@@ -925,13 +938,26 @@ def run_serve(args):
                     done_t[i] = time.perf_counter() - t0
                     served_val[i] = r0
                     ndone += 1
+                if now - last_sample >= 0.002:
+                    sub, adm, pol = G.gtap_serve_progress(c.ctx)
+                    backlog.append(sub - adm)
+                    on_device.append(adm - pol)
+                    last_sample = now
         except G.GtapError as exc:
             failure = str(exc)
         finally:
+            progress = G.gtap_serve_progress(c.ctx)
             stop_status = G.load_library().gtap_serve_stop(c.ctx, 60000)
         if failure is not None or stop_status != 0:
-            print(json.dumps({"metric": "served requests/s", "error": failure or G.STATUS.get(stop_status)}), flush=True)
-            return
+            diag = {"submitted_admitted_polled": list(progress)}
+            try:
+                st = c.stats()
+                diag.update({k: st[k] for k in ("frames_high_water", "scratch_used", "tasks_executed")})
+            except Exception as exc:  # the stats of a failed session may be unreadable
+                diag["stats_error"] = str(exc)
+            print(json.dumps({"metric": "served requests/s", "error": failure or G.STATUS.get(stop_status),
+                              "diagnostics": diag}), flush=True)
+            sys.exit(1)
     lat_served = (done_t - arrivals) * 1e3
     span_served = done_t.max() - arrivals[0]
 
@@ -966,13 +992,18 @@ def run_serve(args):
             "latency_ms": {"p50": pct(lat_served, 50), "p99": pct(lat_served, 99), "max": float(lat_served.max())},
             "per_request_launch": {"value": n_req / span_base, "unit": "req/s", "p50_ms": pct(lat_base, 50),
                                    "p99_ms": pct(lat_base, 99)},
-            "results_identical_alone_and_in_mix": bool(identical)}
+            "results_identical_alone_and_in_mix": bool(identical),
+            "waiting": {"inbox_mean": float(np.mean(backlog)), "inbox_max": int(max(backlog)),
+                        "on_device_mean": float(np.mean(on_device)), "on_device_max": int(max(on_device)),
+                        "samples": len(backlog),
+                        "limit": "admission" if np.mean(backlog) > np.mean(on_device) else "device work"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _pin_one_core()
         n_sample = min(SERVE_CPU_SAMPLE, n_req)
-        rps, _ = _serve_cpu_sample(reqs, n_sample)
+        rps, answers = _serve_cpu_sample(reqs, n_sample)
         line["cpu_baseline"] = {"value": rps, "unit": "req/s", "cores": 1, "kind": "oracle",
                                 "sample": _serve_cpu_note(n_sample)}
+        line["oracle_check"] = {"requests": n_sample, "served_equal_oracle": served_val[:n_sample] == answers}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -1130,6 +1161,7 @@ def run_sched(args):
              G.GTAP_SCHED_GLOBAL: "central queue"}
     rows = []
     reps = max(1, min(args.steps, 5))
+    clk = ClockSampler(local).__enter__()
     for sched in names:
         for grid in SCHED_GRIDS:
             with runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=2 << 30, scheduler=sched, grid_blocks=grid,
@@ -1147,6 +1179,7 @@ def run_sched(args):
                 rows.append({"scheduler": names[sched], "grid_blocks": grid, "threads": grid * 256,
                              "kernel_ms": ms, "tasks_per_s": tasks / (ms / 1e3)})
                 print(json.dumps({"progress": rows[-1]}), file=sys.stderr, flush=True)
+    clk.__exit__(None, None, None)
     best = [r for r in rows if r["scheduler"] == "batched stealing" and r["grid_blocks"] == 608][0]
     line = {"metric": "tasks/s", "value": best["tasks_per_s"], "unit": "tasks/s", "n_gpus": world,
             "steps": reps, "warmup": 1, "ms_per_step": best["kernel_ms"], "higher_is_better": True,
@@ -1155,7 +1188,7 @@ def run_sched(args):
                                    "central queue vs non-batched vs batched stealing across grid sizes of "
                                    "256-thread blocks", "parallelism": "replicas"},
             "value_is": "batched stealing at 608 blocks (4 per SM)", "sweep": rows,
-            "gpu_launches": 2 * (1 + reps) * len(rows)}
+            "gpu_launches": 2 * (1 + reps) * len(rows), "clocks": clk.summary()}
     _finish(line, world, rank)
 
 
@@ -1202,6 +1235,7 @@ def run_micro(args):
 
     out = {"iters_sweep": [], "depth_sweep": [], "hetero": []}
     D = 25
+    clk = ClockSampler(local).__enter__()
     for iters in (1, 16, 256, 2048):
         row = {"depth": D, "compute_iters": iters}
         vals = set()
@@ -1236,6 +1270,8 @@ def run_micro(args):
             row["daq_speedup"] = row["thread_nodaq_ms"] / row["thread_daq_ms"]
             out["hetero"].append(row)
             print(json.dumps({"progress": row}), file=sys.stderr, flush=True)
+    clk.__exit__(None, None, None)
+
     # the depth at which thread mode overtakes each block variant
     def crossover(key):
         for r in out["depth_sweep"]:
@@ -1252,7 +1288,7 @@ def run_micro(args):
             "value_is": "thread mode, D = 25, compute_iters = 2048", **out,
             "thread_overtakes_block_at_depth": crossover("block_over_thread"),
             "thread_overtakes_block_cutoff_at_depth": crossover("cutoff_over_thread"),
-            "gpu_launches": 2 * (1 + reps) * (3 * 4 + 3 * 9 + 3 * 6)}
+            "gpu_launches": 2 * (1 + reps) * (3 * 4 + 3 * 9 + 3 * 6), "clocks": clk.summary()}
     _finish(line, world, rank)
 
 

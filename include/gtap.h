@@ -365,8 +365,12 @@ typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; 
  * lowest position; its non-neighbours and itself are the branches; an empty
  * set adds C(pivots, vertices still to choose)); sets of up to 64 vertices are
  * encoded as a bitset subgraph in the scratch arena and their branch range is
- * split over child tasks ("bitset-encoded split"); larger sets branch on each
- * member as in orientation until they fit 64 bits.  Same count either way. */
+ * split over child tasks ("bitset-encoded split"); a first-level set of 65 to
+ * 1024 vertices is pivoted the same way over multi-word bitset rows that its
+ * own task writes into the scratch arena when it starts, and its branch sets
+ * switch to the 64-bit form once they fit.  A first-level set of more than
+ * 1024 vertices fails the run with GTAP_ERR_INVALID_ARG.  Same count as
+ * orientation. */
 #define GTAP_KCLIQUE_ORIENT 0
 #define GTAP_KCLIQUE_PIVOT 1
 typedef struct { const int64_t* off; const int32_t* adj; const int32_t* src;

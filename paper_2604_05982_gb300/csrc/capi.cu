@@ -723,6 +723,9 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
         P.hflags = c->hflags_dev;
         P.host_abort = &c->hflags_dev->abort;
         P.admit_reserve = std::max<uint64_t>(P.n_frames / 64, 4096);
+        // every request slot starts free (all bytes 0xFF: done == kRootSlotFree)
+        if (cudaMemsetAsync(c->roots, 0xFF, (size_t)c->cfg.max_roots * sizeof(RootEntry), s) != cudaSuccess)
+            return GTAP_ERR_CUDA;
     }
     record(c->ev_k0);
     cudaError_t e = (c->mode == GTAP_MODE_THREAD)

@@ -55,6 +55,14 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ uint32_t ld_acquire_u32(const unsigned int* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -578,6 +586,8 @@ struct TaskCtx {
                 o->seq = pos + 1;
                 __threadfence_system();
                 atomicAdd(&P.ctl->inflight.v, ~0ull);
+                // every task of the request has completed: its root slot may be reused
+                st_release_u32(&r->done, kRootSlotFree);
             } else {
                 if (flags & kFlagAccumulate) atomicAdd(&r->result[slot & 1], v);
                 else st_cg64(&r->result[slot & 1], v);
@@ -618,8 +628,24 @@ static __device__ void serve_poller(const KParams& P, const WarpSh& ws, int* fto
     int ftop = *ftop_io;
     unsigned long long next = 0;              // next inbox sequence to take
     int backoff = 64;
+    // a root slot is free when its `done` word holds kRootSlotFree (completions
+    // release it); the poller is the only taker, so a slot it found free stays
+    // free until it admits a request into it
+    int rslot = -1;
+    uint32_t cursor = 0;
     for (uint32_t iter = 0;; ++iter) {
         ftop = pool_refill(P, ws.fstack, ftop, 32);
+        if (rslot < 0) {
+            const uint32_t cand = (cursor + (uint32_t)lane) % P.n_roots;
+            const bool fr = ld_acquire_u32(&P.roots[cand].done) == kRootSlotFree;
+            const unsigned m = __ballot_sync(0xffffffffu, fr);
+            if (m) {
+                rslot = (int)((cursor + (uint32_t)(__ffs((int)m) - 1)) % P.n_roots);
+                cursor = ((uint32_t)rslot + 1u) % P.n_roots;
+            } else {
+                cursor = (cursor + 32u) % P.n_roots;
+            }
+        }
         int stop = 0, took = 0;
         if (lane == 0) {
             volatile HostFlags* hf = P.hflags;
@@ -638,10 +664,9 @@ static __device__ void serve_poller(const KParams& P, const WarpSh& ws, int* fto
                     const uint32_t q = slot->queue % (uint32_t)Q;
                     const bool room = ws.tail[q] - ws.head_lb[q] + 1u <= cap_mask + 1 ||
                                       ws.tail[q] - (ws.head_lb[q] = __ldcg(&myq[q].head)) + 1u <= cap_mask + 1;
-                    if (free_records >= P.admit_reserve && ftop > 0 && inflight < P.n_roots &&
+                    if (free_records >= P.admit_reserve && ftop > 0 && inflight < P.n_roots && rslot >= 0 &&
                         inflight + unread < P.outbox_cap && room) {
-                        const unsigned long long adm = ld_cg64(&P.ctl->admitted.v);
-                        const uint32_t r = (uint32_t)(adm % P.n_roots);
+                        const uint32_t r = (uint32_t)rslot;
                         const uint32_t id = ws.fstack[--ftop];
                         const uint32_t type = slot->type;
                         // root environment (read by programs with per-root buffers)
@@ -686,6 +711,7 @@ static __device__ void serve_poller(const KParams& P, const WarpSh& ws, int* fto
         ftop = __shfl_sync(0xffffffffu, ftop, 0);
         if (stop) break;
         if (took) {
+            rslot = -1;
             backoff = 64;
         } else {
             __nanosleep(backoff);

@@ -118,6 +118,9 @@ struct DevControl {
     alignas(128) ErrorRecord err;
 };
 
+// Serving: a root slot whose `done` word holds this value is free for a new request.
+constexpr unsigned int kRootSlotFree = 0xFFFFFFFFu;
+
 struct RootEntry {
     unsigned long long result[2];
     unsigned int done;
