@@ -70,7 +70,7 @@ int block_kernel_maxspawn(unsigned pset, int bs) {
 
 size_t block_prog_smem(unsigned pset, int bs) {
     size_t b = 0;
-    if (pset & PS_MSORT) b = std::max(b, (size_t)(2 * kMsPadded * 4 + 8 * 260));
+    if (pset & PS_MSORT) b = std::max(b, (size_t)(kMsStages * kMsStride * 4 + 8 * 260));
     if (pset & PS_INTEGRATE_BLK) b = std::max(b, (size_t)(8 * bs));
     if (pset & PS_DTT) b = std::max(b, sizeof(DttShared) + 16);
     if (pset & PS_BINTREE_BLK) b = std::max(b, (size_t)(8 * 32));

@@ -44,6 +44,8 @@ __device__ __forceinline__ unsigned long long merge_path(unsigned long long na, 
 // element t*ITEMS + k (a stride of ITEMS words) touches 32 different banks.
 __device__ __forceinline__ int padx(int i) { return i + (i >> 5); }
 constexpr int kMsPadded = kMsTile + kMsTile / 32;
+// a tile buffer plus room for the merge windows' reads past the tile's last key
+constexpr int kMsStride = kMsPadded + 32;
 
 // Merge path inside shared memory (padded layout): how many of A's elements
 // precede output position d; equal keys come from A first.
@@ -89,49 +91,53 @@ __device__ __forceinline__ int smem_merge_path(const uint32_t* sa, int na, const
     return lo;
 }
 
-// Serially merge `count` outputs starting at (i, j) of runs A = s[a0 .. a0+na),
-// B = s[b0 .. b0+nb) into registers.  Branch-free: each output is a select,
-// and only the run that advanced is read again (one shared load per output).
+// ITEMS consecutive keys of a padded shared-memory run starting at index
+// `base`; positions at or past `valid` read as 0xFFFFFFFF.  The window crosses
+// at most one 32-word pad boundary, found once.  Reads may go up to
+// ITEMS - 1 words past the run (the callers' buffers leave room for that).
 template <int ITEMS>
-__device__ __forceinline__ void smem_serial_merge(const uint32_t* s, int a0, int na, int b0, int nb, int i, int j,
-                                                  int count, uint32_t (&out)[ITEMS]) {
-    uint32_t av = (i < na) ? s[padx(a0 + i)] : 0xFFFFFFFFu;
-    uint32_t bv = (j < nb) ? s[padx(b0 + j)] : 0xFFFFFFFFu;
-    bool a_ok = i < na, b_ok = j < nb;
+__device__ __forceinline__ void smem_window(const uint32_t* s, int base, int valid, uint32_t (&w)[ITEMS]) {
+    const uint32_t* p = s + base + (base >> 5);
+    const int cross = 32 - (base & 31);   // first window offset past the next pad word
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        const bool takeA = a_ok && (!b_ok || av <= bv);
-        out[k] = takeA ? av : bv;
-        i += takeA ? 1 : 0;
-        j += takeA ? 0 : 1;
-        const bool more = takeA ? (i < na) : (j < nb);
-        const int at = takeA ? a0 + i : b0 + j;
-        const uint32_t nv = (more && k + 1 < count) ? s[padx(at)] : 0xFFFFFFFFu;
-        if (takeA) { av = nv; a_ok = more; } else { bv = nv; b_ok = more; }
+        const uint32_t x = p[k + (k >= cross ? 1 : 0)];
+        w[k] = (k < valid) ? x : 0xFFFFFFFFu;
     }
 }
 
-// One block merges A[0,na) and B[0,nb) (na + nb <= kMsTile) into out, via shared memory.
-template <int BS>
-__device__ void block_merge_tile(const uint32_t* A, int na, const uint32_t* B, int nb, uint32_t* out, uint32_t* sh) {
-    constexpr int kItems = kMsTile / BS;
-    uint32_t* shin = sh;                 // padded: A at [0, na), B at [na, na + nb)
-    uint32_t* shout = sh + kMsPadded;    // padded
-    const int t = threadIdx.x;
-    for (int i = t; i < na; i += BS) shin[padx(i)] = __ldcg(A + i);
-    for (int i = t; i < nb; i += BS) shin[padx(na + i)] = __ldcg(B + i);
-    __syncthreads();
-    const int total = na + nb;
-    const int d0 = min(t * kItems, total), d1 = min(d0 + kItems, total);
-    const int i = smem_merge_path(shin, na, shin, nb, d0, 0, na);
-    uint32_t v[kItems];
-    smem_serial_merge<kItems>(shin, 0, na, na, nb, i, d0 - i, d1 - d0, v);
+// The N smallest of two ascending sequences a and b, ascending, into a.  The
+// element-wise minimum of a and reversed b holds exactly the N smallest of the
+// 2N keys and is bitonic (Batcher's bitonic merge, first half-cleaner); the
+// remaining half-cleaners sort it.  Only key values are produced, so which of
+// two equal keys is taken does not matter.
+template <int N>
+__device__ __forceinline__ void lowest_of_two_sorted(uint32_t (&a)[N], const uint32_t (&b)[N]) {
 #pragma unroll
-    for (int k = 0; k < kItems; ++k)
-        if (d0 + k < d1) shout[padx(d0 + k)] = v[k];
-    __syncthreads();
-    for (int k = t; k < total; k += BS) out[k] = shout[padx(k)];
-    __syncthreads();
+    for (int k = 0; k < N; ++k) a[k] = min(a[k], b[N - 1 - k]);
+#pragma unroll
+    for (int j = N / 2; j > 0; j >>= 1) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            if ((k & j) == 0) {
+                const uint32_t x = a[k], y = a[k + j];
+                a[k] = min(x, y);
+                a[k + j] = max(x, y);
+            }
+        }
+    }
+}
+
+// The ITEMS outputs of merge-path position d of the runs A = s[a0, a0 + na)
+// and B = s[b0, b0 + nb) (padded indices), i of them taken from A: the lowest
+// ITEMS keys of the windows A[i, i + ITEMS) and B[d - i, d - i + ITEMS).
+template <int ITEMS>
+__device__ __forceinline__ void smem_window_merge(const uint32_t* s, int a0, int na, int b0, int nb, int i, int d,
+                                                  uint32_t (&out)[ITEMS]) {
+    uint32_t w[ITEMS];
+    smem_window<ITEMS>(s, a0 + i, na - i, out);
+    smem_window<ITEMS>(s, b0 + (d - i), nb - (d - i), w);
+    lowest_of_two_sorted<ITEMS>(out, w);
 }
 
 // Sort of n <= 4096 keys by one block: every thread sorts kItems keys in
@@ -168,15 +174,18 @@ __device__ void block_sort_leaf(const uint32_t* src, int n, uint32_t* dst, uint3
     for (int k = 0; k < kItems; ++k) x[k] = sh[padx(t * kItems + k)];
     sort_registers<kItems>(x);
     for (int run = kItems; run < kMsMaxLeaf; run <<= 1) {
-        __syncthreads();
+        // while a merged pair of runs lies inside one warp's 32 * kItems keys, the
+        // warp reads and writes only its own keys: a warp barrier is enough
+        const bool warp_local = 2 * run <= 32 * kItems;
+        if (warp_local) __syncwarp(); else __syncthreads();
 #pragma unroll
         for (int k = 0; k < kItems; ++k) sh[padx(t * kItems + k)] = x[k];
-        __syncthreads();
+        if (warp_local) __syncwarp(); else __syncthreads();
         const int o = t * kItems;
         const int base = o & ~(2 * run - 1);
         const int d = o - base;
         const int i = smem_merge_path(sh, run, sh, run, d, base, base + run);
-        smem_serial_merge<kItems>(sh, base, run, base + run, run, i, d - i, kItems, x);
+        smem_window_merge<kItems>(sh, base, run, base + run, run, i, d, x);
     }
     __syncthreads();
 #pragma unroll
@@ -215,13 +224,25 @@ __device__ void msort_fork_merge(BTaskCtx& c, const gtap_mergesort_args& e, uint
     __syncthreads();
 }
 
+// Asynchronous 4-byte global -> shared copy (cp.async, cached in L1 on the way);
+// completion is tracked per thread by commit groups.
+__device__ __forceinline__ void cp_async4(uint32_t* sdst, const uint32_t* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+constexpr int kMsStages = 3;   // shared-memory tiles of a merge piece in flight (one merged, two loading)
+
 // Merge one piece directly (<= merge_cutoff output keys), tile by tile.
 template <int BS>
 __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uint32_t flags, unsigned long long a_lo,
                                   unsigned long long a_hi, unsigned long long b_lo, unsigned long long b_hi,
                                   unsigned long long out_lo) {
     uint32_t* sh = c.prog_smem<uint32_t>();
-    unsigned long long* split = reinterpret_cast<unsigned long long*>(sh + 2 * kMsPadded);
+    unsigned long long* split = reinterpret_cast<unsigned long long*>(sh + kMsStages * kMsStride);
     const uint32_t* X = msort_buf(e, flags & 1u);
     uint32_t* Y = msort_buf(e, flags & 2u);
     const unsigned long long na = a_hi - a_lo, nb = b_hi - b_lo, total = na + nb;
@@ -243,13 +264,13 @@ __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uin
         split[1] = na;
     }
     __syncthreads();
-    // Software pipeline over the piece's tiles: the next tile's keys are loaded
-    // into registers while the current tile is merged from shared memory, and
-    // merged keys go straight from registers to global memory.
+    // Pipeline over the piece's tiles: a ring of kMsStages shared-memory tiles
+    // filled by cp.async; tile k + 2 is requested while tile k is merged, and
+    // merged keys go straight from registers to global memory.  One barrier
+    // per tile: after it every thread's copies of tile k are visible and every
+    // thread has finished merging tile k - 1, whose buffer tile k + 2 reuses.
     constexpr int kItems = kMsTile / BS;
     const int t = threadIdx.x;
-    uint32_t* buf[2] = {sh, sh + kMsPadded};
-    uint32_t pre[kItems];
     auto tile_bounds = [&](int k, int& tna, int& tnb, unsigned long long& i0, unsigned long long& j0) {
         const unsigned long long d0 = (unsigned long long)k * kMsTile, d1 = min(total, d0 + kMsTile);
         i0 = split[k];
@@ -258,34 +279,37 @@ __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uin
         tna = (int)(i1 - i0);
         tnb = (int)((d1 - i1) - j0);
     };
-    auto load_tile = [&](int k) {   // element t + r*BS of the tile's input (A part, then B part)
-        int tna, tnb;
-        unsigned long long i0, j0;
-        tile_bounds(k, tna, tnb, i0, j0);
+    auto issue_tile = [&](int k) {   // element t + r*BS of the tile's input (A part, then B part)
+        if (k < tiles) {
+            int tna, tnb;
+            unsigned long long i0, j0;
+            tile_bounds(k, tna, tnb, i0, j0);
+            uint32_t* dstb = sh + (k % kMsStages) * kMsStride;
+            const uint32_t* ga = A + i0;
+            const uint32_t* gb = B + j0 - tna;
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
-            const int e = t + r * BS;
-            pre[r] = (e < tna) ? __ldcg(A + i0 + e) : ((e < tna + tnb) ? __ldcg(B + j0 + (e - tna)) : 0u);
+            for (int r = 0; r < kItems; ++r) {
+                const int el = t + r * BS;
+                if (el < tna + tnb) cp_async4(dstb + padx(el), (el < tna ? ga : gb) + el);
+            }
         }
+        cp_async_commit();   // an empty group past the last tile keeps the group count uniform
     };
-    auto store_tile = [&](uint32_t* dstb) {
-#pragma unroll
-        for (int r = 0; r < kItems; ++r) dstb[padx(t + r * BS)] = pre[r];
-    };
-    load_tile(0);
-    store_tile(buf[0]);
-    __syncthreads();
+    issue_tile(0);
+    issue_tile(1);
     for (int k = 0; k < tiles; ++k) {
-        if (k + 1 < tiles) load_tile(k + 1);   // in flight during this tile's merge
+        cp_async_wait<1>();   // this thread's copies of tile k have landed
+        __syncthreads();
+        issue_tile(k + 2);
         int tna, tnb;
         unsigned long long i0, j0;
         tile_bounds(k, tna, tnb, i0, j0);
-        const uint32_t* cur = buf[k & 1];
+        const uint32_t* cur = sh + (k % kMsStages) * kMsStride;
         const int ttot = tna + tnb;
         const int d0 = min(t * kItems, ttot), d1 = min(d0 + kItems, ttot);
         const int i = smem_merge_path(cur, tna, cur, tnb, d0, 0, tna);
         uint32_t v[kItems];
-        smem_serial_merge<kItems>(cur, 0, tna, tna, tnb, i, d0 - i, d1 - d0, v);
+        smem_window_merge<kItems>(cur, 0, tna, tna, tnb, i, d0, v);
         uint32_t* o = Y + out_lo + (unsigned long long)k * kMsTile + d0;
         if (d1 - d0 == kItems && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
 #pragma unroll
@@ -295,9 +319,9 @@ __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uin
             for (int r = 0; r < kItems; ++r)
                 if (d0 + r < d1) o[r] = v[r];
         }
-        if (k + 1 < tiles) store_tile(buf[(k + 1) & 1]);
-        __syncthreads();
     }
+    cp_async_wait<0>();
+    __syncthreads();   // the buffers are free for the block's next task
 }
 
 template <int BS>
