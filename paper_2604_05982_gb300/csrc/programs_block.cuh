@@ -234,7 +234,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
-constexpr int kMsStages = 3;   // shared-memory tiles of a merge piece in flight (one merged, two loading)
+constexpr int kMsStages = 3;   // shared-memory tiles of a merge piece in flight (one merged, the rest loading)
 
 // Merge one piece directly (<= merge_cutoff output keys), tile by tile.
 template <int BS>
@@ -265,10 +265,11 @@ __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uin
     }
     __syncthreads();
     // Pipeline over the piece's tiles: a ring of kMsStages shared-memory tiles
-    // filled by cp.async; tile k + 2 is requested while tile k is merged, and
-    // merged keys go straight from registers to global memory.  One barrier
-    // per tile: after it every thread's copies of tile k are visible and every
-    // thread has finished merging tile k - 1, whose buffer tile k + 2 reuses.
+    // filled by cp.async; tile k + kMsStages - 1 is requested while tile k is
+    // merged, and merged keys go straight from registers to global memory.
+    // One barrier per tile: after it every thread's copies of tile k are
+    // visible and every thread has finished merging tile k - 1, whose buffer
+    // the newly requested tile reuses.
     constexpr int kItems = kMsTile / BS;
     const int t = threadIdx.x;
     auto tile_bounds = [&](int k, int& tna, int& tnb, unsigned long long& i0, unsigned long long& j0) {
@@ -295,12 +296,12 @@ __device__ void msort_merge_piece(BTaskCtx& c, const gtap_mergesort_args& e, uin
         }
         cp_async_commit();   // an empty group past the last tile keeps the group count uniform
     };
-    issue_tile(0);
-    issue_tile(1);
+#pragma unroll
+    for (int k = 0; k < kMsStages - 1; ++k) issue_tile(k);
     for (int k = 0; k < tiles; ++k) {
-        cp_async_wait<1>();   // this thread's copies of tile k have landed
+        cp_async_wait<kMsStages - 2>();   // this thread's copies of tile k have landed
         __syncthreads();
-        issue_tile(k + 2);
+        issue_tile(k + kMsStages - 1);
         int tna, tnb;
         unsigned long long i0, j0;
         tile_bounds(k, tna, tnb, i0, j0);
