@@ -160,23 +160,53 @@ static __device__ __noinline__ void raise_error(const KParams& P, int code, int 
 }
 
 // Debug event log: code:4 | lane:5 | worker:15 | iteration:24 | aux:16.
-__device__ __forceinline__ void dbg_log(const KParams& P, uint32_t id, unsigned code, int worker, uint32_t iter,
-                                        unsigned aux) {
-    if (P.flog == nullptr || id >= P.n_frames) return;
+// The debug paths below run only in debug contexts; their bodies are kept out
+// of line so that the scheduler loops' hot code stays compact.
+static __device__ __noinline__ void dbg_log_record(const KParams& P, uint32_t id, unsigned code, int worker,
+                                                   uint32_t iter, unsigned aux) {
+    if (id >= P.n_frames) return;
     unsigned k = atomicAdd(&P.flogn[id], 1u);
     unsigned long long ev = ((unsigned long long)code << 60) | ((unsigned long long)(threadIdx.x & 31) << 55) |
                             ((unsigned long long)(worker & 0x7FFF) << 40) | ((unsigned long long)(iter & 0xFFFFFF) << 16) |
                             (aux & 0xFFFF);
     P.flog[(size_t)id * 8 + (k & 7)] = ev;
 }
+__device__ __forceinline__ void dbg_log(const KParams& P, uint32_t id, unsigned code, int worker, uint32_t iter,
+                                        unsigned aux) {
+    if (P.flog != nullptr) dbg_log_record(P, id, code, worker, iter, aux);
+}
 
 // Debug checks on record ownership (only when P.fstate is set).
-__device__ __forceinline__ void dbg_transition(const KParams& P, uint32_t id, unsigned from, unsigned to,
-                                               unsigned long long fault, int type, int worker) {
-    if (P.fstate == nullptr) return;
+static __device__ __noinline__ void dbg_transition_check(const KParams& P, uint32_t id, unsigned from, unsigned to,
+                                                         unsigned long long fault, int type, int worker) {
     if (id >= P.n_frames) { raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, (DBG_BAD_ID << 32) | id); return; }
     unsigned old = atomicCAS(&P.fstate[id], from, to);
     if (old != from) raise_error(P, GTAP_ERR_TASK_FAILED, type, worker, (fault << 32) | id);
+}
+__device__ __forceinline__ void dbg_transition(const KParams& P, uint32_t id, unsigned from, unsigned to,
+                                               unsigned long long fault, int type, int worker) {
+    if (P.fstate != nullptr) dbg_transition_check(P, id, from, to, fault, type, worker);
+}
+// A task ID taken from a ring slot: the slot is cleared so that a second take of it is caught.
+static __device__ __noinline__ void dbg_take_slot(const KParams& P, uint32_t* slot, uint32_t tid, int code, int worker) {
+    uint32_t was = atomicExch(slot, kNoTask);
+    if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, code, worker, (DBG_BAD_ID << 32) | was);
+}
+// A task about to run must be queued (3); it becomes running (2).
+static __device__ __noinline__ void dbg_exec_check(const KParams& P, uint32_t tid, int src, int worker) {
+    unsigned old = (tid < P.n_frames) ? atomicCAS(&P.fstate[tid], 3u, 2u) : 99u;
+    if (old != 3u) raise_error(P, GTAP_ERR_TASK_FAILED, (int)(old * 16 + src), worker, (DBG_EXEC_NOT_ALLOCATED << 32) | tid);
+}
+// A record is queued only from "allocated" (1), or from "running" (2) by itself; returns true
+// when the running task staged itself.
+static __device__ __noinline__ bool dbg_stage_check(const KParams& P, uint32_t id, uint32_t self, uint32_t parent,
+                                                    int worker) {
+    unsigned old = atomicCAS(&P.fstate[id], 1u, 3u);
+    if (old == 1u) return false;
+    if (id == self && old == 2u && atomicCAS(&P.fstate[id], 2u, 3u) == 2u) return true;
+    raise_error(P, GTAP_ERR_TASK_FAILED, (int)(200 + old * 16 + (id == self ? 1 : 0) + (id == parent ? 2 : 0)), worker,
+                (5ull << 32) | id);
+    return false;
 }
 
 __device__ __forceinline__ bool abort_requested(const KParams& P, bool check_host) {
@@ -510,14 +540,7 @@ struct TaskCtx {
         return ws.fstack[t];
     }
     __device__ void stage(uint32_t id, int q) {
-        if (P.fstate != nullptr) {
-            // debug: a record is queued only from "allocated" (1), or from "running" (2) by itself
-            unsigned old = atomicCAS(&P.fstate[id], 1u, 3u);
-            if (old != 1u) {
-                if (id == self && old == 2u && atomicCAS(&P.fstate[id], 2u, 3u) == 2u) staged_self = true;
-                else raise_error(P, GTAP_ERR_TASK_FAILED, (int)(200 + old * 16 + (id == self ? 1 : 0) + (id == h.parent ? 2 : 0)), worker, (5ull << 32) | id);
-            }
-        }
+        if (P.fstate != nullptr && dbg_stage_check(P, id, self, h.parent, worker)) staged_self = true;
         dbg_log(P, id, 2, worker, iter, id == self ? 1u : (id == h.parent ? 2u : 0u));
         q = (P.n_queues > 1) ? (int)((unsigned)q % P.n_queues) : 0;
         int p = atomicAdd(&ws.ctrl[2], 1);
@@ -619,7 +642,7 @@ struct TaskCtx {
 // and pushes it on its own deque, from which the other warps steal it.
 // Requests that arrive while others run are admitted as records and root
 // slots free up, so their work overlaps on the device (continuous batching).
-static __device__ void serve_poller(const KParams& P, const WarpSh& ws, int* ftop_io) {
+static __device__ __noinline__ void serve_poller(const KParams& P, const WarpSh& ws, int* ftop_io) {
     const int lane = threadIdx.x & 31;
     const int Q = (int)P.n_queues;
     const uint32_t cap_mask = P.ring_mask;
@@ -896,10 +919,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                             tid = __ldcg(slot);
                             src = 1;
                             dbg_log(P, tid, 7, wid, iter, (t + (uint32_t)(lane - cnt)) & 0xFFFF);
-                            if (P.fstate != nullptr) {
-                                uint32_t was = atomicExch(slot, kNoTask);
-                                if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 1, wid, (DBG_BAD_ID << 32) | was);
-                            }
+                            if (P.fstate != nullptr) dbg_take_slot(P, slot, tid, 100 + 1, wid);
                         }
                         __syncwarp();
                         if (lane == 0) ws.tail[q] = t;
@@ -1023,10 +1043,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
                             tid = __ldcg(slot);
                             src = 2;
                             dbg_log(P, tid, 8, wid, iter, (unsigned)victim & 0xFFFF);
-                            if (P.fstate != nullptr) {
-                                uint32_t was = atomicExch(slot, kNoTask);
-                                if (was != tid || tid == kNoTask) raise_error(P, GTAP_ERR_TASK_FAILED, 100 + 2, wid, (DBG_BAD_ID << 32) | was);
-                            }
+                            if (P.fstate != nullptr) dbg_take_slot(P, slot, tid, 100 + 2, wid);
                         }
                         // every claimed ID is in a register before the head moves (wrap-around safety, Sec. 5.1.3)
                         const uint32_t used = __reduce_or_sync(0xffffffffu, (lane >= cnt && lane < cnt + claim) ? tid : 0u);
@@ -1086,10 +1103,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
         // ---- Execute: lanes [0, cnt) run one step of their task.
         int spawned = 0;
         if (lane < cnt) {
-            if (P.fstate != nullptr) {
-                unsigned old = (tid < P.n_frames) ? atomicCAS(&P.fstate[tid], 3u, 2u) : 99u;
-                if (old != 3u) raise_error(P, GTAP_ERR_TASK_FAILED, (int)(old * 16 + src), wid, (DBG_EXEC_NOT_ALLOCATED << 32) | tid);
-            }
+            if (P.fstate != nullptr) dbg_exec_check(P, tid, src, wid);
             TaskCtx c(P, ws, tid, wid);
             c.iter = iter;
             dbg_log(P, tid, 3, wid, iter, (unsigned)c.pc() | ((unsigned)src << 8));

@@ -68,7 +68,10 @@ def main(argv=None):
                     c.spawn(t, G.gtap_mergesort_args(src.data_ptr() + o, dst.data_ptr() + o, tmp.data_ptr() + o,
                                                      sub, 4096, 65536))
                 c.run()
-                print("mergesort", n, sub, c.stats()["kernel_ms"])
+                st = c.stats()
+                # block-loop phase cycles per block (acquire, task bodies, post-step, idle), in ms at the max SM clock
+                ph = [st[k] / st["n_workers"] / 2.07e6 for k in ("cycles_pop", "cycles_exec", "cycles_push", "cycles_idle")]
+                print("mergesort", n, sub, st["kernel_ms"], "phases_ms acquire %.3f body %.3f post %.3f idle %.3f" % tuple(ph))
         out = dst.cpu().numpy().view(np.uint32).reshape(-1, sub)
         assert np.all(out[:, 1:] >= out[:, :-1])
     elif args.case == "kclique":
