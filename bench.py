@@ -677,7 +677,7 @@ def run_reference_kclique(args):
         return
     from paper_2604_05982_gb300 import inputs
     _pin_one_core()
-    n, e = inputs.rmat_graph(KC_SCALE, 16, seed=7)
+    n, e = inputs.rmat_graph(args.scale, 16, seed=7)
     for _ in range(min(args.warmup, 1)):
         _kclique_cpu_sample(n, e, args.k)
     vals = [_kclique_cpu_sample(n, e, args.k)[0] for _ in range(args.steps)]
@@ -685,7 +685,7 @@ def run_reference_kclique(args):
     line = {"impl": "reference", "metric": "k-clique time", "value": value, "unit": "ms/instance", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"{args.k}-clique count, R-MAT scale {KC_SCALE} edge factor 16, seed 7 (oracle)"},
+            "config": {"workload": f"{args.k}-clique count, R-MAT scale {args.scale} edge factor 16, seed 7 (oracle)"},
             "cpu_baseline": {"value": value, "unit": "ms/instance", "cores": 1, "kind": "oracle",
                              "sample": _kclique_cpu_note(len(e), args.k)},
             "e2e": {"value": value, "unit": "ms/instance", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -706,7 +706,7 @@ def run_kclique(args):
     torch.cuda.set_device(local)
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    n, e = inputs.rmat_graph(KC_SCALE, 16, seed=7)
+    n, e = inputs.rmat_graph(args.scale, 16, seed=7)
     edges = torch.from_numpy(np.ascontiguousarray(e)).cuda()
     m = int(edges.shape[0])
     off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
@@ -718,14 +718,17 @@ def run_kclique(args):
     thr = 32 if algo == G.GTAP_KCLIQUE_PIVOT else 64
     kargs = G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), 0, m, args.k, thr, 1, algo)
     big = args.k > 4 or args.algorithm == "pivot"   # larger frontier: rings of 16384, 4 GiB pool
-    pool, scratch = (4 << 30, 4 << 30) if big else (1 << 30, 4 << 30)
+    pool = 4 << 30 if big else 1 << 30
+    # pivoting keeps a bitset subgraph per split set: its scratch high-water mark is far above orientation's
+    scratch = (48 << 30) if args.algorithm == "pivot" else (4 << 30)
     ring = 16384 if big else 4096
+    deadline_ns = (600 if big else 60) * 10 ** 9   # device deadline of one counting run
 
     def step():
         G.gtap_kclique_orient(edges.data_ptr(), m, n, off.data_ptr(), adj.data_ptr(), src.data_ptr(),
                               work.data_ptr(), 0)
         with runner.Context(G.GTAP_MODE_THREAD, KC_QUEUES, pool_bytes=pool, scratch_bytes=scratch,
-                            deque_capacity=ring) as c:
+                            deque_capacity=ring, timeout_ns=deadline_ns) as c:
             t = c.register("kclique")
             h = c.spawn(t, kargs)
             c.run()
@@ -736,7 +739,7 @@ def run_kclique(args):
     # parity (outside the timed region): the full count against the oracle's golden value
     # (tests/golden, written from the oracle alone) where one exists, and sampled DAG-edge
     # ranges against the oracle run here
-    gold = _kclique_golden(f"kclique_rmat{KC_SCALE}_k{args.k}.txt")
+    gold = _kclique_golden(f"kclique_rmat{args.scale}_k{args.k}.txt")
     if gold is not None:
         assert count == gold["total"], (count, gold["total"])
     if args.k <= 4:
@@ -745,13 +748,13 @@ def run_kclique(args):
         # larger k: the oracle's cost per edge explodes at the dense low-id end, so sample the rest
         ranges = [(lo, lo + 64) for lo in ((2 * m) // 3, (5 * m) // 6)] + [(m - 200, m)]
     want = [oracle.kclique_edge_range(n, e, args.k, lo, hi) for lo, hi in ranges]
-    sampled = _kclique_golden(f"kclique_rmat{KC_SCALE}_k{args.k}_sampled.txt")
+    sampled = _kclique_golden(f"kclique_rmat{args.scale}_k{args.k}_sampled.txt")
     if sampled is not None:
         # the oracle's sampled ranges over the whole graph (written ahead by the golden script)
         ranges += [(lo, hi) for lo, hi, _ in sampled["ranges"]]
         want += [cnt for _, _, cnt in sampled["ranges"]]
     with runner.Context(G.GTAP_MODE_THREAD, 4, pool_bytes=pool, scratch_bytes=scratch, deque_capacity=ring,
-                        max_roots=max(4096, len(ranges))) as c:
+                        max_roots=max(4096, len(ranges)), timeout_ns=deadline_ns) as c:
         t = c.register("kclique")
         hs = [c.spawn(t, G.gtap_kclique_args(off.data_ptr(), adj.data_ptr(), src.data_ptr(), lo, hi, args.k, thr, 1,
                                              algo))
@@ -776,7 +779,7 @@ def run_kclique(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"{args.k}-clique count by {'pivoting' if algo else 'orientation'}, R-MAT scale "
-                               f"{KC_SCALE} edge factor 16 (a,b,c=0.57,0.19,0.19, seed 7, {m} undirected edges), "
+                               f"{args.scale} edge factor 16 (a,b,c=0.57,0.19,0.19, seed 7, {m} undirected edges), "
                                f"degree-ordered DAG, thread mode, DAQ {KC_QUEUES} queues by recursion depth, split "
                                f"threshold {thr}; one step = orientation + gtap_init + run + gtap_finalize (wall "
                                "clock, synchronised)", "parallelism": "replicas",
@@ -1410,6 +1413,7 @@ def main():
                          "launches; sched: scheduler comparison on fib(35); micro: mode/DAQ binary-tree sweeps")
     ap.add_argument("--requests", type=int, default=SERVE_REQUESTS)
     ap.add_argument("--k", type=int, default=KC_K, choices=[4, 5, 6, 7], help="kclique: clique size")
+    ap.add_argument("--scale", type=int, default=KC_SCALE, help="kclique: R-MAT scale of the graph (default 20)")
     ap.add_argument("--algorithm", default="orient", choices=["orient", "pivot"],
                     help="kclique: orientation or pivoting (Sec. 6.4.2)")
     ap.add_argument("--fmm-precision", default="mixed", choices=["mixed", "fp64"])

@@ -300,17 +300,17 @@ static __device__ int kc_intersect(const int* a, int na, LA la, const int* b, in
             if (lo < na && la(a + lo) == x) { if (out && cnt < cap) out[cnt] = x; ++cnt; ++lo; }
         }
     } else {
+        // branch-free merge: lanes of a warp with different data take the same path
+        // every iteration (only the trip counts differ)
         int i = 0, j = 0;
-        int x = la(a), y = lb(b);
-        while (true) {
-            if (x < y) { if (++i == na) break; x = la(a + i); }
-            else if (y < x) { if (++j == nb) break; y = lb(b + j); }
-            else {
+        while (i < na && j < nb) {
+            const int x = la(a + i), y = lb(b + j);
+            if (x == y) {
                 if (out && cnt < cap) out[cnt] = x;
                 ++cnt;
-                if (++i == na || ++j == nb) break;
-                x = la(a + i); y = lb(b + j);
             }
+            i += (x <= y) ? 1 : 0;
+            j += (y <= x) ? 1 : 0;
         }
     }
     return cnt;
@@ -337,11 +337,11 @@ static __device__ unsigned long long kc_count_small(const int* S, int ns, int j,
             }
         } else {
             int i = 0, b = 0;
-            while (i < len && b < ns) {
+            while (i < len && b < ns) {   // branch-free merge
                 const int x = __ldg(nb + i), y = S[b];
-                if (x < y) ++i;
-                else if (y < x) ++b;
-                else { bits |= 1ull << b; ++i; ++b; }
+                bits |= (x == y) ? (1ull << b) : 0ull;
+                i += (x <= y) ? 1 : 0;
+                b += (y <= x) ? 1 : 0;
             }
         }
         row[a] = bits;
