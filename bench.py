@@ -923,6 +923,7 @@ def run_serve(args):
         # where requests wait: sampled every 2 ms from gtap_serve_progress
         # (submitted - admitted = inbox backlog; admitted - polled = on the device)
         backlog, on_device, last_sample = [], [], -1.0
+        clk = ClockSampler(local).__enter__()
         try:
             while ndone < n_req:
                 now = time.perf_counter() - t0
@@ -949,6 +950,7 @@ def run_serve(args):
         except G.GtapError as exc:
             failure = str(exc)
         finally:
+            clk.__exit__(None, None, None)
             progress = G.gtap_serve_progress(c.ctx)
             stop_status = G.load_library().gtap_serve_stop(c.ctx, 60000)
         if failure is not None or stop_status != 0:
@@ -995,7 +997,12 @@ def run_serve(args):
             "latency_ms": {"p50": pct(lat_served, 50), "p99": pct(lat_served, 99), "max": float(lat_served.max())},
             "per_request_launch": {"value": n_req / span_base, "unit": "req/s", "p50_ms": pct(lat_base, 50),
                                    "p99_ms": pct(lat_base, 99)},
-            "results_identical_alone_and_in_mix": bool(identical),
+            "results_identical_alone_and_in_mix": bool(identical), "clocks": clk.summary(),
+            "e2e": {"value": n_req / span_served, "unit": "req/s", "h2d_bytes_per_step": 128 * n_req,
+                    "d2h_bytes_per_step": 48 * n_req,
+                    "note": "the served rate is end to end: requests written by the host into the mapped inbox "
+                            "(128 B each), completions read from the mapped outbox (48 B each)"},
+            "gpu_launches": 2,
             "waiting": {"inbox_mean": float(np.mean(backlog)), "inbox_max": int(max(backlog)),
                         "on_device_mean": float(np.mean(on_device)), "on_device_max": int(max(on_device)),
                         "samples": len(backlog),

@@ -639,7 +639,8 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
         pset = thread_kernel_pset(c->registered);
         maxspawn = thread_kernel_maxspawn(pset);
         frame_bytes = c->cfg.frame_bytes ? (uint32_t)c->cfg.frame_bytes : thread_record_bytes(pset);
-        smem = (size_t)(c->threads_per_block / 32) * thread_warp_smem(maxspawn);
+        P.warp_smem = (uint32_t)(thread_warp_smem(maxspawn) + thread_prog_smem(pset));
+        smem = (size_t)(c->threads_per_block / 32) * P.warp_smem;
         int occ = 0;
         {
             const cudaError_t oe = thread_kernel_occupancy(pset, c->cfg.scheduler, c->threads_per_block, smem, &occ);

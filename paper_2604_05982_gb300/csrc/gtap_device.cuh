@@ -451,6 +451,7 @@ struct WarpSh {
     uint32_t* fstack;   // [fcap]
     uint32_t* staged_id;// [scap]
     uint8_t* staged_q;  // [scap]
+    char* prog;         // the program set's per-warp area (thread_prog_smem bytes, 16-byte aligned)
     int fcap, scap;
 };
 
@@ -470,6 +471,7 @@ __device__ __forceinline__ WarpSh carve_warp(char* base, int maxspawn) {
     w.fstack = reinterpret_cast<uint32_t*>(base + 512);
     w.staged_id = w.fstack + w.fcap;
     w.staged_q = reinterpret_cast<uint8_t*>(w.staged_id + w.scap);
+    w.prog = base + thread_warp_smem(maxspawn);
     return w;
 }
 
@@ -771,6 +773,11 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
         ws.head_lb[lane] = 0;
     }
     if (lane == 0) { ws.ctrl[0] = 0; ws.ctrl[1] = 0; ws.ctrl[2] = 0; ws.ctrl[3] = 0; }
+    {
+        // the program set's warp area starts zeroed
+        const int pwords = ((int)P.warp_smem - thread_warp_smem((int)P.maxspawn)) / 4;
+        for (int i = lane; i < pwords; i += 32) reinterpret_cast<int*>(ws.prog)[i] = 0;
+    }
     __syncwarp();
 
     if (P.serving && wid == 0) {

@@ -189,6 +189,7 @@ struct KParams {
     const RootDesc* root_desc;
     uint32_t n_roots;
     uint32_t maxspawn;        // max children one step stages: per lane (thread mode) / per block (block mode)
+    uint32_t warp_smem;       // thread mode: shared bytes per warp (runtime part + the program set's warp area)
     WorkerStats* stats;
     volatile int* host_abort; // mapped pinned host word, may be null
     uint64_t timeout_ns;

@@ -67,7 +67,7 @@ template <unsigned PSET, int SCHED>
 __global__ void __launch_bounds__(256, thread_min_blocks<PSET>()) thread_kernel(KParams P) {
     extern __shared__ __align__(16) char smem[];
     const int wib = threadIdx.x >> 5;
-    thread_mode_loop<ThreadDispatch<PSET>, SCHED>(P, smem + (size_t)wib * thread_warp_smem((int)P.maxspawn));
+    thread_mode_loop<ThreadDispatch<PSET>, SCHED>(P, smem + (size_t)wib * P.warp_smem);
 }
 
 // Default scheduler for every program set; the Sec. 6.5 comparison variants for
@@ -104,6 +104,8 @@ int thread_kernel_maxspawn(unsigned pset) {
     if (pset & PS_CILKSORT) m = max(m, 2);
     return m;
 }
+
+size_t thread_prog_smem(unsigned pset) { return (pset & PS_KCLIQUE) ? (size_t)kKcCoopSmem : 0; }
 
 uint32_t thread_record_bytes(unsigned) { return 64; }
 

@@ -13,6 +13,7 @@ cudaError_t launch_thread_kernel(unsigned pset, int sched, const KParams& P, int
 cudaError_t thread_kernel_occupancy(unsigned pset, int sched, int block, size_t smem, int* blocks_per_sm);
 unsigned thread_kernel_pset(unsigned registered);   // instantiation that covers the registered programs
 int thread_kernel_maxspawn(unsigned pset);
+size_t thread_prog_smem(unsigned pset);             // per-warp shared bytes the programs of the set use
 uint32_t thread_record_bytes(unsigned pset);
 
 // Block mode (block size 128 or 256).

@@ -316,6 +316,8 @@ static __device__ int kc_intersect(const int* a, int na, LA la, const int* b, in
     return cnt;
 }
 
+static __device__ unsigned long long kc_count_rows(const unsigned long long* row, int ns, int j);
+
 // count(S, j) for |S| <= 64 inside one lane, with 64-bit adjacency bitsets.
 static __device__ unsigned long long kc_count_small(const int* S, int ns, int j, const int64_t* off, const int* adj) {
     if (j == 1) return (unsigned long long)ns;
@@ -346,6 +348,13 @@ static __device__ unsigned long long kc_count_small(const int* S, int ns, int j,
         }
         row[a] = bits;
     }
+    return kc_count_rows(row, ns, j);
+}
+
+// count(S, j) from S's adjacency rows (bit b of row[a]: S[b] is an out-neighbour of S[a]), ns <= 64.
+static __device__ unsigned long long kc_count_rows(const unsigned long long* row, int ns, int j) {
+    if (j == 1) return (unsigned long long)ns;
+    if (ns < j) return 0;
     const unsigned long long full = (ns == 64) ? ~0ull : ((1ull << ns) - 1ull);
     if (j == 2) {
         unsigned long long t = 0;
@@ -776,6 +785,127 @@ static __device__ void kclique_pivb_step(TaskCtx& c) {
     c.join(1, kc_queue(e, (int)depth));
 }
 
+// Warp-cooperative edge pass (orientation): the lanes of a warp that run a
+// range step take every such lane's DAG edges one after another, all together,
+// so that lanes with short and long adjacency lists no longer wait for each
+// other.  Per edge (u, v): C = N+(u) n N+(v) by binary searches of the shorter
+// list's elements (split over the lanes) in the longer one, compacted in order
+// into the warp's area; then, for C of at most split_threshold members, the
+// rows of the subgraph C induces (lanes split each member's out-list and look
+// its elements up in C), and the owner lane counts from the rows.  Larger sets
+// are handed back to the owner lane, which spawns them as set tasks.
+// Per-warp area: C (kKcMaxThr ints), its rows (kKcMaxThr words) and a claim
+// word: the lanes that run the pass must be one converged group, and should a
+// second group of the same warp arrive while the area is claimed, it takes the
+// per-lane path instead.
+constexpr int kKcCoopSmem = kKcMaxThr * 4 + kKcMaxThr * 8 + 16;
+
+__device__ __forceinline__ bool kc_contains(const int* L, int n, int x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(L + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo < n && __ldg(L + lo) == x;
+}
+
+__device__ __forceinline__ int kc_index_of(const int* C, int n, int x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (C[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && C[lo] == x) ? lo : -1;
+}
+
+// Adds this lane's count for its own edges [lo, hi) to *local; edges whose C
+// exceeds thr go to dei / dcn (at most hi - lo of them, *dn on return).
+// Returns false, having done nothing, when the warp's area is in use.
+static __device__ __noinline__ bool kc_coop_edges(const gtap_kclique_args& e, int* cbuf, uint32_t lo, uint32_t hi,
+                                                  int need, int thr, uint32_t* dei, int* dcn, int* dn,
+                                                  unsigned long long* local) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int nact = __popc(mask);
+    const int rank = __popc(mask & below);
+    const int leader = __ffs((int)mask) - 1;
+    unsigned long long* rows = reinterpret_cast<unsigned long long*>(cbuf + kKcMaxThr);
+    int* claim = reinterpret_cast<int*>(rows + kKcMaxThr);
+    int got = 0;
+    if (lane == leader) got = atomicCAS(claim, 0, 1) == 0 ? 1 : 0;
+    if (__shfl_sync(mask, got, leader) == 0) return false;
+    unsigned long long mine = 0;
+    int nd = 0;
+    for (unsigned m = mask; m != 0u; m &= m - 1u) {
+        const int owner = __ffs((int)m) - 1;
+        // the owner's task: its edge range, and its root's graph and parameters (lanes of one
+        // warp may run tasks of different roots, i.e. different graphs)
+        const uint32_t olo = __shfl_sync(mask, lo, owner), ohi = __shfl_sync(mask, hi, owner);
+        const long long* goff = reinterpret_cast<const long long*>(
+            __shfl_sync(mask, reinterpret_cast<unsigned long long>(e.off), owner));
+        const int* gadj = reinterpret_cast<const int*>(__shfl_sync(mask, reinterpret_cast<unsigned long long>(e.adj), owner));
+        const int* gsrc = reinterpret_cast<const int*>(__shfl_sync(mask, reinterpret_cast<unsigned long long>(e.src), owner));
+        const int oneed = __shfl_sync(mask, need, owner), othr = __shfl_sync(mask, thr, owner);
+        for (uint32_t ei = olo; ei < ohi; ++ei) {
+            const int u = __ldg(gsrc + ei), v = __ldg(gadj + ei);
+            const long long ou = __ldg(goff + u), ov = __ldg(goff + v);
+            const int nu = (int)(__ldg(goff + u + 1) - ou), nv = (int)(__ldg(goff + v + 1) - ov);
+            const bool ushort = nu <= nv;
+            const int* S = gadj + (ushort ? ou : ov);
+            const int* L = gadj + (ushort ? ov : ou);
+            const int ns = ushort ? nu : nv, nl = ushort ? nv : nu;
+            int cn = 0;
+            for (int b = 0; b < ns; b += nact) {
+                const int j = b + rank;
+                int x = 0;
+                bool in = false;
+                if (j < ns) {
+                    x = __ldg(S + j);
+                    in = kc_contains(L, nl, x);
+                }
+                const unsigned bal = __ballot_sync(mask, in);
+                if (in) {
+                    const int p = cn + __popc(bal & below);
+                    if (p < kKcMaxThr) cbuf[p] = x;   // C in ascending order (S is sorted, lanes in rank order)
+                }
+                cn += __popc(bal);
+            }
+            __syncwarp(mask);
+            unsigned long long add = 0;
+            if (oneed == 1) {
+                add = (unsigned long long)cn;
+            } else if (cn >= oneed && cn <= othr) {
+                for (int a2 = 0; a2 < cn; ++a2) {
+                    const int w = cbuf[a2];
+                    const long long ow = __ldg(goff + w);
+                    const int nw = (int)(__ldg(goff + w + 1) - ow);
+                    unsigned long long bits = 0;
+                    for (int b = rank; b < nw; b += nact) {
+                        const int idx = kc_index_of(cbuf, cn, __ldg(gadj + ow + b));
+                        if (idx >= 0) bits |= 1ull << idx;
+                    }
+                    const unsigned r0 = __reduce_or_sync(mask, (unsigned)bits);
+                    const unsigned r1 = __reduce_or_sync(mask, (unsigned)(bits >> 32));
+                    if (rank == 0) rows[a2] = ((unsigned long long)r1 << 32) | r0;
+                }
+                __syncwarp(mask);
+                if (lane == owner) add = kc_count_rows(rows, cn, oneed);
+            } else if (cn >= oneed && lane == owner) {
+                dei[nd] = ei;
+                dcn[nd] = cn;
+                ++nd;
+            }
+            if (lane == owner) mine += add;
+            __syncwarp(mask);   // the area is rewritten for the next edge
+        }
+    }
+    if (lane == leader) atomicExch(claim, 0);
+    *dn = nd;
+    *local = mine;
+    return true;
+}
+
 static __device__ void kclique_range_step(TaskCtx& c) {
     const KcRangeSpawn a = c.load<KcRangeSpawn>();
     const gtap_kclique_args& e = kc_env(c.P, a.root);
@@ -793,6 +923,26 @@ static __device__ void kclique_range_step(TaskCtx& c) {
     const int need = e.k - 2;
     const bool pivot = e.algorithm == GTAP_KCLIQUE_PIVOT;
     unsigned long long local = 0;
+    uint32_t dei[kKcFan];
+    int dcn[kKcFan];
+    int dn = 0;
+    if (!pivot && kc_coop_edges(e, reinterpret_cast<int*>(c.ws.prog), a.lo, a.hi, need, thr, dei, dcn, &dn, &local)) {
+        // orientation, warp-cooperative pass done; the sets too large to count there become set tasks
+        for (int q = 0; q < dn; ++q) {
+            const uint32_t ei = dei[q];
+            const int u = __ldg(e.src + ei), v = __ldg(e.adj + ei);
+            const long long ou = kc_off(e, u);
+            const int nu = (int)(kc_off(e, u + 1) - ou);
+            c.spawn(T_KCLIQUE_SET, kKcRangeSlotAcc, kc_queue(e, 1),
+                    KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)(e.adj + ou), (uint32_t)nu, (uint32_t)v,
+                               (uint32_t)dcn[q], kKcLazy, 0ull, 0ull},
+                    kFlagAccumulate);
+        }
+        if (c.nspawned == 0) { c.ret(local); return; }
+        st_cg64(c.frame + kKcRangeLocal, local);
+        c.join(1, kc_queue(e, 0));
+        return;
+    }
     int C[kKcMaxThr];
     for (uint32_t ei = a.lo; ei < a.hi; ++ei) {
         const int u = __ldg(e.src + ei), v = __ldg(e.adj + ei);
