@@ -785,28 +785,17 @@ static __device__ void kclique_pivb_step(TaskCtx& c) {
     c.join(1, kc_queue(e, (int)depth));
 }
 
-// Warp-cooperative edge pass (orientation): the lanes of a warp that run a
-// range step take every such lane's DAG edges one after another, all together,
-// so that lanes with short and long adjacency lists no longer wait for each
-// other.  Per edge (u, v): C = N+(u) n N+(v) by binary searches of the shorter
-// list's elements (split over the lanes) in the longer one, compacted in order
-// into the warp's area; then, for C of at most split_threshold members, the
-// rows of the subgraph C induces (lanes split each member's out-list and look
-// its elements up in C), and the owner lane counts from the rows.  Larger sets
-// are handed back to the owner lane, which spawns them as set tasks.
-// Per-warp area: C (kKcMaxThr ints), its rows (kKcMaxThr words) and a claim
-// word: the lanes that run the pass must be one converged group, and should a
-// second group of the same warp arrive while the area is claimed, it takes the
-// per-lane path instead.
-constexpr int kKcCoopSmem = kKcMaxThr * 4 + kKcMaxThr * 8 + 16;
+template <bool SCRATCH>
+__device__ __forceinline__ int kc_ld(const int* p) { return SCRATCH ? __ldcg(p) : __ldg(p); }
 
+template <bool SCRATCH>
 __device__ __forceinline__ bool kc_contains(const int* L, int n, int x) {
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (__ldg(L + mid) < x) lo = mid + 1; else hi = mid;
+        if (kc_ld<SCRATCH>(L + mid) < x) lo = mid + 1; else hi = mid;
     }
-    return lo < n && __ldg(L + lo) == x;
+    return lo < n && kc_ld<SCRATCH>(L + lo) == x;
 }
 
 __device__ __forceinline__ int kc_index_of(const int* C, int n, int x) {
@@ -818,89 +807,183 @@ __device__ __forceinline__ int kc_index_of(const int* C, int n, int x) {
     return (lo < n && C[lo] == x) ? lo : -1;
 }
 
-// Adds this lane's count for its own edges [lo, hi) to *local; edges whose C
-// exceeds thr go to dei / dcn (at most hi - lo of them, *dn on return).
-// Returns false, having done nothing, when the warp's area is in use.
-static __device__ __noinline__ bool kc_coop_edges(const gtap_kclique_args& e, int* cbuf, uint32_t lo, uint32_t hi,
-                                                  int need, int thr, uint32_t* dei, int* dcn, int* dn,
-                                                  unsigned long long* local) {
-    const unsigned mask = __activemask();
-    const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
-    const int nact = __popc(mask);
-    const int rank = __popc(mask & below);
-    const int leader = __ffs((int)mask) - 1;
-    unsigned long long* rows = reinterpret_cast<unsigned long long*>(cbuf + kKcMaxThr);
-    int* claim = reinterpret_cast<int*>(rows + kKcMaxThr);
+// The lanes of `mask` that run a cooperative pass (see below) and their shared area.
+struct KcCoop {
+    unsigned mask, below;
+    int lane, nact, rank, leader;
+    int* cbuf;
+    unsigned long long* rows;
+    int* claim;
+};
+
+// Claims the warp's area for the lanes now converged here; false when another
+// group of the same warp holds it.
+__device__ __forceinline__ bool kc_coop_begin(KcCoop& k, int* area) {
+    k.mask = __activemask();
+    k.lane = threadIdx.x & 31;
+    k.below = (1u << k.lane) - 1u;
+    k.nact = __popc(k.mask);
+    k.rank = __popc(k.mask & k.below);
+    k.leader = __ffs((int)k.mask) - 1;
+    k.cbuf = area;
+    k.rows = reinterpret_cast<unsigned long long*>(area + kKcMaxThr);
+    k.claim = reinterpret_cast<int*>(k.rows + kKcMaxThr);
+    // the group's earlier writes (a set a lane has just materialised) become visible to all of it
+    __syncwarp(k.mask);
     int got = 0;
-    if (lane == leader) got = atomicCAS(claim, 0, 1) == 0 ? 1 : 0;
-    if (__shfl_sync(mask, got, leader) == 0) return false;
+    if (k.lane == k.leader) got = atomicCAS(k.claim, 0, 1) == 0 ? 1 : 0;
+    return __shfl_sync(k.mask, got, k.leader) != 0;
+}
+__device__ __forceinline__ void kc_coop_end(const KcCoop& k) {
+    __syncwarp(k.mask);
+    if (k.lane == k.leader) atomicExch(k.claim, 0);
+}
+
+// C = S n L by the lanes of the group (S the shorter sorted list, split over the
+// lanes; L searched), kept in order in the area (up to kKcMaxThr members).
+template <bool SSET, bool LSET>
+__device__ __forceinline__ int kc_coop_collect(const KcCoop& k, const int* S, int ns, const int* L, int nl) {
+    int cn = 0;
+    for (int b = 0; b < ns; b += k.nact) {
+        const int j = b + k.rank;
+        int x = 0;
+        bool in = false;
+        if (j < ns) {
+            x = kc_ld<SSET>(S + j);
+            in = kc_contains<LSET>(L, nl, x);
+        }
+        const unsigned bal = __ballot_sync(k.mask, in);
+        if (in) {
+            const int p = cn + __popc(bal & k.below);
+            if (p < kKcMaxThr) k.cbuf[p] = x;   // C in ascending order (S is sorted, lanes in rank order)
+        }
+        cn += __popc(bal);
+    }
+    return cn;
+}
+
+// One item, by all lanes of the group: C = A n B (sorted lists of the owner's
+// graph, B an out-list; A in the scratch arena when ASET, read through L2),
+// kept in order in the area; for need >= 2 and |C| <= thr also the rows of the
+// subgraph C induces, and the owner's count from them.  Returns |C|; *add gets
+// the owner's count (need == 1: |C|; 0 when C is larger than thr).
+template <bool ASET>
+__device__ __forceinline__ int kc_coop_item(const KcCoop& k, int owner, const int* A, int na, const int* B, int nb,
+                                            const long long* goff, const int* gadj, int need, int thr,
+                                            unsigned long long* add) {
+    const int cn = (na <= nb) ? kc_coop_collect<ASET, false>(k, A, na, B, nb)
+                              : kc_coop_collect<false, ASET>(k, B, nb, A, na);
+    __syncwarp(k.mask);
+    *add = 0;
+    if (need == 1) {
+        *add = (k.lane == owner) ? (unsigned long long)cn : 0ull;
+    } else if (cn >= need && cn <= thr) {
+        for (int a2 = 0; a2 < cn; ++a2) {
+            const int w = k.cbuf[a2];
+            const long long ow = __ldg(goff + w);
+            const int nw = (int)(__ldg(goff + w + 1) - ow);
+            unsigned long long bits = 0;
+            for (int b = k.rank; b < nw; b += k.nact) {
+                const int idx = kc_index_of(k.cbuf, cn, __ldg(gadj + ow + b));
+                if (idx >= 0) bits |= 1ull << idx;
+            }
+            const unsigned r0 = __reduce_or_sync(k.mask, (unsigned)bits);
+            const unsigned r1 = __reduce_or_sync(k.mask, (unsigned)(bits >> 32));
+            if (k.rank == 0) k.rows[a2] = ((unsigned long long)r1 << 32) | r0;
+        }
+        __syncwarp(k.mask);
+        if (k.lane == owner) *add = kc_count_rows(k.rows, cn, need);
+    }
+    __syncwarp(k.mask);   // the area is rewritten by the next item
+    return cn;
+}
+
+// Warp-cooperative passes (orientation, where C's rows are built: at least two
+// vertices still to choose): the lanes of a warp that reach the same task step
+// take every such lane's items (DAG edges of a range step, branches of a set
+// step) one after another, all together, so that lanes with short and long
+// adjacency lists no longer wait for each other.  Per item the
+// shorter list's elements are split over the lanes and looked up by binary
+// search in the longer one; the rows of a small C are built the same way, one
+// member's out-list per round.  Items whose C exceeds split_threshold go back
+// to their owner lane (di / dc, at most hi - lo of them), which spawns them.
+// Lanes of one warp may run tasks of different roots (batched or served
+// graphs), so an item's graph, k and threshold are broadcast from its owner.
+// Per-warp area: C (kKcMaxThr ints), its rows (kKcMaxThr words), a claim word.
+constexpr int kKcCoopSmem = kKcMaxThr * 4 + kKcMaxThr * 8 + 16;
+
+__device__ __forceinline__ const int* kc_bcast_ptr(unsigned mask, const void* p, int owner) {
+    return reinterpret_cast<const int*>(__shfl_sync(mask, reinterpret_cast<unsigned long long>(p), owner));
+}
+
+// Range step: the DAG edges [lo, hi) of this lane.  Returns false, having done
+// nothing, when the warp's area is in use.
+static __device__ __noinline__ bool kc_coop_edges(const gtap_kclique_args& e, int* area, uint32_t lo, uint32_t hi,
+                                                  int need, int thr, uint32_t* di, int* dc, int* dn,
+                                                  unsigned long long* local) {
+    KcCoop k;
+    if (!kc_coop_begin(k, area)) return false;
     unsigned long long mine = 0;
     int nd = 0;
-    for (unsigned m = mask; m != 0u; m &= m - 1u) {
+    for (unsigned m = k.mask; m != 0u; m &= m - 1u) {
         const int owner = __ffs((int)m) - 1;
-        // the owner's task: its edge range, and its root's graph and parameters (lanes of one
-        // warp may run tasks of different roots, i.e. different graphs)
-        const uint32_t olo = __shfl_sync(mask, lo, owner), ohi = __shfl_sync(mask, hi, owner);
-        const long long* goff = reinterpret_cast<const long long*>(
-            __shfl_sync(mask, reinterpret_cast<unsigned long long>(e.off), owner));
-        const int* gadj = reinterpret_cast<const int*>(__shfl_sync(mask, reinterpret_cast<unsigned long long>(e.adj), owner));
-        const int* gsrc = reinterpret_cast<const int*>(__shfl_sync(mask, reinterpret_cast<unsigned long long>(e.src), owner));
-        const int oneed = __shfl_sync(mask, need, owner), othr = __shfl_sync(mask, thr, owner);
+        const uint32_t olo = __shfl_sync(k.mask, lo, owner), ohi = __shfl_sync(k.mask, hi, owner);
+        const long long* goff = reinterpret_cast<const long long*>(kc_bcast_ptr(k.mask, e.off, owner));
+        const int* gadj = kc_bcast_ptr(k.mask, e.adj, owner);
+        const int* gsrc = kc_bcast_ptr(k.mask, e.src, owner);
+        const int oneed = __shfl_sync(k.mask, need, owner), othr = __shfl_sync(k.mask, thr, owner);
         for (uint32_t ei = olo; ei < ohi; ++ei) {
             const int u = __ldg(gsrc + ei), v = __ldg(gadj + ei);
             const long long ou = __ldg(goff + u), ov = __ldg(goff + v);
             const int nu = (int)(__ldg(goff + u + 1) - ou), nv = (int)(__ldg(goff + v + 1) - ov);
-            const bool ushort = nu <= nv;
-            const int* S = gadj + (ushort ? ou : ov);
-            const int* L = gadj + (ushort ? ov : ou);
-            const int ns = ushort ? nu : nv, nl = ushort ? nv : nu;
-            int cn = 0;
-            for (int b = 0; b < ns; b += nact) {
-                const int j = b + rank;
-                int x = 0;
-                bool in = false;
-                if (j < ns) {
-                    x = __ldg(S + j);
-                    in = kc_contains(L, nl, x);
-                }
-                const unsigned bal = __ballot_sync(mask, in);
-                if (in) {
-                    const int p = cn + __popc(bal & below);
-                    if (p < kKcMaxThr) cbuf[p] = x;   // C in ascending order (S is sorted, lanes in rank order)
-                }
-                cn += __popc(bal);
-            }
-            __syncwarp(mask);
-            unsigned long long add = 0;
-            if (oneed == 1) {
-                add = (unsigned long long)cn;
-            } else if (cn >= oneed && cn <= othr) {
-                for (int a2 = 0; a2 < cn; ++a2) {
-                    const int w = cbuf[a2];
-                    const long long ow = __ldg(goff + w);
-                    const int nw = (int)(__ldg(goff + w + 1) - ow);
-                    unsigned long long bits = 0;
-                    for (int b = rank; b < nw; b += nact) {
-                        const int idx = kc_index_of(cbuf, cn, __ldg(gadj + ow + b));
-                        if (idx >= 0) bits |= 1ull << idx;
-                    }
-                    const unsigned r0 = __reduce_or_sync(mask, (unsigned)bits);
-                    const unsigned r1 = __reduce_or_sync(mask, (unsigned)(bits >> 32));
-                    if (rank == 0) rows[a2] = ((unsigned long long)r1 << 32) | r0;
-                }
-                __syncwarp(mask);
-                if (lane == owner) add = kc_count_rows(rows, cn, oneed);
-            } else if (cn >= oneed && lane == owner) {
-                dei[nd] = ei;
-                dcn[nd] = cn;
+            unsigned long long add;
+            const int cn = kc_coop_item<false>(k, owner, gadj + ou, nu, gadj + ov, nv, goff, gadj, oneed, othr, &add);
+            mine += add;
+            if (k.lane == owner && oneed >= 2 && cn >= oneed && cn > othr) {
+                di[nd] = ei;
+                dc[nd] = cn;
                 ++nd;
             }
-            if (lane == owner) mine += add;
-            __syncwarp(mask);   // the area is rewritten for the next edge
         }
     }
-    if (lane == leader) atomicExch(claim, 0);
+    kc_coop_end(k);
+    *dn = nd;
+    *local = mine;
+    return true;
+}
+
+// Set step: the branches [lo, hi) of this lane's set (len members, in the
+// scratch arena).  Returns false, having done nothing, when the area is in use.
+static __device__ __noinline__ bool kc_coop_branches(const gtap_kclique_args& e, int* area, const int* set, uint32_t len,
+                                                     uint32_t lo, uint32_t hi, int need, int thr, uint32_t* di, int* dc,
+                                                     int* dn, unsigned long long* local) {
+    KcCoop k;
+    if (!kc_coop_begin(k, area)) return false;
+    unsigned long long mine = 0;
+    int nd = 0;
+    for (unsigned m = k.mask; m != 0u; m &= m - 1u) {
+        const int owner = __ffs((int)m) - 1;
+        const uint32_t olo = __shfl_sync(k.mask, lo, owner), ohi = __shfl_sync(k.mask, hi, owner);
+        const uint32_t olen = __shfl_sync(k.mask, len, owner);
+        const int* oset = kc_bcast_ptr(k.mask, set, owner);
+        const long long* goff = reinterpret_cast<const long long*>(kc_bcast_ptr(k.mask, e.off, owner));
+        const int* gadj = kc_bcast_ptr(k.mask, e.adj, owner);
+        const int oneed = __shfl_sync(k.mask, need, owner), othr = __shfl_sync(k.mask, thr, owner);
+        for (uint32_t i = olo; i < ohi; ++i) {
+            const int w = __ldcg(oset + i);
+            const long long ow = __ldg(goff + w);
+            const int nw = (int)(__ldg(goff + w + 1) - ow);
+            unsigned long long add;
+            const int cn = kc_coop_item<true>(k, owner, oset, (int)olen, gadj + ow, nw, goff, gadj, oneed, othr, &add);
+            mine += add;
+            if (k.lane == owner && oneed >= 2 && cn >= oneed && cn > othr) {
+                di[nd] = i;
+                dc[nd] = cn;
+                ++nd;
+            }
+        }
+    }
+    kc_coop_end(k);
     *dn = nd;
     *local = mine;
     return true;
@@ -926,7 +1009,8 @@ static __device__ void kclique_range_step(TaskCtx& c) {
     uint32_t dei[kKcFan];
     int dcn[kKcFan];
     int dn = 0;
-    if (!pivot && kc_coop_edges(e, reinterpret_cast<int*>(c.ws.prog), a.lo, a.hi, need, thr, dei, dcn, &dn, &local)) {
+    if (!pivot && need >= 2 &&
+        kc_coop_edges(e, reinterpret_cast<int*>(c.ws.prog), a.lo, a.hi, need, thr, dei, dcn, &dn, &local)) {
         // orientation, warp-cooperative pass done; the sets too large to count there become set tasks
         for (int q = 0; q < dn; ++q) {
             const uint32_t ei = dei[q];
@@ -1024,6 +1108,29 @@ static __device__ void kclique_set_step(TaskCtx& c) {
     const int need = (int)a.j - 1;
     const bool pivot = e.algorithm == GTAP_KCLIQUE_PIVOT;
     unsigned long long local = 0;
+    uint32_t di[kKcFan];
+    int dc[kKcFan];
+    int dn = 0;
+    // cooperative only where C's rows are built (need >= 2): a count alone (need == 1) is one
+    // latency-bound search per branch, better overlapped across the lanes' own branches
+    if (!pivot && need >= 2 &&
+        kc_coop_branches(e, reinterpret_cast<int*>(c.ws.prog), set, len, lo, hi, need, thr, di, dc, &dn, &local)) {
+        // orientation, warp-cooperative pass done; this lane materialises and spawns its larger sets
+        for (int q = 0; q < dn; ++q) {
+            const int w = __ldcg(set + di[q]);
+            const long long ow = kc_off(e, w);
+            const int nw = (int)(kc_off(e, w + 1) - ow);
+            bool pooled;
+            int* S = kc_scratch_alloc(c, dc[q], &pooled);
+            if (!S) return;
+            kc_intersect(set, (int)len, SetLoad{}, e.adj + ow, nw, AdjLoad{}, S, dc[q]);
+            c.spawn(T_KCLIQUE_SET, kKcSetSlotAcc, kc_queue(e, depth + 1),
+                    KcSetSpawn{a.root, (uint32_t)need, (unsigned long long)S, (uint32_t)dc[q], 0u, (uint32_t)dc[q],
+                               pooled ? 1u : 0u, 0ull, 0ull},
+                    kFlagAccumulate);
+        }
+        hi = lo;   // the per-lane loop below has nothing left to do
+    }
     int C[kKcMaxThr];
     for (uint32_t i = lo; i < hi; ++i) {
         const int w = __ldcg(set + i);

@@ -25,6 +25,7 @@ def main(argv=None):
     ap.add_argument("--sched", type=int, default=0, help="fib/tree: GTAP_SCHED_* scheduler variant")
     ap.add_argument("--iters", type=int, default=256, help="bintree: compute_iters")
     ap.add_argument("--K", type=int, default=1, help="bintree: leaf compute functions")
+    ap.add_argument("--k", type=int, default=4, help="kclique: clique size")
     ap.add_argument("--block", type=int, default=0, help="bintree: 1 block mode")
     ap.add_argument("--grid", type=int, default=0, help="explicit grid size (0: the default)")
     ap.add_argument("--cutoff", type=int, default=0, help="fib / nqueens: sequential cutoff (0: none)")
@@ -78,7 +79,7 @@ def main(argv=None):
         n, e = inputs.rmat_graph(args.n or 16, 16, seed=7)
         g = runner.DeviceGraph(n, e)
         for _ in range(args.reps):
-            r = runner.kclique(g, 4, n_queues=args.queues, route=args.route)
+            r = runner.kclique(g, args.k, n_queues=args.queues, route=args.route)
             print("kclique", r.values, r.stats["kernel_ms"])
     elif args.case == "fmm":
         n = 1 << (args.n or 18)
