@@ -324,7 +324,7 @@ def run_reference_fmm(args):
     secs = sum(times) / len(times)
     value = secs * 1e3 * FMM_N / FMM_CPU_SAMPLE_N
     line = {"impl": "reference", "metric": "FMM time", "value": value, "unit": "ms/instance", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2 * value, "higher_is_better": False,
+            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 2 * value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"Laplace FMM N=2^20, p={FMM_P}, theta={FMM_THETA}, leaf {FMM_LEAF} (oracle)"},
             "cpu_baseline": {"value": value, "unit": "ms/instance", "cores": 1, "kind": "oracle",
@@ -412,7 +412,7 @@ def run_reference_small(args):
                     "oracle 4-clique count of graphs 0, 18, 27, 36 of the batch (scales 12-15) per step; "
                     "the larger graphs are slower, so this overstates the oracle's rate on the whole batch")
     line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": wl},
             "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": note},
@@ -683,7 +683,7 @@ def run_reference_kclique(args):
     vals = [_kclique_cpu_sample(n, e, args.k)[0] for _ in range(args.steps)]
     value = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": "k-clique time", "value": value, "unit": "ms/instance", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"{args.k}-clique count, R-MAT scale {args.scale} edge factor 16, seed 7 (oracle)"},
             "cpu_baseline": {"value": value, "unit": "ms/instance", "cores": 1, "kind": "oracle",
@@ -851,7 +851,7 @@ def run_reference_serve(args):
     vals = [_serve_cpu_sample(reqs, n_sample)[0] for _ in range(args.steps)]
     value = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": "served requests/s", "value": value, "unit": "req/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_sample / value,
+            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * n_sample / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "served mix: fib n in [20,32], N-Queens n in [8,12], 4-clique on R-MAT scale "
                                    "[10,14], hashed tree root [100,2000] (oracle)"},
