@@ -29,7 +29,7 @@ struct ThreadDispatch {
             if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_range_step(c); return; }
             break;
         case T_KCLIQUE_SET:
-            if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_set_step(c); return; }
+            if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_set_dispatch(c); return; }
             break;
         case T_KCLIQUE_PIV:
             if constexpr ((PSET & PS_KCLIQUE) != 0) { kclique_piv_step(c); return; }

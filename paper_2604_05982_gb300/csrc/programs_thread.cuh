@@ -1064,6 +1064,10 @@ static __device__ void kclique_range_step(TaskCtx& c) {
     c.join(1, kc_queue(e, 0));
 }
 
+// COOP: the warp-cooperative branch pass is compiled in (the dispatcher picks it
+// for orientation steps that build rows); without it the per-lane step keeps
+// the registers it had.
+template <bool COOP>
 static __device__ void kclique_set_step(TaskCtx& c) {
     const KcSetSpawn a = c.load<KcSetSpawn>();
     const gtap_kclique_args& e = kc_env(c.P, a.root);
@@ -1113,7 +1117,7 @@ static __device__ void kclique_set_step(TaskCtx& c) {
     int dn = 0;
     // cooperative only where C's rows are built (need >= 2): a count alone (need == 1) is one
     // latency-bound search per branch, better overlapped across the lanes' own branches
-    if (!pivot && need >= 2 &&
+    if (COOP && !pivot && need >= 2 &&
         kc_coop_branches(e, reinterpret_cast<int*>(c.ws.prog), set, len, lo, hi, need, thr, di, dc, &dn, &local)) {
         // orientation, warp-cooperative pass done; this lane materialises and spawns its larger sets
         for (int q = 0; q < dn; ++q) {
@@ -1164,6 +1168,15 @@ static __device__ void kclique_set_step(TaskCtx& c) {
     }
     st_cg64(c.frame + kKcSetLocal, local);
     c.join(1, kc_queue(e, depth));
+}
+
+// A set step whose branches still need at least two more vertices (j >= 3) runs
+// the cooperative pass (orientation only); the rest take the lean per-lane step.
+__device__ __forceinline__ void kclique_set_dispatch(TaskCtx& c) {
+    const unsigned long long w2 = c.word<2>();   // record bytes 16..23: root, j
+    const uint32_t j = (uint32_t)(w2 >> 32);
+    if (c.pc() == 0 && j >= 3 && kc_env(c.P, (uint32_t)w2).algorithm != GTAP_KCLIQUE_PIVOT) kclique_set_step<true>(c);
+    else kclique_set_step<false>(c);
 }
 
 }  // namespace gtap
