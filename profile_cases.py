@@ -94,7 +94,7 @@ def main(argv=None):
                                n_queues=args.queues, **geo)
             print("bintree", r.values, r.stats["kernel_ms"])
     else:
-        print(f"case {args.case} is not available in this build", file=sys.stderr)
+        print(f"case {args.case} is not available", file=sys.stderr)
         return 2
     return 0
 
