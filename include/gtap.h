@@ -77,8 +77,9 @@ typedef struct {
     void* stream;           /* cudaStream_t for runs (default: the legacy default stream) */
     uint64_t timeout_ns;    /* device-side run deadline (default 60 s); exceeded -> GTAP_ERR_TIMEOUT */
     uint64_t seed;          /* victim-selection seed (default 0x5EED) */
-    size_t scratch_bytes;   /* device scratch arena for programs that need it (k-clique candidate sets):
-                               4 KiB blocks recycled through a free-block queue, default 0 */
+    size_t scratch_bytes;   /* device scratch arena for programs that need it (k-clique candidate sets and
+                               pivoting rows): 4 KiB blocks and 64 KiB chunks, each size recycled through
+                               its own free queue, default 0 */
     int grid_blocks;        /* explicit persistent grid size (overrides blocks_per_sm x SM count), e.g. 1 */
     int debug_checks;       /* 1: track every record's state (free / allocated / running) and report
                                double allocation, double free or double execution as GTAP_ERR_TASK_FAILED */
@@ -353,9 +354,13 @@ typedef struct { const uint32_t* src; uint32_t* dst; uint32_t* tmp; uint64_t n; 
  * (k-2)-cliques of C = N+(u) n N+(v); a set larger than split_threshold
  * (<= 64, default 64) is materialised in the context's scratch arena
  * (gtap_config.scratch_bytes) and forked into child tasks over its branch
- * range; smaller ones are counted in the lane with 64-bit bitsets.  A
- * first-level set is written by its own task when that task starts (waiting
- * first-level tasks hold no scratch); deeper sets by the task that spawns them.
+ * range; smaller ones are counted with 64-bit adjacency rows.  Where rows are
+ * built (at least two more vertices to choose), the lanes of a warp that run
+ * the same step process their edges or branches together, one at a time
+ * (binary searches split over the lanes, C and its rows in the warp's shared
+ * memory); elsewhere each lane intersects its own lists.  A first-level set is
+ * written by its own task when that task starts (waiting first-level tasks
+ * hold no scratch); deeper sets by the task that spawns them.
  * route 1: queue = recursion depth mod n_queues.  k in [3, 16].  Result: uint64 count.
  *
  * algorithm 1 (GTAP_KCLIQUE_PIVOT) counts by pivoting instead (Sec. 6.4.2, the
