@@ -163,20 +163,22 @@ def run_gpu(args):
     # launch configuration per workload from the autotuner (outside the timed region); the
     # workload definitions stay fixed: N-Queens keeps its 4 DAQ queues, the others one queue
     tuned = {}
-    tmask = G.GTAP_TUNE_BLOCKS | G.GTAP_TUNE_STEAL | G.GTAP_TUNE_CAPACITY
+    tmask = G.GTAP_TUNE_BLOCKS | G.GTAP_TUNE_STEAL | G.GTAP_TUNE_CAPACITY | G.GTAP_TUNE_BACKOFF
     for key, mode, prog, a, q, pool in (("nqueens", G.GTAP_MODE_THREAD, "nqueens", nq_args, 4, 1 << 30),
                                         ("tree", G.GTAP_MODE_THREAD, "uts", ut_args, 1, 1 << 30),
                                         ("mergesort", G.GTAP_MODE_BLOCK, "mergesort", ms_args, 1, 256 << 20)):
         if args.no_tune:
-            tuned[key] = {"blocks_per_sm": 4, "steal_policy": 0, "deque_capacity": 4096 if mode == 0 else 1024}
+            tuned[key] = {"blocks_per_sm": 4, "steal_policy": 0, "deque_capacity": 4096 if mode == 0 else 1024,
+                          "idle_backoff_ns": 512}
         else:
             best, _ = G.gtap_autotune(mode, prog, [a], pool, runner.make_config(), reps=3, n_queues=q, tune_mask=tmask)
-            tuned[key] = {k: best[k] for k in ("blocks_per_sm", "steal_policy", "deque_capacity")}
+            tuned[key] = {k: best[k] for k in ("blocks_per_sm", "steal_policy", "deque_capacity", "idle_backoff_ns")}
 
     def ctx_for(key, mode, q, pool):
         c = tuned[key]
         return runner.Context(mode, q, pool_bytes=pool, blocks_per_sm=c["blocks_per_sm"],
-                              steal_policy=c["steal_policy"], deque_capacity=c["deque_capacity"])
+                              steal_policy=c["steal_policy"], deque_capacity=c["deque_capacity"],
+                              idle_backoff_ns=c["idle_backoff_ns"])
 
     nq = ctx_for("nqueens", G.GTAP_MODE_THREAD, 4, 1 << 30)
     t = nq.register("nqueens")
@@ -255,8 +257,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic", "config": CONFIG,
         "breakdown_ms": {k: sorted(v)[len(v) // 2] for k, v in per_kernel.items()},
-        "launch_config": {"source": "default" if args.no_tune else "gtap_autotune (blocks/SM, steal policy, ring "
-                          "capacity; queue counts fixed by the workloads)", **tuned},
+        "launch_config": {"source": "default" if args.no_tune else "gtap_autotune (blocks/SM, steal policy, idle "
+                          "back-off, ring capacity; queue counts fixed by the workloads)", **tuned},
         "roofline": {"bound": "hbm", "kernel": "block_kernel<mergesort> (2^26 keys)", "achieved": achieved,
                      "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": traffic, "algorithmic_bytes": MSORT_BYTES},
@@ -1084,13 +1086,13 @@ def run_fib(args):
     from paper_2604_05982_gb300 import runner
     world, rank, local = _gpu_setup(args)
     fa = G.gtap_fib_args(FIB_N, 0)
-    tmask = G.GTAP_TUNE_BLOCKS | G.GTAP_TUNE_STEAL | G.GTAP_TUNE_CAPACITY
+    tmask = G.GTAP_TUNE_BLOCKS | G.GTAP_TUNE_STEAL | G.GTAP_TUNE_CAPACITY | G.GTAP_TUNE_BACKOFF
     if args.no_tune:
-        tuned = {"blocks_per_sm": 4, "steal_policy": 0, "deque_capacity": 4096}
+        tuned = {"blocks_per_sm": 4, "steal_policy": 0, "deque_capacity": 4096, "idle_backoff_ns": 512}
     else:
         best, _ = G.gtap_autotune(G.GTAP_MODE_THREAD, "fib", [fa], 1 << 30, runner.make_config(), reps=3,
                                   n_queues=1, tune_mask=tmask)
-        tuned = {k: best[k] for k in ("blocks_per_sm", "steal_policy", "deque_capacity")}
+        tuned = {k: best[k] for k in ("blocks_per_sm", "steal_policy", "deque_capacity", "idle_backoff_ns")}
     c = runner.Context(G.GTAP_MODE_THREAD, 1, pool_bytes=1 << 30, **tuned)
     t = c.register("fib")
     h = c.spawn(t, fa)

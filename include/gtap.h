@@ -85,7 +85,8 @@ typedef struct {
                                double allocation, double free or double execution as GTAP_ERR_TASK_FAILED */
     int scheduler;          /* thread-mode queue management (GTAP_SCHED_*, default GTAP_SCHED_BATCHED);
                                the alternatives exist for the scheduler comparison of Sec. 6.5 */
-    int pad_;
+    int idle_backoff_ns;    /* thread mode: longest sleep of an idle warp between steal rounds, 32..65536 ns
+                               (default 512); longer relieves L2 of idle probing, shorter spreads new work faster */
 } gtap_config;
 
 /* Thread-mode scheduler designs compared in Sec. 6.5 ("GPU-Side Scheduler
@@ -404,15 +405,17 @@ gtap_status gtap_microbench(int kind, void* region, uint64_t region_bytes, int b
 
 /* ------------------------------------------------------------------------
  * Autotuner.  For one program and one batch of roots, pick blocks per SM,
- * ring capacity, DAQ queue count and steal policy by coordinate descent over
+ * ring capacity, DAQ queue count, steal policy and (thread mode) the idle
+ * back-off by coordinate descent over
  *   thread mode: blocks/SM {1,2,4,6,8}, steal {FILL, EMPTY, HALF, EMPTY|HALF},
- *                queues {1,2,3,4}, capacity {1024, 4096, 16384};
+ *                queues {1,2,3,4}, capacity {1024, 4096, 16384},
+ *                idle back-off {512, 2048, 8192} ns;
  *   block mode:  blocks/SM {1,2,3,4,6}, steal {half of the victim, ONE},
  *                queues {1}, capacity {1024, 4096, 16384},
- * starting from 4 blocks/SM, capacity 4096, n_queues queues and default
- * stealing; tune_mask selects the dimensions that may change
- * (GTAP_TUNE_BLOCKS | GTAP_TUNE_STEAL | GTAP_TUNE_QUEUES | GTAP_TUNE_CAPACITY,
- * 0 = all).  Each trial creates a context (gtap_init with `base` and the
+ * starting from 4 blocks/SM, capacity 4096, n_queues queues, default
+ * stealing and the base configuration's back-off; tune_mask selects the
+ * dimensions that may change (GTAP_TUNE_BLOCKS | GTAP_TUNE_STEAL |
+ * GTAP_TUNE_QUEUES | GTAP_TUNE_CAPACITY | GTAP_TUNE_BACKOFF, 0 = all).  Each trial creates a context (gtap_init with `base` and the
  * trial's fields, frame_pool_bytes), queues n_roots roots whose argument
  * structs lie back to back in root_args (host, args_bytes each, queue 0), runs
  * once to warm up and `reps` more times, and is scored by the median
@@ -426,11 +429,14 @@ gtap_status gtap_microbench(int kind, void* region, uint64_t region_bytes, int b
 #define GTAP_TUNE_STEAL 2
 #define GTAP_TUNE_QUEUES 4
 #define GTAP_TUNE_CAPACITY 8
+#define GTAP_TUNE_BACKOFF 16
 
 typedef struct {
     int blocks_per_sm, deque_capacity, n_queues, steal_policy;
     float kernel_ms;   /* median persistent-kernel time of the trial */
     int status;        /* gtap_status of the trial */
+    int idle_backoff_ns;
+    int pad;
 } gtap_tune_trial;
 
 gtap_status gtap_autotune(int mode, const char* program, const void* root_args, size_t args_bytes, int n_roots,

@@ -1,7 +1,7 @@
 // Autotuner of the launch configuration (batching and tuning, one of the
 // systems patterns the runtime takes on): for one program and one batch of
-// roots it picks blocks per SM, ring (deque) capacity, DAQ queue count and
-// steal policy by coordinate descent, timing the persistent kernel of each
+// roots it picks blocks per SM, ring (deque) capacity, DAQ queue count, steal
+// policy and the idle back-off by coordinate descent, timing the persistent kernel of each
 // trial (median of `reps` runs after one warm-up).  Built on the public calls
 // only; every trial must reproduce the root results of the first trial byte
 // for byte, so a configuration can change speed but never an answer.
@@ -14,7 +14,7 @@
 namespace {
 
 struct Trial {
-    int bps, cap, queues, steal;
+    int bps, cap, queues, steal, backoff;
 };
 
 struct Tuner {
@@ -36,6 +36,7 @@ struct Tuner {
         cfg.blocks_per_sm = tr.bps;
         cfg.deque_capacity = tr.cap;
         cfg.steal_policy = tr.steal;
+        cfg.idle_backoff_ns = tr.backoff;
         gtap_ctx* c = nullptr;
         gtap_status st = gtap_init((gtap_mode)mode, tr.queues, pool_bytes, &cfg, &c);
         if (st != GTAP_OK) return st;
@@ -75,6 +76,8 @@ struct Tuner {
             t.steal_policy = tr.steal;
             t.kernel_ms = *ms;
             t.status = (int)st;
+            t.idle_backoff_ns = tr.backoff;
+            t.pad = 0;
         }
         ++n_out;
         return st;
@@ -89,9 +92,10 @@ extern "C" gtap_status gtap_autotune(int mode, const char* program, const void* 
                                      gtap_tune_trial* best) {
     if ((mode != GTAP_MODE_THREAD && mode != GTAP_MODE_BLOCK) || !program || !root_args || args_bytes == 0 ||
         n_roots < 1 || reps < 1 || !best || max_trials < 0 || n_queues < 1 || n_queues > 8 ||
-        (mode == GTAP_MODE_BLOCK && n_queues != 1) || (tune_mask & ~15) != 0)
+        (mode == GTAP_MODE_BLOCK && n_queues != 1) || (tune_mask & ~31) != 0)
         return GTAP_ERR_INVALID_ARG;
-    if (tune_mask == 0) tune_mask = GTAP_TUNE_BLOCKS | GTAP_TUNE_STEAL | GTAP_TUNE_QUEUES | GTAP_TUNE_CAPACITY;
+    if (tune_mask == 0)
+        tune_mask = GTAP_TUNE_BLOCKS | GTAP_TUNE_STEAL | GTAP_TUNE_QUEUES | GTAP_TUNE_CAPACITY | GTAP_TUNE_BACKOFF;
     Tuner t;
     t.mode = mode;
     t.program = program;
@@ -112,8 +116,10 @@ extern "C" gtap_status gtap_autotune(int mode, const char* program, const void* 
                                           : std::vector<int>{0, GTAP_STEAL_ONE};
     const std::vector<int> queues = thread ? std::vector<int>{1, 2, 3, 4} : std::vector<int>{1};
     const std::vector<int> caps = {1024, 4096, 16384};
+    // the idle back-off exists in thread mode only
+    const std::vector<int> backoffs = thread ? std::vector<int>{512, 2048, 8192} : std::vector<int>{};
 
-    Trial cur{4, 4096, n_queues, thread ? GTAP_STEAL_FILL : 0};
+    Trial cur{4, 4096, n_queues, thread ? GTAP_STEAL_FILL : 0, t.base.idle_backoff_ns ? t.base.idle_backoff_ns : 512};
     float cur_ms = 0.f;
     gtap_status st = t.run(cur, &cur_ms);
     if (st != GTAP_OK) {
@@ -121,14 +127,15 @@ extern "C" gtap_status gtap_autotune(int mode, const char* program, const void* 
         return st;
     }
     // coordinate descent, one sweep per parameter in this order
-    for (int dim = 0; dim < 4; ++dim) {
+    for (int dim = 0; dim < 5; ++dim) {
         if ((tune_mask & (1 << dim)) == 0) continue;
-        const std::vector<int>& vals = dim == 0 ? bps : dim == 1 ? steal : dim == 2 ? queues : caps;
-        const int start = dim == 0 ? cur.bps : dim == 1 ? cur.steal : dim == 2 ? cur.queues : cur.cap;
+        const std::vector<int>& vals = dim == 0 ? bps : dim == 1 ? steal : dim == 2 ? queues : dim == 3 ? caps : backoffs;
+        const int start = dim == 0 ? cur.bps : dim == 1 ? cur.steal : dim == 2 ? cur.queues : dim == 3 ? cur.cap
+                                                                                                      : cur.backoff;
         for (int v : vals) {
             if (v == start) continue;   // already timed
             Trial tr = cur;
-            int& field = dim == 0 ? tr.bps : dim == 1 ? tr.steal : dim == 2 ? tr.queues : tr.cap;
+            int& field = dim == 0 ? tr.bps : dim == 1 ? tr.steal : dim == 2 ? tr.queues : dim == 3 ? tr.cap : tr.backoff;
             field = v;
             float ms = 0.f;
             gtap_status s = t.run(tr, &ms);
@@ -146,6 +153,8 @@ extern "C" gtap_status gtap_autotune(int mode, const char* program, const void* 
     best->deque_capacity = cur.cap;
     best->n_queues = cur.queues;
     best->steal_policy = cur.steal;
+    best->idle_backoff_ns = cur.backoff;
+    best->pad = 0;
     best->kernel_ms = cur_ms;
     best->status = GTAP_OK;
     if (n_trials) *n_trials = t.n_out;

@@ -216,6 +216,8 @@ static gtap_status plan_arena(gtap_mode mode, int n_queues, size_t frame_pool_by
     if (cfg.max_roots < 1 || cfg.max_roots > (1 << 24)) return GTAP_ERR_INVALID_ARG;
     if (!cfg.timeout_ns) cfg.timeout_ns = 60ull * 1000000000ull;
     if (!cfg.seed) cfg.seed = 0x5EEDull;
+    if (!cfg.idle_backoff_ns) cfg.idle_backoff_ns = 512;
+    if (cfg.idle_backoff_ns < 32 || cfg.idle_backoff_ns > 65536) return GTAP_ERR_INVALID_ARG;
     if (cfg.grid_blocks < 0) return GTAP_ERR_INVALID_ARG;
     if (cfg.scheduler < 0 || cfg.scheduler > 2) return GTAP_ERR_INVALID_ARG;
     // the scheduler comparison variants are thread-mode designs with one queue per warp
@@ -690,6 +692,7 @@ static gtap_status plan_and_enqueue(gtap_ctx* c, cudaStream_t s, LaunchPlan* lp,
     P.timeout_ns = c->cfg.timeout_ns;
     P.seed = c->cfg.seed;
     P.steal_policy = c->cfg.steal_policy;
+    P.idle_backoff_ns = c->cfg.idle_backoff_ns;
     P.scratch = c->blocks;
     P.scratch_bytes = c->blocks_bytes;
     P.sq_seq = c->sq_seq;

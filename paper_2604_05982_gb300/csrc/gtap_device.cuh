@@ -749,10 +749,10 @@ static __device__ __noinline__ void serve_poller(const KParams& P, const WarpSh&
 // ---------------------------------------------------------------------------
 // Thread-mode scheduler loop (Algorithm 1), one instance per warp.
 // Dispatch is a functor: Dispatch::run(TaskCtx&) executes one step.
-// Longest sleep of an idle warp between steal rounds.  Longer sleeps relieve L2
-// of idle probing (the hashed tree gained 8 % at 4 us) but slow the spread of
-// work at start-up (fib and N-Queens lost 15-25 % at 4 us).
-constexpr int kIdleBackoffMaxNs = 512;
+// The longest sleep of an idle warp between steal rounds is a configuration
+// field (default 512 ns): longer sleeps relieve L2 of idle probing (the hashed
+// tree gained 8 % at 4 us) but slow the spread of work at start-up (fib and
+// N-Queens lost 15-25 % at 4 us), so the autotuner picks it per program.
 
 template <class Dispatch, int SCHED = SCHED_BATCHED>
 __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
@@ -1095,7 +1095,7 @@ __device__ void thread_mode_loop(const KParams& P, char* smem_warp) {
             }
             if (__shfl_sync(0xffffffffu, stop, 0)) break;
             __nanosleep(backoff);
-            backoff = min(backoff * 2, kIdleBackoffMaxNs);
+            backoff = min(backoff * 2, P.idle_backoff_ns);
             { const long long t = clock64(); cy_idle += (unsigned long long)(t - tc0); tc0 = t; }
             continue;
         }

@@ -195,6 +195,7 @@ struct KParams {
     uint64_t timeout_ns;
     uint64_t seed;
     int steal_policy;
+    int idle_backoff_ns;      // thread mode: longest sleep of an idle warp between steal rounds
     int pad0;
     char* scratch;            // scratch blocks for programs (k-clique candidate sets), kScratchBlock bytes each
     uint64_t scratch_bytes;   // bytes of the block region

@@ -45,7 +45,7 @@ class gtap_config(ctypes.Structure):
                 ("frame_bytes", ctypes.c_int), ("device_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
                 ("stream", ctypes.c_void_p), ("timeout_ns", ctypes.c_uint64), ("seed", ctypes.c_uint64),
                 ("scratch_bytes", ctypes.c_size_t), ("grid_blocks", ctypes.c_int), ("debug_checks", ctypes.c_int),
-                ("scheduler", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("scheduler", ctypes.c_int), ("idle_backoff_ns", ctypes.c_int)]
 
 
 class gtap_stats(ctypes.Structure):
@@ -131,10 +131,11 @@ GTAP_FMM_MIXED = 1
 
 class gtap_tune_trial(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int), ("deque_capacity", ctypes.c_int), ("n_queues", ctypes.c_int),
-                ("steal_policy", ctypes.c_int), ("kernel_ms", ctypes.c_float), ("status", ctypes.c_int)]
+                ("steal_policy", ctypes.c_int), ("kernel_ms", ctypes.c_float), ("status", ctypes.c_int),
+                ("idle_backoff_ns", ctypes.c_int), ("pad", ctypes.c_int)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
 
 
 class gtap_completion(ctypes.Structure):
@@ -408,7 +409,7 @@ def gtap_fmm_destroy(f: int) -> None:
     _check(load_library().gtap_fmm_destroy(f), "gtap_fmm_destroy")
 
 
-GTAP_TUNE_BLOCKS, GTAP_TUNE_STEAL, GTAP_TUNE_QUEUES, GTAP_TUNE_CAPACITY = 1, 2, 4, 8
+GTAP_TUNE_BLOCKS, GTAP_TUNE_STEAL, GTAP_TUNE_QUEUES, GTAP_TUNE_CAPACITY, GTAP_TUNE_BACKOFF = 1, 2, 4, 8, 16
 
 
 def gtap_autotune(mode: int, program: str, root_args, frame_pool_bytes: int, base: gtap_config | None = None,

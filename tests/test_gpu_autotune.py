@@ -22,11 +22,13 @@ def test_autotune_thread_mode_nqueens_batch():
     args = [G.gtap_nqueens_args(n, 1) for n in (9, 10, 11)]
     best, trials = G.gtap_autotune(G.GTAP_MODE_THREAD, "nqueens", args, 256 << 20, runner.make_config(), reps=2)
     _check(best, trials)
-    assert len(trials) == 1 + 4 + 3 + 3 + 2
+    # start + blocks/SM 4 + steal 3 + queues 3 + capacity 2 + idle back-off 2
+    assert len(trials) == 1 + 4 + 3 + 3 + 2 + 2
+    assert best["idle_backoff_ns"] in (512, 2048, 8192)
     # the tuned configuration still gives the oracle's counts
     with runner.Context(G.GTAP_MODE_THREAD, best["n_queues"], pool_bytes=256 << 20,
                         blocks_per_sm=best["blocks_per_sm"], deque_capacity=best["deque_capacity"],
-                        steal_policy=best["steal_policy"]) as c:
+                        steal_policy=best["steal_policy"], idle_backoff_ns=best["idle_backoff_ns"]) as c:
         t = c.register("nqueens")
         hs = [c.spawn(t, a) for a in args]
         c.run()

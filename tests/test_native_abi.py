@@ -50,7 +50,7 @@ def test_struct_layouts_match_header(lib_path, tmp_path):
                "gtap_kclique_args": G.gtap_kclique_args, "gtap_uts_args": G.gtap_uts_args,
                "gtap_mergesort_args": G.gtap_mergesort_args, "gtap_fib_args": G.gtap_fib_args,
                "gtap_nqueens_args": G.gtap_nqueens_args, "gtap_bintree_args": G.gtap_bintree_args,
-               "gtap_integrate_args": G.gtap_integrate_args}
+               "gtap_integrate_args": G.gtap_integrate_args, "gtap_tune_trial": G.gtap_tune_trial}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gtap.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
