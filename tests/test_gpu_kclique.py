@@ -79,6 +79,23 @@ def test_batched_graphs_one_launch():
     assert runner.kclique(graphs[5], 4).values == [wants[5]]
 
 
+def test_batched_roots_of_different_k_threshold_and_algorithm():
+    # lanes of one warp hold tasks of different roots: the cooperative passes must take each
+    # item's graph, k and split threshold from its owner lane
+    specs = [(8, 3, 64, 0), (9, 4, 64, 0), (10, 5, 16, 0), (9, 6, 32, 0), (8, 4, 8, 1), (10, 4, 64, 0)]
+    with runner.Context(G.GTAP_MODE_THREAD, 1, scratch_bytes=1 << 30) as c:
+        t = c.register("kclique")
+        hs, wants, keep = [], [], []
+        for i, (scale, k, thr, algo) in enumerate(specs):
+            n, e = inputs.rmat_graph(scale, 16, seed=11 + i)
+            g = _graph(n, e)
+            keep.append(g)
+            hs.append(c.spawn(t, g.args(k, thr, 0, 0, None, algo)))
+            wants.append(oracle.kclique(n, e, k))
+        c.run()
+        assert [c.result_u64(h) for h in hs] == wants
+
+
 def test_scale20_sampled_edge_ranges():
     n, e = inputs.rmat_graph(20, 16, seed=7)
     g = _graph(n, e)
